@@ -1,0 +1,197 @@
+/*
+ * srmra.h -- C ABI of libsrmra.so: projected expectation-maximization for 2D
+ * super-resolution multi-reference alignment (SR-MRA) on one NVIDIA GB300 (sm_103a).
+ *
+ * Method: Shani, Tirer, Giryes, Bendory, "Denoiser-based projections for 2D
+ * super-resolution MRA" (arXiv 2204.04754).  Section references below are to that
+ * paper.
+ *
+ * Data model (Sec. 1, Eq. 1):  y_i = P R_{s_i} x + eps_i,  i = 0..N-1, where
+ *   x      is the L x L high-resolution image (L = L_high),
+ *   R_s    is the 2D circular translation (R_s x)[q1,q2] = x[q1-s1, q2-s2] (mod L),
+ *   P      keeps the l x l samples z[n1*K, n2*K], l = L / K (K integer),
+ *   eps_i  is i.i.d. N(0, sigma^2) noise, s1 ~ rho1, s2 ~ rho2 i.i.d.
+ * The shift index is s = s1 * L + s2 with s1 acting on the first (row) axis.
+ *
+ * One EM iteration (Sec. 2, Eqs. weights_EM, x_EM, rho_EM) maps theta_t = (x, rho1,
+ * rho2) to theta_{t+1}:
+ *   w[i,s]  = rho1[s1] rho2[s2] exp(-||y_i - P R_s x||^2 / (2 sigma^2)) / C_i,
+ *   x_{t+1} = b / A with b = sum_{i,s} w R_s^T P^T y_i and A the diagonal of
+ *             sum_{i,s} w R_s^T P^T P R_s (P^{-1} in the paper read as P^T); a pixel
+ *             with A = 0 keeps its value,
+ *   rho[s]  = sum_i w[i,s] / sum_{i,s'} w[i,s'], rho1 / rho2 its marginals,
+ *   LL(theta_t) = sum_i log sum_s rho[s] exp(-||y_i - P R_s x||^2 / (2 sigma^2))
+ *             (Eq. likelihood_EM without its Gaussian constant).
+ * Projected EM (Algorithm 2) applies a denoiser x <- D(x, sigma_BM) after every F
+ * EM steps and decays sigma_BM_t = 2^{-1/10} sigma_BM_{t-1} (Eq. decaying_function).
+ *
+ * Conventions for every entry point:
+ *   - Arrays are C-contiguous.  y is N x l x l float32 (y[i][n1][n2]); x is L x L
+ *     float32 (x[q1][q2]); rho1 (indexed by s1) and rho2 (by s2) are float64, length L.
+ *   - "host" pointers are ordinary CPU memory (pinned or pageable); "device" pointers
+ *     are CUDA global memory on the context's device.
+ *   - Every call returns srmra_status; no C++ exception crosses this ABI.  On an error
+ *     the context state is unchanged unless the entry point says otherwise, and
+ *     srmra_last_error() returns a message.
+ *   - There is no CPU fallback: without a usable sm_103a GPU every call that needs one
+ *     returns SRMRA_ECUDA.
+ *   - Work is enqueued on the CUDA stream given at creation.  Entry points that return
+ *     host values (log-likelihoods, state) synchronise that stream; the others do not.
+ */
+#ifndef SRMRA_H
+#define SRMRA_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct srmra_ctx srmra_ctx; /* opaque; owned by the library */
+
+typedef enum {
+  SRMRA_OK = 0,
+  SRMRA_EINVAL = 1,   /* invalid argument (shape, sigma, rho not on the simplex, ...) */
+  SRMRA_ENOMEM = 2,   /* device or host allocation failed */
+  SRMRA_ECUDA = 3,    /* CUDA error, or no usable sm_103a device */
+  SRMRA_ETIMEOUT = 4, /* a bounded device-side wait gave up */
+  SRMRA_ENUMERIC = 5, /* NaN / Inf met in the log-likelihood, x or rho */
+  SRMRA_EBUSY = 6     /* context in use by a batched call */
+} srmra_status;
+
+/* Arithmetic of the two contractions <y_i, P R_s x> and sum_i w y_i.
+ *   SRMRA_FP32   : float32 CUDA-core FMA (the plain form).
+ *   SRMRA_BF16   : bf16 tensor-core operands, float32 accumulation and softmax.
+ *   SRMRA_BF16X3 : split-bf16 (hi + lo) for the cross term, hi*hi + hi*lo + lo*hi on
+ *                  tensor cores with float32 accumulation; bf16 weights for the
+ *                  M-step sum.  The global log-likelihood is reduced in float64 in
+ *                  every form. */
+typedef enum { SRMRA_FP32 = 0, SRMRA_BF16 = 1, SRMRA_BF16X3 = 2 } srmra_precision;
+
+/* flags */
+#define SRMRA_FLAG_CHECK_NUMERIC 1u /* scan x, rho, LL for NaN/Inf after each iteration */
+
+typedef struct {
+  int32_t L_high;  /* L >= 2 */
+  int32_t K;       /* down-sampling factor, K >= 1, K divides L */
+  int64_t N;       /* number of observations, N >= 1 */
+  double sigma;    /* noise standard deviation, sigma > 0 */
+  int32_t prec;    /* srmra_precision */
+  uint32_t flags;  /* SRMRA_FLAG_* */
+} srmra_params;
+
+/* A user denoiser D(x, sigma_BM) for srmra_project / srmra_solve.  x_dev is the L x L
+ * float32 image in device memory, valid only during the call; the callback must
+ * enqueue its work on `stream` (a cudaStream_t) and return 0 on success.  A non-zero
+ * return makes the calling entry point fail with SRMRA_EINVAL. */
+typedef int32_t (*srmra_denoiser_fn)(float* x_dev, int32_t L, double sigma_bm,
+                                     void* stream, void* user);
+
+/* srmra_create -- allocate a context for one SR-MRA problem (Eq. 1).
+ *   p          : problem sizes and options.  EINVAL if K does not divide L, sigma <= 0,
+ *                N < 1, L < 2 or prec is unknown.
+ *   y          : N x l x l float32 observations; host memory if y_is_device == 0,
+ *                device memory otherwise.  The library copies them into its own
+ *                device buffers (and derives the layouts its kernels read); the
+ *                caller keeps ownership of y and may free it after the call.
+ *   x0         : L x L float32 initial image (host), or NULL for the nearest-neighbour
+ *                upsampling of the mean observation.
+ *   rho1_0/2_0 : length-L float64 initial distributions (host), or NULL for uniform.
+ *                EINVAL if an entry is negative or the sum is off 1 by more than 1e-6;
+ *                otherwise they are renormalised.
+ *   cuda_stream: cudaStream_t on which all work is enqueued (NULL = legacy default).
+ *   out        : receives the context.  Device memory is held until srmra_destroy.
+ * Errors: EINVAL, ENOMEM (device allocation), ECUDA.  *out is NULL on error. */
+srmra_status srmra_create(const srmra_params* p, const float* y, int32_t y_is_device,
+                          const float* x0, const double* rho1_0, const double* rho2_0,
+                          void* cuda_stream, srmra_ctx** out);
+
+/* srmra_em_iter -- run n_iters EM iterations theta_t -> theta_{t+1} (Sec. 2, Eqs.
+ * weights_EM, x_EM, rho_EM), without projection.
+ *   loglik_out : host array of n_iters float64 receiving LL(theta_t) of each iteration
+ *                (the likelihood of the parameters the E-step used), or NULL.  When it
+ *                is non-NULL the call synchronises the stream and also checks the
+ *                device status word (ETIMEOUT / ENUMERIC).
+ * Errors: EINVAL (n_iters < 0), ECUDA, ETIMEOUT, ENUMERIC. */
+srmra_status srmra_em_iter(srmra_ctx* ctx, int32_t n_iters, double* loglik_out);
+
+/* srmra_project -- x <- D(x, sigma_bm) (Algorithm 2, step 2).  fn == NULL selects the
+ * built-in denoiser: non-overlapping 8 x 8 blocks anchored at pixel (0,0), orthonormal
+ * 2D DCT-II in float64, DC coefficient kept, an AC coefficient kept iff
+ * |c| > 2.7 * sigma_bm, inverse DCT.  The built-in denoiser needs L % 8 == 0 (EINVAL
+ * otherwise).  Does not change the context's sigma_BM. */
+srmra_status srmra_project(srmra_ctx* ctx, double sigma_bm, srmra_denoiser_fn fn,
+                           void* user);
+
+/* srmra_solve -- Algorithm 2 (projected EM) for `iters` EM iterations: after every
+ * iteration whose 1-based global count t+1 is a multiple of F, apply D(x, sigma_BM)
+ * (fn, or the built-in DCT denoiser if fn == NULL) and set sigma_BM <- decay * sigma_BM
+ * (Eq. decaying_function uses decay = 2^{-1/10}).  F == 0 runs plain EM.
+ * sigma_bm1 > 0 resets the context's sigma_BM to sigma_bm1 first (Eq. decaying_function
+ * starts at sigma_BM_1 = 1); sigma_bm1 <= 0 continues from the stored sigma_BM (resume).
+ * loglik_out: host array of `iters` float64 (LL(theta_t) per iteration) or NULL. */
+srmra_status srmra_solve(srmra_ctx* ctx, int32_t iters, int32_t F, double sigma_bm1,
+                         double decay, srmra_denoiser_fn fn, void* user,
+                         double* loglik_out);
+
+/* srmra_get_state -- copy the current estimate to host buffers (any may be NULL):
+ * x (L*L float32), rho1, rho2 (L float64 each), sigma_BM, iteration count t.
+ * Synchronises the stream. */
+srmra_status srmra_get_state(srmra_ctx* ctx, float* x, double* rho1, double* rho2,
+                             double* sigma_bm, int32_t* t);
+
+/* srmra_set_state -- replace the estimate (checkpoint resume).  x: L*L float32 host;
+ * rho1, rho2: L float64 host (validated as in srmra_create); sigma_bm and t are stored
+ * as given.  Resuming from a state returned by srmra_get_state reproduces the
+ * uninterrupted run bit for bit (all reductions have a fixed order). */
+srmra_status srmra_set_state(srmra_ctx* ctx, const float* x, const double* rho1,
+                             const double* rho2, double sigma_bm, int32_t t);
+
+/* srmra_get_lse -- diagnostics of the last E-step: lse[i] = log sum_s rho[s]
+ * exp(-||y_i - P R_s x||^2 / (2 sigma^2)) (float64, N entries, host) and/or the
+ * per-shift weight sums c[s] = sum_i w[i,s] (float64, L*L entries, host).  Either
+ * pointer may be NULL.  EINVAL before the first iteration.  Synchronises. */
+srmra_status srmra_get_estep(srmra_ctx* ctx, double* lse, double* c);
+
+/* srmra_launch_count -- number of CUDA kernels this context has launched so far. */
+srmra_status srmra_launch_count(const srmra_ctx* ctx, int64_t* count);
+
+/* Phases of one iteration, for srmra_profile_read. */
+enum {
+  SRMRA_PHASE_PREP = 0,     /* sub-image statistics, logit column terms, templates */
+  SRMRA_PHASE_PASS1 = 1,    /* logits + online log-sum-exp partials */
+  SRMRA_PHASE_COMBINE = 2,  /* per-observation lse, float64 log-likelihood partials */
+  SRMRA_PHASE_PASS2 = 3,    /* recomputed weights -> M-step partial sums */
+  SRMRA_PHASE_FINAL = 4,    /* rho, coverage, x = b / A */
+  SRMRA_PHASE_DENOISE = 5,  /* built-in denoiser */
+  SRMRA_NUM_PHASES = 6
+};
+
+/* srmra_profile -- enable (1) or disable (0) per-phase timing: CUDA events are recorded
+ * on the context's stream around every phase launched from now on. */
+srmra_status srmra_profile(srmra_ctx* ctx, int32_t enable);
+
+/* srmra_profile_read -- synchronise, then add the device time (ms) and launch count of
+ * every recorded phase since the last read into ms[p] and count[p] (arrays of
+ * SRMRA_NUM_PHASES, host, either may be NULL), and clear the records. */
+srmra_status srmra_profile_read(srmra_ctx* ctx, double* ms, int64_t* count);
+
+/* srmra_sync -- wait for all work enqueued by this context. */
+srmra_status srmra_sync(srmra_ctx* ctx);
+
+/* srmra_destroy -- free the context and its device memory (NULL is a no-op).  Waits
+ * for the context's pending work first. */
+void srmra_destroy(srmra_ctx* ctx);
+
+/* srmra_last_error -- message of the last failing call on ctx (ctx may be NULL: then
+ * the message of the last failing srmra_create in this thread). */
+const char* srmra_last_error(const srmra_ctx* ctx);
+
+/* srmra_version -- library version string. */
+const char* srmra_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SRMRA_H */

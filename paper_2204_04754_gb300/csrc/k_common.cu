@@ -1,0 +1,359 @@
+// Kernels shared by every precision form: observation centring, per-iteration
+// operand preparation, the log-sum-exp combine, the M-step finalisation and the
+// built-in block-DCT denoiser.
+//
+// Notation (Sec. 1-2 of the paper): x is L x L, K = L / l, the template of shift
+// s = (s1, s2) is T_s = P R_s x with T_s[n] = x[(n1 K - s1) mod L, (n2 K - s2) mod L].
+// Writing s = t K - r (mod L, per axis) with r = (-s) mod K, T_s is the low-resolution
+// circular translate by t of the sub-image x_r[m] = x[r + m K] (proof of Theorem 1).
+// The kernels use centred operands: y'_i = y_i - ybar_i and x'_r = x_r - m_r, which
+// turns ||y_i - T_s||^2 into ||y'_i||^2 - 2 <y'_i, T'_s> + nu'_r + l^2 (ybar_i - m_r)^2
+// with nu'_r = ||x'_r||^2 (exact algebra; it shrinks the operands of the contraction).
+#include <math.h>
+
+#include "srmra_internal.cuh"
+
+namespace srmra {
+
+namespace {
+
+constexpr double kLog2e = 1.4426950408889634073599246810019;
+constexpr double kLn2 = 0.69314718055994530941723212145818;
+
+__device__ __forceinline__ int mod_pos(int a, int m) {
+  int r = a % m;
+  return r < 0 ? r + m : r;
+}
+
+// Block-wide float64 sum with a fixed reduction tree (deterministic).
+template <int NT>
+__device__ double block_sum_f64(double v, double* red) {
+  red[threadIdx.x] = v;
+  __syncthreads();
+#pragma unroll 1
+  for (int w = NT / 2; w > 0; w >>= 1) {
+    if (threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+    __syncthreads();
+  }
+  double r = red[0];
+  __syncthreads();
+  return r;
+}
+
+// y'_i = y_i - mean(y_i); per-row mean and ||y'_i||^2 (float64 accumulation).
+__global__ void __launch_bounds__(128) k_center_obs(const float* __restrict__ y, int l2,
+                                                    int ldy, float* __restrict__ Yc,
+                                                    float* __restrict__ ybar,
+                                                    double* __restrict__ yy) {
+  __shared__ double red[128];
+  const int64_t i = blockIdx.x;
+  const float* yi = y + i * (int64_t)l2;
+  double s = 0.0;
+  for (int n = threadIdx.x; n < l2; n += 128) s += (double)yi[n];
+  const double mean = block_sum_f64<128>(s, red) / (double)l2;
+  double q = 0.0;
+  for (int n = threadIdx.x; n < ldy; n += 128) {
+    float v = 0.f;
+    if (n < l2) {
+      const double d = (double)yi[n] - mean;
+      v = (float)d;
+      q += d * d;
+    }
+    Yc[i * ldy + n] = v;
+  }
+  const double qq = block_sum_f64<128>(q, red);
+  if (threadIdx.x == 0) {
+    ybar[i] = (float)mean;
+    yy[i] = qq;
+  }
+}
+
+// out[c][r] = in[r][c] for an R x C row-major matrix (32 x 32 tiles).
+__global__ void k_transpose(const float* __restrict__ in, int64_t R, int64_t C,
+                            float* __restrict__ out) {
+  __shared__ float tile[32][33];
+  const int64_t r0 = (int64_t)blockIdx.y * 32, c0 = (int64_t)blockIdx.x * 32;
+  for (int k = threadIdx.y; k < 32; k += 8) {
+    const int64_t r = r0 + k, c = c0 + threadIdx.x;
+    tile[k][threadIdx.x] = (r < R && c < C) ? in[r * C + c] : 0.f;
+  }
+  __syncthreads();
+  for (int k = threadIdx.y; k < 32; k += 8) {
+    const int64_t c = c0 + k, r = r0 + threadIdx.x;
+    if (c < C && r < R) out[c * R + r] = tile[threadIdx.x][k];
+  }
+}
+
+// Sub-image statistics: m_r = mean(x_r), nu'_r = ||x_r - m_r||^2 (float64).
+__global__ void __launch_bounds__(256) k_sub_stats(const float* __restrict__ x, int L, int K,
+                                                   int l, double* __restrict__ sub) {
+  __shared__ double red[256];
+  const int r = blockIdx.x, r1 = r / K, r2 = r % K, l2 = l * l;
+  double s = 0.0;
+  for (int m = threadIdx.x; m < l2; m += 256)
+    s += (double)x[(r1 + (m / l) * K) * L + r2 + (m % l) * K];
+  const double mean = block_sum_f64<256>(s, red) / (double)l2;
+  double q = 0.0;
+  for (int m = threadIdx.x; m < l2; m += 256) {
+    const double d = (double)x[(r1 + (m / l) * K) * L + r2 + (m % l) * K] - mean;
+    q += d * d;
+  }
+  const double nu = block_sum_f64<256>(q, red);
+  if (threadIdx.x == 0) {
+    sub[r] = mean;
+    sub[K * K + r] = nu;
+  }
+}
+
+// Column terms of the logit: colb[s] = log2(e) (-nu'_r / (2 sigma^2) + log rho1[s1] +
+// log rho2[s2]), colm[s] = m_r.  Padding columns get -inf / 0.
+__global__ void k_columns(const double* __restrict__ sub, const double* __restrict__ rho1,
+                          const double* __restrict__ rho2, int L, int K, int S, int Spad,
+                          double inv2s2, float* __restrict__ colb, float* __restrict__ colm) {
+  const int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= Spad) return;
+  if (s >= S) {
+    colb[s] = -INFINITY;
+    colm[s] = 0.f;
+    return;
+  }
+  const int s1 = s / L, s2 = s % L;
+  const int r = mod_pos(-s1, K) * K + mod_pos(-s2, K);
+  const double lr = log(rho1[s1]) + log(rho2[s2]);  // -inf for a zero entry
+  colb[s] = (float)(kLog2e * (lr - sub[K * K + r] * inv2s2));
+  colm[s] = (float)sub[r];
+}
+
+// Centred templates, pixel-major: AxT[n][s] = x'_r(s)[n - t(s)] (zero for padding).
+__global__ void k_templates_T(const float* __restrict__ x, const double* __restrict__ sub,
+                              int L, int K, int l, int S, int Spad, int l2,
+                              float* __restrict__ AxT) {
+  const int s = blockIdx.x * blockDim.x + threadIdx.x;
+  const int n = blockIdx.y;
+  if (s >= Spad) return;
+  float v = 0.f;
+  if (s < S && n < l2) {
+    const int s1 = s / L, s2 = s % L;
+    const int r1 = mod_pos(-s1, K), r2 = mod_pos(-s2, K);
+    const int t1 = ((s1 + r1) / K) % l, t2 = ((s2 + r2) / K) % l;
+    const int m1 = mod_pos(n / l - t1, l), m2 = mod_pos(n % l - t2, l);
+    v = (float)((double)x[(r1 + m1 * K) * L + r2 + m2 * K] - sub[r1 * K + r2]);
+  }
+  AxT[(int64_t)n * Spad + s] = v;
+}
+
+// Combine the per-group (max, sum) partials of pass 1 into lse2[i] (base 2, of the
+// centred logits) and the per-observation log-likelihood
+//   lse[i] = ln 2 * lse2[i] - ||y'_i||^2 / (2 sigma^2)
+// = log sum_s rho[s] exp(-||y_i - T_s||^2 / (2 sigma^2)); block partial sums in float64.
+__global__ void __launch_bounds__(256) k_lse_combine(
+    const float* __restrict__ pm, const float* __restrict__ ps, int groups, int64_t Npad,
+    int64_t N, const double* __restrict__ yy, double inv2s2, float* __restrict__ lse2,
+    double* __restrict__ lse, double* __restrict__ llpart) {
+  __shared__ double red[256];
+  const int64_t i = (int64_t)blockIdx.x * 256 + threadIdx.x;
+  double ll = 0.0;
+  if (i < N) {
+    float m = -INFINITY;
+    for (int gI = 0; gI < groups; ++gI) m = fmaxf(m, pm[gI * Npad + i]);
+    double s = 0.0;
+    if (m != -INFINITY)
+      for (int gI = 0; gI < groups; ++gI) {
+        const float mg = pm[gI * Npad + i];
+        if (mg != -INFINITY) s += (double)ps[gI * Npad + i] * exp2((double)mg - (double)m);
+      }
+    const double l2v = (double)m + log2(s);
+    lse2[i] = (float)l2v;
+    ll = kLn2 * l2v - yy[i] * inv2s2;
+    lse[i] = ll;
+  } else if (i < Npad) {
+    lse2[i] = 0.f;
+  }
+  const double tot = block_sum_f64<256>(ll, red);
+  if (threadIdx.x == 0) llpart[blockIdx.x] = tot;
+}
+
+// M-step totals (single block, fixed-order float64 reductions):
+//   c_s = sum of the partial weight sums, zb_s likewise;
+//   rho (Eq. rho_EM): joint c_s / sum c, marginals rho1, rho2;
+//   coverage A_r = sum_t c_{(r,t)} and ZB_r = sum_t zb_{(r,t)} per sub-image;
+//   LL(theta_t) = sum of the lse-combine block partials.
+__global__ void __launch_bounds__(1024) k_fin_counts(
+    const float* __restrict__ cp, const float* __restrict__ zbp, int nparts, int Spad, int S,
+    int L, int K, int l, const double* __restrict__ llpart, int ll_blocks,
+    double* __restrict__ rho1, double* __restrict__ rho2, double* __restrict__ Ar,
+    double* __restrict__ cfin, double* __restrict__ ll_out, int* __restrict__ status) {
+  __shared__ double red[1024];
+  double loc = 0.0;
+  for (int s = threadIdx.x; s < S; s += 1024) {
+    double c = 0.0, z = 0.0;
+    for (int p = 0; p < nparts; ++p) {
+      c += (double)cp[(int64_t)p * Spad + s];
+      z += (double)zbp[(int64_t)p * Spad + s];
+    }
+    cfin[s] = c;
+    cfin[Spad + s] = z;
+    loc += c;
+  }
+  const double ctot = block_sum_f64<1024>(loc, red);  // also orders the cfin writes
+  for (int j = threadIdx.x; j < 2 * L; j += 1024) {
+    double acc = 0.0;
+    if (j < L) {
+      for (int s2 = 0; s2 < L; ++s2) acc += cfin[j * L + s2];
+      rho1[j] = acc / ctot;
+    } else {
+      const int s2 = j - L;
+      for (int s1 = 0; s1 < L; ++s1) acc += cfin[s1 * L + s2];
+      rho2[s2] = acc / ctot;
+    }
+  }
+  const int l2 = l * l;
+  for (int r = threadIdx.x; r < K * K; r += 1024) {
+    const int r1 = r / K, r2 = r % K;
+    double a = 0.0, z = 0.0;
+    for (int t = 0; t < l2; ++t) {
+      const int s1 = mod_pos((t / l) * K - r1, L), s2 = mod_pos((t % l) * K - r2, L);
+      a += cfin[s1 * L + s2];
+      z += cfin[Spad + s1 * L + s2];
+    }
+    Ar[r] = a;
+    Ar[K * K + r] = z;
+  }
+  if (threadIdx.x == 0) {
+    double ll = 0.0;
+    for (int b = 0; b < ll_blocks; ++b) ll += llpart[b];
+    *ll_out = ll;
+    if (!isfinite(ll) || !(ctot > 0.0) || !isfinite(ctot)) atomicOr(status, STATUS_NUMERIC);
+  }
+}
+
+// x_{t+1}[q] = (b'[q] + ZB_r) / A_r with b'[q] = sum_t Z'[s(r,t)][m + t] summed over the
+// partial slices (Eq. x_EM on sub-image r = q mod K, m = q div K); one warp per pixel.
+// A pixel with A_r = 0 keeps its value (reading of an uncovered pixel).
+__global__ void __launch_bounds__(256) k_fin_x(const float* __restrict__ Zp, int nparts,
+                                               int Spad, int ldy, int L, int K, int l,
+                                               const double* __restrict__ Ar,
+                                               float* __restrict__ x,
+                                               int* __restrict__ status) {
+  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (warp >= L * L) return;
+  const int q1 = warp / L, q2 = warp % L;
+  const int r1 = q1 % K, r2 = q2 % K, m1 = q1 / K, m2 = q2 / K;
+  const int l2 = l * l;
+  double acc = 0.0;
+  for (int t = lane; t < l2; t += 32) {
+    const int t1 = t / l, t2 = t % l;
+    const int s = mod_pos(t1 * K - r1, L) * L + mod_pos(t2 * K - r2, L);
+    const int n = ((m1 + t1) % l) * l + (m2 + t2) % l;
+    for (int p = 0; p < nparts; ++p) acc += (double)Zp[((int64_t)p * Spad + s) * ldy + n];
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  if (lane == 0) {
+    const int r = r1 * K + r2;
+    const double A = Ar[r];
+    if (A > 0.0) {
+      const double v = (acc + Ar[K * K + r]) / A;
+      x[warp] = (float)v;
+      if (!isfinite(v)) atomicOr(status, STATUS_NUMERIC);
+    }
+  }
+}
+
+// Built-in denoiser: per 8x8 block, orthonormal 2D DCT-II in float64, keep DC and the
+// AC coefficients with |c| > thr, inverse transform.
+__global__ void __launch_bounds__(64) k_dct8(float* __restrict__ x, int L, double thr) {
+  __shared__ double C[8][8], B[8][8], T[8][8];
+  const int u = threadIdx.x >> 3, v = threadIdx.x & 7;
+  const int b1 = blockIdx.x / (L / 8), b2 = blockIdx.x % (L / 8);
+  C[u][v] = (u == 0 ? sqrt(0.125) : 0.5) * cospi((double)((2 * v + 1) * u) / 16.0);
+  float* px = x + (b1 * 8 + u) * L + b2 * 8 + v;
+  B[u][v] = (double)*px;
+  __syncthreads();
+  double a = 0.0;
+#pragma unroll
+  for (int k = 0; k < 8; ++k) a += C[u][k] * B[k][v];  // C B
+  T[u][v] = a;
+  __syncthreads();
+  double X = 0.0;
+#pragma unroll
+  for (int k = 0; k < 8; ++k) X += T[u][k] * C[v][k];  // (C B) C^T
+  const bool keep = (u == 0 && v == 0) || fabs(X) > thr;
+  __syncthreads();
+  B[u][v] = keep ? X : 0.0;
+  __syncthreads();
+  a = 0.0;
+#pragma unroll
+  for (int k = 0; k < 8; ++k) a += C[k][u] * B[k][v];  // C^T X
+  T[u][v] = a;
+  __syncthreads();
+  double o = 0.0;
+#pragma unroll
+  for (int k = 0; k < 8; ++k) o += T[u][k] * C[k][v];  // (C^T X) C
+  *px = (float)o;
+}
+
+}  // namespace
+
+LogitScalars logit_scalars(const Geom& g) {
+  LogitScalars s;
+  const double inv_s2 = 1.0 / (g.sigma * g.sigma);
+  s.a2 = (float)(kLog2e * inv_s2);
+  s.c2 = (float)(kLog2e * (double)g.l2 * 0.5 * inv_s2);
+  return s;
+}
+
+void launch_center_obs(srmra_ctx* c, const float* y_dev) {
+  const Geom& g = c->g;
+  k_center_obs<<<(unsigned)g.N, 128, 0, c->stream>>>(y_dev, g.l2, g.ldy, c->Yc, c->ybar, c->yy);
+  c->launches++;
+  if (c->YcT) {
+    dim3 grid((unsigned)ceil_div(g.ldy, 32), (unsigned)ceil_div(g.Npad, 32));
+    k_transpose<<<grid, dim3(32, 8), 0, c->stream>>>(c->Yc, g.Npad, g.ldy, c->YcT);
+    c->launches++;
+  }
+}
+
+void launch_prep_iter(srmra_ctx* c) {
+  const Geom& g = c->g;
+  k_sub_stats<<<g.K * g.K, 256, 0, c->stream>>>(c->x, g.L, g.K, g.l, c->sub);
+  k_columns<<<(unsigned)ceil_div(g.Spad, 256), 256, 0, c->stream>>>(
+      c->sub, c->rho1, c->rho2, g.L, g.K, g.S, g.Spad, 0.5 / (g.sigma * g.sigma), c->colb,
+      c->colm);
+  c->launches += 2;
+  if (c->AxT) {
+    dim3 grid((unsigned)ceil_div(g.Spad, 256), (unsigned)g.ldy);
+    k_templates_T<<<grid, 256, 0, c->stream>>>(c->x, c->sub, g.L, g.K, g.l, g.S, g.Spad,
+                                                g.l2, c->AxT);
+    c->launches++;
+  }
+}
+
+void launch_lse_combine(srmra_ctx* c, int groups) {
+  const Geom& g = c->g;
+  k_lse_combine<<<c->plan.ll_blocks, 256, 0, c->stream>>>(
+      c->pm, c->ps, groups, g.Npad, g.N, c->yy, 0.5 / (g.sigma * g.sigma), c->lse2, c->lse,
+      c->llpart);
+  c->launches++;
+}
+
+void launch_finalize(srmra_ctx* c, int ll_index) {
+  const Geom& g = c->g;
+  k_fin_counts<<<1, 1024, 0, c->stream>>>(c->cp, c->zbp, c->plan.nparts_c, g.Spad, g.S, g.L,
+                                          g.K, g.l, c->llpart, c->plan.ll_blocks, c->rho1,
+                                          c->rho2, c->Ar, c->cfin, c->ll_hist + ll_index,
+                                          c->status);
+  const int warps = g.L * g.L;
+  k_fin_x<<<(unsigned)ceil_div(warps, 8), 256, 0, c->stream>>>(
+      c->Zp, c->plan.nparts_z, g.Spad, g.ldy, g.L, g.K, g.l, c->Ar, c->x, c->status);
+  c->launches += 2;
+}
+
+void launch_dct_denoise(srmra_ctx* c, double sigma_bm, double thr) {
+  const Geom& g = c->g;
+  k_dct8<<<(g.L / 8) * (g.L / 8), 64, 0, c->stream>>>(c->x, g.L, thr * sigma_bm);
+  c->launches++;
+}
+
+}  // namespace srmra

@@ -1,0 +1,418 @@
+// Float32 form of the E-step / M-step contractions on CUDA cores (FFMA).
+//
+// Pass 1 (Eq. weights_EM, Eq. likelihood_EM): for an observation tile and a group of
+// shift tiles, logit2[i,s] = a2 <y'_i, T'_s> + colb[s] - c2 (ybar_i - colm[s])^2 and the
+// running (max, sum of 2^(logit2 - max)) per observation -> partials per shift group.
+//
+// Pass 2 (Eq. x_EM, Eq. rho_EM): w[i,s] = 2^(logit2[i,s] - lse2[i]) is recomputed from
+// the same contraction, and the M-step sums
+//   Z'[s][n] = sum_i w[i,s] y'_i[n],  c[s] = sum_i w[i,s],  zb[s] = sum_i w[i,s] ybar_i
+// are accumulated.  The N x L^2 weight matrix is never stored: a cluster of gc CTAs
+// (one per 256-pixel chunk of Z') works on one 64-shift tile; each CTA computes the
+// weights of its own 64 observations per round and the others read them through
+// distributed shared memory, so no CTA recomputes another's logits.
+#include <cooperative_groups.h>
+
+#include "srmra_internal.cuh"
+
+namespace cg = cooperative_groups;
+
+namespace srmra {
+
+namespace {
+
+__device__ __forceinline__ float4 ld4(const float* p) {
+  return *reinterpret_cast<const float4*>(p);
+}
+__device__ __forceinline__ void st4(float* p, float4 v) {
+  *reinterpret_cast<float4*>(p) = v;
+}
+
+// ----------------------------------------------------------------------------- pass 1
+// Tile 128 observations x 128 shifts, 256 threads, 8x8 outputs per thread, k-step 8.
+// Operands are pixel-major: YcT[k][i], AxT[k][s].
+__global__ void __launch_bounds__(256, 2)
+    k_p1_f32(const float* __restrict__ YcT, int64_t Npad, const float* __restrict__ AxT,
+             int Spad, int ldy, const float* __restrict__ ybar,
+             const float* __restrict__ colb, const float* __restrict__ colm, float a2,
+             float c2, int tiles_per_group, int n_tiles, int64_t N, float* __restrict__ pm,
+             float* __restrict__ ps) {
+  __shared__ __align__(16) float As[2][8][128];
+  __shared__ __align__(16) float Bs[2][8][128];
+  const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+  const int64_t i0 = (int64_t)blockIdx.x * 128;
+  const int grp = blockIdx.y;
+  const int tb = grp * tiles_per_group;
+  const int te = min(n_tiles, tb + tiles_per_group);
+  const int lk = tid >> 5, lc = (tid & 31) * 4;
+
+  float yb[8], rm[8], rs[8];
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    yb[j] = ybar[i0 + ty * 4 + j];
+    yb[4 + j] = ybar[i0 + 64 + ty * 4 + j];
+  }
+#pragma unroll
+  for (int j = 0; j < 8; ++j) {
+    rm[j] = -INFINITY;
+    rs[j] = 0.f;
+  }
+
+  for (int tile = tb; tile < te; ++tile) {
+    const int s0 = tile * 128;
+    float acc[8][8];
+#pragma unroll
+    for (int j = 0; j < 8; ++j)
+#pragma unroll
+      for (int c = 0; c < 8; ++c) acc[j][c] = 0.f;
+
+    float4 ra = ld4(YcT + (int64_t)lk * Npad + i0 + lc);
+    float4 rb = ld4(AxT + (int64_t)lk * Spad + s0 + lc);
+    st4(&As[0][lk][lc], ra);
+    st4(&Bs[0][lk][lc], rb);
+    __syncthreads();
+    int cur = 0;
+    for (int kc = 0; kc < ldy; kc += 8) {
+      const bool more = kc + 8 < ldy;
+      if (more) {
+        ra = ld4(YcT + (int64_t)(kc + 8 + lk) * Npad + i0 + lc);
+        rb = ld4(AxT + (int64_t)(kc + 8 + lk) * Spad + s0 + lc);
+      }
+#pragma unroll
+      for (int kk = 0; kk < 8; ++kk) {
+        const float4 a0 = ld4(&As[cur][kk][ty * 4]);
+        const float4 a1 = ld4(&As[cur][kk][64 + ty * 4]);
+        const float4 b0 = ld4(&Bs[cur][kk][tx * 4]);
+        const float4 b1 = ld4(&Bs[cur][kk][64 + tx * 4]);
+        const float a[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
+        const float b[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
+#pragma unroll
+        for (int j = 0; j < 8; ++j)
+#pragma unroll
+          for (int c = 0; c < 8; ++c) acc[j][c] = fmaf(a[j], b[c], acc[j][c]);
+      }
+      if (more) {
+        st4(&As[cur ^ 1][lk][lc], ra);
+        st4(&Bs[cur ^ 1][lk][lc], rb);
+      }
+      __syncthreads();
+      cur ^= 1;
+    }
+
+    // online log-sum-exp over this tile's 128 shifts (16 lanes share a row)
+    float cb[8], cm[8];
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      cb[c] = colb[s0 + tx * 4 + c];
+      cm[c] = colm[s0 + tx * 4 + c];
+      cb[4 + c] = colb[s0 + 64 + tx * 4 + c];
+      cm[4 + c] = colm[s0 + 64 + tx * 4 + c];
+    }
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      float v[8];
+      float mx = -INFINITY;
+#pragma unroll
+      for (int c = 0; c < 8; ++c) {
+        const float d = yb[j] - cm[c];
+        v[c] = fmaf(acc[j][c], a2, cb[c]) - c2 * d * d;
+        mx = fmaxf(mx, v[c]);
+      }
+#pragma unroll
+      for (int o = 1; o < 16; o <<= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+      const float nm = fmaxf(rm[j], mx);
+      const float base = (nm == -INFINITY) ? 0.f : nm;
+      float sm = 0.f;
+#pragma unroll
+      for (int c = 0; c < 8; ++c) sm += exp2f(v[c] - base);
+#pragma unroll
+      for (int o = 1; o < 16; o <<= 1) sm += __shfl_xor_sync(0xffffffffu, sm, o);
+      rs[j] = rs[j] * exp2f(rm[j] - base) + sm;
+      rm[j] = nm;
+    }
+  }
+  if (tx == 0) {
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      const int64_t i = i0 + (j < 4 ? ty * 4 + j : 64 + ty * 4 + (j - 4));
+      if (i < N) {
+        pm[grp * Npad + i] = rm[j];
+        ps[grp * Npad + i] = rs[j];
+      }
+    }
+  }
+}
+
+// ----------------------------------------------------------------------------- pass 2
+// Cluster of gc CTAs (blockIdx.x = rank), one 64-shift tile (blockIdx.y), one
+// observation range x chunk group (blockIdx.z).  Per round each rank computes the
+// 64x64 weight tile of its own observation block (phase A+B), then every rank
+// accumulates Z' over its 256-pixel chunk for all gc blocks of the round (phase C),
+// reading the other ranks' weight tiles from their shared memory.
+constexpr int P2_SMEM_FLOATS = 2 * 64 * 64 + 2 * 16 * 256;  // P[2] + staging
+constexpr size_t P2_SMEM_BYTES = P2_SMEM_FLOATS * sizeof(float);
+
+__global__ void __launch_bounds__(256, 1)
+    k_p2_f32(const float* __restrict__ YcT, const float* __restrict__ Yc, int64_t Npad,
+             const float* __restrict__ AxT, int Spad, int ldy,
+             const float* __restrict__ ybar, const float* __restrict__ colb,
+             const float* __restrict__ colm, const float* __restrict__ lse2, float a2,
+             float c2, int64_t N, int S, int n_iblk, int iblk_per_split, int gc,
+             int n_cgroups, float* __restrict__ Zp, float* __restrict__ cp,
+             float* __restrict__ zbp) {
+  extern __shared__ __align__(16) float smem[];
+  float* const Pbuf = smem;             // [2][64 obs][64 shifts]
+  float* const stg = smem + 2 * 4096;   // phase A: As[2][16][64], Bs[2][16][64]; C: Ys[2][16][256]
+  cg::cluster_group cluster = cg::this_cluster();
+  const int rank = (int)cluster.block_rank();
+  const int tid = threadIdx.x;
+  const int s0 = blockIdx.y * 64;
+  const int split = blockIdx.z / n_cgroups, cgrp = blockIdx.z % n_cgroups;
+  const int p0 = (cgrp * gc + rank) * 256;
+  const int b_begin = split * iblk_per_split;
+  const int b_end = min(n_iblk, b_begin + iblk_per_split);
+  const int nb = max(0, b_end - b_begin);
+  const int rounds = (nb + gc - 1) / gc;
+
+  const int ts = tid & 15, ti = tid >> 4;   // phase A/B: 4 shifts x 4 observations
+  const int sg = tid >> 5, pg = tid & 31;   // phase C: 8 shifts x 8 pixels
+  const int lk = tid >> 4, lc = (tid & 15) * 4;
+
+  float z[8][8];
+#pragma unroll
+  for (int a = 0; a < 8; ++a)
+#pragma unroll
+    for (int b = 0; b < 8; ++b) z[a][b] = 0.f;
+  float cacc[4] = {0.f, 0.f, 0.f, 0.f}, zacc[4] = {0.f, 0.f, 0.f, 0.f};
+  float cbA[4], cmA[4];
+#pragma unroll
+  for (int a = 0; a < 4; ++a) {
+    cbA[a] = colb[s0 + ts * 4 + a];
+    cmA[a] = colm[s0 + ts * 4 + a];
+  }
+
+  for (int rd = 0; rd < rounds; ++rd) {
+    float* const P = Pbuf + (rd & 1) * 4096;
+    const int myb = b_begin + rd * gc + rank;
+    if (myb < b_end) {
+      // phase A: S[s][i] = <T'_s, y'_i>, 64 x 64, k-step 16
+      const int64_t ib = (int64_t)myb * 64;
+      float acc[4][4];
+#pragma unroll
+      for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b = 0; b < 4; ++b) acc[a][b] = 0.f;
+      float* const As = stg;
+      float* const Bs = stg + 2048;
+      float4 ra = ld4(AxT + (int64_t)lk * Spad + s0 + lc);
+      float4 rb = ld4(YcT + (int64_t)lk * Npad + ib + lc);
+      st4(As + lk * 64 + lc, ra);
+      st4(Bs + lk * 64 + lc, rb);
+      __syncthreads();
+      int cur = 0;
+      for (int kc = 0; kc < ldy; kc += 16) {
+        const bool more = kc + 16 < ldy;
+        if (more) {
+          ra = ld4(AxT + (int64_t)(kc + 16 + lk) * Spad + s0 + lc);
+          rb = ld4(YcT + (int64_t)(kc + 16 + lk) * Npad + ib + lc);
+        }
+        const float* Ac = As + cur * 1024;
+        const float* Bc = Bs + cur * 1024;
+#pragma unroll
+        for (int kk = 0; kk < 16; ++kk) {
+          const float4 a4 = ld4(Ac + kk * 64 + ts * 4);
+          const float4 b4 = ld4(Bc + kk * 64 + ti * 4);
+          const float av[4] = {a4.x, a4.y, a4.z, a4.w};
+          const float bv[4] = {b4.x, b4.y, b4.z, b4.w};
+#pragma unroll
+          for (int a = 0; a < 4; ++a)
+#pragma unroll
+            for (int b = 0; b < 4; ++b) acc[a][b] = fmaf(av[a], bv[b], acc[a][b]);
+        }
+        if (more) {
+          st4(As + (cur ^ 1) * 1024 + lk * 64 + lc, ra);
+          st4(Bs + (cur ^ 1) * 1024 + lk * 64 + lc, rb);
+        }
+        __syncthreads();
+        cur ^= 1;
+      }
+      // phase B: w = 2^(logit2 - lse2), partial c and zb
+#pragma unroll
+      for (int b = 0; b < 4; ++b) {
+        const int64_t i = ib + ti * 4 + b;
+        const float yb = ybar[i];
+        const float ls = lse2[i];
+        const bool iv = i < N;
+        float w[4];
+#pragma unroll
+        for (int a = 0; a < 4; ++a) {
+          const float d = yb - cmA[a];
+          const float v = fmaf(acc[a][b], a2, cbA[a]) - c2 * d * d - ls;
+          w[a] = (iv && (s0 + ts * 4 + a) < S) ? exp2f(v) : 0.f;
+          cacc[a] += w[a];
+          zacc[a] = fmaf(w[a], yb, zacc[a]);
+        }
+        st4(P + (ti * 4 + b) * 64 + ts * 4, make_float4(w[0], w[1], w[2], w[3]));
+      }
+    }
+    cluster.sync();  // weight tiles of this round are complete in every rank
+
+    // phase C: Z'[s][p] += sum_i w[i][s] y'_i[p] over the round's observation blocks
+    const int nq = min(gc, b_end - (b_begin + rd * gc));
+    const int nchunks = nq * 4;
+    float* const Ys = stg;
+    float4 rY[4];
+    auto loadY = [&](int cidx) {
+      const int q = cidx >> 2, ic = (cidx & 3) * 16;
+      const int64_t ib = (int64_t)(b_begin + rd * gc + q) * 64 + ic;
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const int row = (tid >> 6) + 4 * j, col = (tid & 63) * 4;
+        const int p = p0 + col;
+        rY[j] = (p < ldy) ? ld4(Yc + (ib + row) * ldy + p) : make_float4(0.f, 0.f, 0.f, 0.f);
+      }
+    };
+    auto storeY = [&](int buf) {
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const int row = (tid >> 6) + 4 * j, col = (tid & 63) * 4;
+        st4(Ys + buf * 4096 + row * 256 + col, rY[j]);
+      }
+    };
+    if (nchunks > 0) {
+      loadY(0);
+      storeY(0);
+    }
+    __syncthreads();
+    for (int cidx = 0; cidx < nchunks; ++cidx) {
+      const int cur = cidx & 1;
+      if (cidx + 1 < nchunks) loadY(cidx + 1);
+      const int q = cidx >> 2, ic = (cidx & 3) * 16;
+      const float* Pq = cluster.map_shared_rank(P, q) + ic * 64 + sg * 8;
+      const float* Yb = Ys + cur * 4096;
+#pragma unroll
+      for (int k = 0; k < 16; ++k) {
+        const float4 w0 = ld4(Pq + k * 64);
+        const float4 w1 = ld4(Pq + k * 64 + 4);
+        const float4 y0 = ld4(Yb + k * 256 + pg * 4);
+        const float4 y1 = ld4(Yb + k * 256 + 128 + pg * 4);
+        const float wv[8] = {w0.x, w0.y, w0.z, w0.w, w1.x, w1.y, w1.z, w1.w};
+        const float yv[8] = {y0.x, y0.y, y0.z, y0.w, y1.x, y1.y, y1.z, y1.w};
+#pragma unroll
+        for (int a = 0; a < 8; ++a)
+#pragma unroll
+          for (int b = 0; b < 8; ++b) z[a][b] = fmaf(wv[a], yv[b], z[a][b]);
+      }
+      if (cidx + 1 < nchunks) storeY(cur ^ 1);
+      __syncthreads();
+    }
+  }
+  cluster.sync();  // no rank leaves while another may still read its weight tiles
+
+  // partial M-step sums of this (observation range, shift tile, pixel chunk)
+#pragma unroll
+  for (int a = 0; a < 8; ++a) {
+    const int s = s0 + sg * 8 + a;
+    float* zr = Zp + ((int64_t)split * Spad + s) * ldy;
+    const int pa = p0 + pg * 4, pb = p0 + 128 + pg * 4;
+    if (pa < ldy) st4(zr + pa, make_float4(z[a][0], z[a][1], z[a][2], z[a][3]));
+    if (pb < ldy) st4(zr + pb, make_float4(z[a][4], z[a][5], z[a][6], z[a][7]));
+  }
+  if (cgrp == 0) {
+    float* red = stg;  // [16][64] c, then [16][64] zb
+    __syncthreads();
+#pragma unroll
+    for (int a = 0; a < 4; ++a) {
+      red[ti * 64 + ts * 4 + a] = cacc[a];
+      red[1024 + ti * 64 + ts * 4 + a] = zacc[a];
+    }
+    __syncthreads();
+    if (tid < 64) {
+      float c = 0.f, zb = 0.f;
+      for (int k = 0; k < 16; ++k) {
+        c += red[k * 64 + tid];
+        zb += red[1024 + k * 64 + tid];
+      }
+      const int64_t part = (int64_t)split * gc + rank;
+      cp[part * Spad + s0 + tid] = c;
+      zbp[part * Spad + s0 + tid] = zb;
+    }
+  }
+}
+
+}  // namespace
+
+void plan_simt(srmra_ctx* c) {
+  const Geom& g = c->g;
+  Plan& p = c->plan;
+  const int slots = c->num_sms * 2;
+  const int n_tiles = g.Spad / P1_BN;
+  const int iblk1 = (int)(g.Npad / P1_BM);
+  int G = (int)ceil_div(4 * (int64_t)slots, iblk1);
+  G = G < 1 ? 1 : (G > n_tiles ? n_tiles : G);
+  p.p1_tiles_per_group = (int)ceil_div(n_tiles, G);
+  p.p1_groups = (int)ceil_div(n_tiles, p.p1_tiles_per_group);
+
+  const int chunks = (int)ceil_div(g.l2, P2_BP);
+  p.p2_chunk_groups = (int)ceil_div(chunks, 8);
+  p.p2_gc = (int)ceil_div(chunks, p.p2_chunk_groups);
+  const int n_iblk2 = (int)(g.Npad / P2_BI);
+  const int64_t per_split = (int64_t)p.p2_gc * (g.Spad / P2_BS) * p.p2_chunk_groups;
+  int ns = (int)((4 * (int64_t)slots + per_split / 2) / per_split);
+  const int max_ns = (n_iblk2 + p.p2_gc - 1) / p.p2_gc;
+  ns = ns < 1 ? 1 : (ns > max_ns ? max_ns : ns);
+  if (ns > 32) ns = 32;
+  p.p2_iblk_per_split = (int)round_up(ceil_div(n_iblk2, ns), p.p2_gc);
+  p.p2_nsplit = (int)ceil_div(n_iblk2, p.p2_iblk_per_split);
+  p.nparts_z = p.p2_nsplit;
+  p.nparts_c = p.p2_nsplit * p.p2_gc;
+  p.ll_blocks = (int)ceil_div(g.Npad, 256);
+}
+
+void launch_pass1_f32(srmra_ctx* c) {
+  const Geom& g = c->g;
+  const Plan& p = c->plan;
+  const LogitScalars ls = logit_scalars(g);
+  dim3 grid((unsigned)(g.Npad / P1_BM), (unsigned)p.p1_groups);
+  k_p1_f32<<<grid, 256, 0, c->stream>>>(c->YcT, g.Npad, c->AxT, g.Spad, g.ldy, c->ybar,
+                                         c->colb, c->colm, ls.a2, ls.c2, p.p1_tiles_per_group,
+                                         g.Spad / P1_BN, g.N, c->pm, c->ps);
+  c->launches++;
+}
+
+cudaError_t launch_pass2_f32(srmra_ctx* c) {
+  static bool attr_done = false;
+  if (!attr_done) {
+    cudaError_t e = cudaFuncSetAttribute(k_p2_f32, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)P2_SMEM_BYTES);
+    if (e != cudaSuccess) return e;
+    attr_done = true;
+  }
+  const Geom& g = c->g;
+  const Plan& p = c->plan;
+  const LogitScalars ls = logit_scalars(g);
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)p.p2_gc, (unsigned)(g.Spad / P2_BS),
+                     (unsigned)(p.p2_nsplit * p.p2_chunk_groups));
+  cfg.blockDim = dim3(256, 1, 1);
+  cfg.dynamicSmemBytes = P2_SMEM_BYTES;
+  cfg.stream = c->stream;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = (unsigned)p.p2_gc;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  const int n_iblk2 = (int)(g.Npad / P2_BI);
+  cudaError_t e = cudaLaunchKernelEx(&cfg, k_p2_f32, (const float*)c->YcT, (const float*)c->Yc,
+                                     g.Npad, (const float*)c->AxT, g.Spad, g.ldy,
+                                     (const float*)c->ybar, (const float*)c->colb,
+                                     (const float*)c->colm, (const float*)c->lse2, ls.a2, ls.c2,
+                                     g.N, g.S, n_iblk2, p.p2_iblk_per_split, p.p2_gc,
+                                     p.p2_chunk_groups, c->Zp, c->cp, c->zbp);
+  c->launches++;
+  return e;
+}
+
+}  // namespace srmra

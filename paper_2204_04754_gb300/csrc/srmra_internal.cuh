@@ -1,0 +1,135 @@
+// Internal declarations of libsrmra: the context, device-buffer layout and the kernel
+// launchers shared by the host driver (api.cu) and the kernel files.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/srmra.h"
+
+namespace srmra {
+
+// Device status word bits (set by kernels, read by the host after a sync).
+enum : int {
+  STATUS_TIMEOUT = 1,   // a bounded mbarrier / flag wait gave up
+  STATUS_NUMERIC = 2,   // NaN / Inf in LL, x or rho
+};
+
+// Tile sizes of the float32 (CUDA-core) kernels.
+constexpr int P1_BM = 128;  // pass 1: observations per tile
+constexpr int P1_BN = 128;  // pass 1: shifts per tile
+constexpr int P2_BS = 64;   // pass 2: shifts per tile
+constexpr int P2_BI = 64;   // pass 2: observations per round
+constexpr int P2_BP = 256;  // pass 2: pixels of the M-step sum per CTA
+constexpr int NPAD = 128;   // observation padding (multiple of every i-tile)
+constexpr int SPAD = 256;   // shift padding (multiple of every s-tile)
+
+inline int64_t round_up(int64_t a, int64_t b) { return (a + b - 1) / b * b; }
+inline int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }
+
+// Geometry of one problem, shared by all kernels.
+struct Geom {
+  int L, K, l, l2;  // L_high, factor, L_low, L_low^2
+  int S;            // L^2 shifts
+  int Spad;         // S rounded up to SPAD
+  int ldy;          // pitch (pixels) of a centred observation row, l2 rounded up to 8
+  int64_t N;        // observations
+  int64_t Npad;     // N rounded up to NPAD
+  double sigma;
+};
+
+// Per-iteration scalars of the logit in base-2 units:
+//   logit2[i,s] = acc[i,s] * a2 + colb[s] - c2 * (ybar[i] - colm[s])^2
+// with acc = <y'_i, T'_s> (centred operands), a2 = log2(e)/sigma^2,
+// c2 = log2(e) * l^2 / (2 sigma^2), colb[s] = log2(e) (-nu'_r / (2 sigma^2) + log rho[s]),
+// colm[s] = m_r (mean of sub-image r(s)).
+struct LogitScalars {
+  float a2;
+  float c2;
+};
+
+struct Plan {
+  int p1_groups = 1;        // shift groups per observation tile in pass 1
+  int p1_tiles_per_group = 1;
+  int p2_gc = 1;            // cluster size (pixel chunks sharing one weight tile)
+  int p2_chunk_groups = 1;  // groups of gc chunks (each recomputes the logits)
+  int p2_nsplit = 1;        // observation ranges with separate M-step partial sums
+  int p2_iblk_per_split = 1;
+  int nparts_c = 1;         // number of partial c / zb slices
+  int nparts_z = 1;         // number of partial Z slices
+  int ll_blocks = 1;        // blocks of the lse-combine kernel
+};
+
+}  // namespace srmra
+
+struct srmra_ctx {
+  srmra::Geom g;
+  int prec = 0;
+  unsigned flags = 0;
+  cudaStream_t stream = nullptr;
+  int device = 0;
+  int num_sms = 0;
+  srmra::Plan plan;
+
+  // --- observations (fixed for the life of the context)
+  float* Yc = nullptr;     // [Npad][ldy]  centred observations y'_i = y_i - ybar_i (fp32)
+  float* YcT = nullptr;    // [ldy][Npad]  the same, pixel-major (fp32 kernels)
+  float* ybar = nullptr;   // [Npad]       mean of each observation
+  double* yy = nullptr;    // [Npad]       ||y'_i||^2
+
+  // --- estimate theta_t
+  float* x = nullptr;      // [L*L]
+  double* rho1 = nullptr;  // [L]
+  double* rho2 = nullptr;  // [L]
+  double sigma_bm = 1.0;
+  int32_t t = 0;
+
+  // --- per-iteration work buffers
+  double* sub = nullptr;   // [2*K*K]  m_r, nu'_r
+  float* colb = nullptr;   // [Spad]
+  float* colm = nullptr;   // [Spad]
+  float* AxT = nullptr;    // [ldy][Spad] centred templates, pixel-major (fp32 kernels)
+  float* pm = nullptr;     // [p1_groups][Npad] running max (base 2)
+  float* ps = nullptr;     // [p1_groups][Npad] running sum
+  float* lse2 = nullptr;   // [Npad] log2 sum_s 2^{logit2}
+  double* lse = nullptr;   // [Npad] per-observation log-likelihood (natural log)
+  double* llpart = nullptr;// [ll_blocks]
+  float* Zp = nullptr;     // [nparts_z][Spad][ldy] partial sum_i w y'_i
+  float* cp = nullptr;     // [nparts_c][Spad] partial sum_i w
+  float* zbp = nullptr;    // [nparts_c][Spad] partial sum_i w ybar_i
+  double* cfin = nullptr;  // [Spad] c_s of the last E-step
+  double* Ar = nullptr;    // [K*K] coverage per sub-image, then ZB per sub-image [K*K]
+  double* ll_hist = nullptr;  // [ll_cap]
+  int ll_cap = 0;
+  int* status = nullptr;   // device status word
+  bool have_estep = false;
+
+  int64_t launches = 0;
+  std::string err;
+  // per-phase timing (srmra_profile)
+  bool profiling = false;
+  struct Mark { int phase; cudaEvent_t a, b; };
+  std::vector<Mark> marks;
+  std::vector<cudaEvent_t> event_pool;
+  std::vector<void*> owned;  // every device buffer allocated for this context
+};
+
+namespace srmra {
+
+// ---- k_common.cu
+void launch_center_obs(srmra_ctx* c, const float* y_dev);
+void launch_prep_iter(srmra_ctx* c);           // sub-image stats, column terms, templates
+void launch_lse_combine(srmra_ctx* c, int groups);
+void launch_finalize(srmra_ctx* c, int ll_index);
+void launch_dct_denoise(srmra_ctx* c, double sigma_bm, double thr);
+LogitScalars logit_scalars(const Geom& g);
+
+// ---- k_simt.cu (float32 form)
+void plan_simt(srmra_ctx* c);
+void launch_pass1_f32(srmra_ctx* c);
+cudaError_t launch_pass2_f32(srmra_ctx* c);
+
+}  // namespace srmra

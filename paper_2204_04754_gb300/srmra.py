@@ -1,0 +1,270 @@
+"""Thin ctypes binding of libsrmra.so (C ABI in include/srmra.h).
+
+The functions ``srmra_create``, ``srmra_em_iter``, ... carry the C names and only
+marshal arguments; every step of the computation runs in the CUDA library.  The
+:class:`Solver` class is a small convenience wrapper over the same calls.
+
+The library is loaded on first use.  If it has not been built (``python -m
+paper_2204_04754_gb300.build``) a RuntimeError is raised; there is no fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from ctypes import (CFUNCTYPE, POINTER, Structure, byref, c_char_p, c_double, c_float,
+                    c_int32, c_int64, c_uint32, c_void_p)
+
+import numpy as np
+
+LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "libsrmra.so")
+
+SRMRA_OK, SRMRA_EINVAL, SRMRA_ENOMEM, SRMRA_ECUDA, SRMRA_ETIMEOUT, SRMRA_ENUMERIC, \
+    SRMRA_EBUSY = range(7)
+STATUS_NAMES = {0: "OK", 1: "EINVAL", 2: "ENOMEM", 3: "ECUDA", 4: "ETIMEOUT",
+                5: "ENUMERIC", 6: "EBUSY"}
+SRMRA_FP32, SRMRA_BF16, SRMRA_BF16X3 = 0, 1, 2
+PRECISIONS = {"fp32": SRMRA_FP32, "bf16": SRMRA_BF16, "bf16x3": SRMRA_BF16X3}
+SRMRA_FLAG_CHECK_NUMERIC = 1
+
+
+class srmra_params(Structure):
+    _fields_ = [("L_high", c_int32), ("K", c_int32), ("N", c_int64), ("sigma", c_double),
+                ("prec", c_int32), ("flags", c_uint32)]
+
+
+DENOISER_FN = CFUNCTYPE(c_int32, POINTER(c_float), c_int32, c_double, c_void_p, c_void_p)
+
+
+class SrmraError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {msg}")
+        self.status = status
+
+
+_lib = None
+
+
+def lib() -> ctypes.CDLL:
+    """Load libsrmra.so (once) and declare the C prototypes."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError(f"{LIB_PATH} is missing; build it with "
+                           "`python -m paper_2204_04754_gb300.build`")
+    L = ctypes.CDLL(LIB_PATH)
+    P = POINTER
+    sig = {
+        "srmra_create": (c_int32, [P(srmra_params), c_void_p, c_int32, c_void_p, c_void_p,
+                                   c_void_p, c_void_p, P(c_void_p)]),
+        "srmra_em_iter": (c_int32, [c_void_p, c_int32, c_void_p]),
+        "srmra_project": (c_int32, [c_void_p, c_double, c_void_p, c_void_p]),
+        "srmra_solve": (c_int32, [c_void_p, c_int32, c_int32, c_double, c_double, c_void_p,
+                                  c_void_p, c_void_p]),
+        "srmra_get_state": (c_int32, [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p,
+                                      c_void_p]),
+        "srmra_set_state": (c_int32, [c_void_p, c_void_p, c_void_p, c_void_p, c_double,
+                                      c_int32]),
+        "srmra_get_estep": (c_int32, [c_void_p, c_void_p, c_void_p]),
+        "srmra_launch_count": (c_int32, [c_void_p, P(c_int64)]),
+        "srmra_sync": (c_int32, [c_void_p]),
+        "srmra_profile": (c_int32, [c_void_p, c_int32]),
+        "srmra_profile_read": (c_int32, [c_void_p, c_void_p, c_void_p]),
+        "srmra_destroy": (None, [c_void_p]),
+        "srmra_last_error": (c_char_p, [c_void_p]),
+        "srmra_version": (c_char_p, []),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(L, name)
+        f.restype = res
+        f.argtypes = args
+    _lib = L
+    return L
+
+
+def _ptr(a) -> int | None:
+    """Address of a numpy array / torch tensor / None."""
+    if a is None:
+        return None
+    if isinstance(a, np.ndarray):
+        return a.ctypes.data
+    if hasattr(a, "data_ptr"):
+        return a.data_ptr()
+    raise TypeError(type(a))
+
+
+def _check(st: int, ctx=None):
+    if st != SRMRA_OK:
+        msg = lib().srmra_last_error(ctx)
+        raise SrmraError(st, msg.decode() if msg else "")
+
+
+# ----------------------------------------------------------------------------- C names
+
+def srmra_create(params: srmra_params, y, y_is_device: bool, x0=None, rho1_0=None,
+                 rho2_0=None, stream: int = 0) -> int:
+    ctx = c_void_p()
+    st = lib().srmra_create(byref(params), _ptr(y), int(bool(y_is_device)), _ptr(x0),
+                            _ptr(rho1_0), _ptr(rho2_0), c_void_p(stream or None), byref(ctx))
+    _check(st, None)
+    return ctx.value
+
+
+def srmra_em_iter(ctx: int, n_iters: int, loglik_out=None) -> None:
+    _check(lib().srmra_em_iter(ctx, n_iters, _ptr(loglik_out)), ctx)
+
+
+def srmra_project(ctx: int, sigma_bm: float, fn=None, user=None) -> None:
+    _check(lib().srmra_project(ctx, sigma_bm, fn, user), ctx)
+
+
+def srmra_solve(ctx: int, iters: int, F: int, sigma_bm1: float, decay: float,
+                fn=None, user=None, loglik_out=None) -> None:
+    _check(lib().srmra_solve(ctx, iters, F, sigma_bm1, decay, fn, user, _ptr(loglik_out)), ctx)
+
+
+def srmra_get_state(ctx: int, x=None, rho1=None, rho2=None):
+    sbm = c_double()
+    t = c_int32()
+    _check(lib().srmra_get_state(ctx, _ptr(x), _ptr(rho1), _ptr(rho2), byref(sbm), byref(t)),
+           ctx)
+    return sbm.value, t.value
+
+
+def srmra_set_state(ctx: int, x, rho1, rho2, sigma_bm: float, t: int) -> None:
+    _check(lib().srmra_set_state(ctx, _ptr(x), _ptr(rho1), _ptr(rho2), sigma_bm, t), ctx)
+
+
+def srmra_get_estep(ctx: int, lse=None, c=None) -> None:
+    _check(lib().srmra_get_estep(ctx, _ptr(lse), _ptr(c)), ctx)
+
+
+def srmra_launch_count(ctx: int) -> int:
+    n = c_int64()
+    _check(lib().srmra_launch_count(ctx, byref(n)), ctx)
+    return n.value
+
+
+PHASES = ["prep", "pass1", "combine", "pass2", "final", "denoise"]
+
+
+def srmra_profile(ctx: int, enable: bool) -> None:
+    _check(lib().srmra_profile(ctx, int(bool(enable))), ctx)
+
+
+def srmra_profile_read(ctx: int):
+    ms = np.zeros(len(PHASES))
+    n = np.zeros(len(PHASES), np.int64)
+    _check(lib().srmra_profile_read(ctx, ms.ctypes.data, n.ctypes.data), ctx)
+    return ms, n
+
+
+def srmra_sync(ctx: int) -> None:
+    _check(lib().srmra_sync(ctx), ctx)
+
+
+def srmra_destroy(ctx: int) -> None:
+    lib().srmra_destroy(ctx)
+
+
+def srmra_version() -> str:
+    return lib().srmra_version().decode()
+
+
+# ----------------------------------------------------------------------------- wrapper
+
+class Solver:
+    """One SR-MRA problem held on the GPU.
+
+    y: (N, l, l) float32 numpy array (host) or CUDA tensor (device, C-contiguous).
+    prec: 'fp32' | 'bf16' | 'bf16x3'.  stream: cudaStream_t as an int (0 = default).
+    """
+
+    def __init__(self, L: int, K: int, sigma: float, y, prec: str = "fp32", x0=None,
+                 rho1=None, rho2=None, stream: int = 0, flags: int = 0,
+                 y_on_device: bool | None = None):
+        if y_on_device is None:
+            y_on_device = bool(getattr(y, "is_cuda", False))
+        on_device = y_on_device
+        if isinstance(y, np.ndarray):
+            y = np.ascontiguousarray(y, dtype=np.float32)
+        self.L, self.K, self.N = int(L), int(K), int(y.shape[0])
+        self.l = self.L // self.K
+        p = srmra_params(self.L, self.K, self.N, float(sigma), PRECISIONS[prec], flags)
+        x0 = None if x0 is None else np.ascontiguousarray(x0, dtype=np.float32)
+        r1 = None if rho1 is None else np.ascontiguousarray(rho1, dtype=np.float64)
+        r2 = None if rho2 is None else np.ascontiguousarray(rho2, dtype=np.float64)
+        self._keep = (y,)
+        self.ctx = srmra_create(p, y, on_device, x0, r1, r2, stream)
+
+    def em_iter(self, n: int = 1, loglik: bool = True):
+        out = np.empty(max(n, 1)) if loglik else None
+        srmra_em_iter(self.ctx, n, out)
+        return None if out is None else out[:n]
+
+    def solve(self, iters: int, F: int, sigma_bm1: float = 1.0, decay: float = 2.0 ** -0.1,
+              denoiser=None, loglik: bool = True):
+        out = np.empty(max(iters, 1)) if loglik else None
+        fn = None
+        if denoiser is not None:
+            fn = DENOISER_FN(denoiser)
+            self._fn = fn
+        srmra_solve(self.ctx, iters, F, sigma_bm1, decay, fn, None, out)
+        return None if out is None else out[:iters]
+
+    def project(self, sigma_bm: float, denoiser=None):
+        fn = None
+        if denoiser is not None:
+            fn = DENOISER_FN(denoiser)
+            self._fn = fn
+        srmra_project(self.ctx, sigma_bm, fn, None)
+
+    def state(self):
+        x = np.empty((self.L, self.L), np.float32)
+        r1 = np.empty(self.L)
+        r2 = np.empty(self.L)
+        sbm, t = srmra_get_state(self.ctx, x, r1, r2)
+        return x, r1, r2, sbm, t
+
+    def set_state(self, x, rho1, rho2, sigma_bm: float, t: int):
+        srmra_set_state(self.ctx, np.ascontiguousarray(x, np.float32),
+                        np.ascontiguousarray(rho1, np.float64),
+                        np.ascontiguousarray(rho2, np.float64), sigma_bm, t)
+
+    def estep(self):
+        lse = np.empty(self.N)
+        c = np.empty(self.L * self.L)
+        srmra_get_estep(self.ctx, lse, c)
+        return lse, c
+
+    @property
+    def launches(self) -> int:
+        return srmra_launch_count(self.ctx)
+
+    def sync(self):
+        srmra_sync(self.ctx)
+
+    def profile(self, enable: bool = True):
+        srmra_profile(self.ctx, enable)
+
+    def profile_read(self):
+        """-> ({phase: ms}, {phase: launches}) accumulated since the last read."""
+        ms, n = srmra_profile_read(self.ctx)
+        return dict(zip(PHASES, ms.tolist())), dict(zip(PHASES, n.tolist()))
+
+    def close(self):
+        if getattr(self, "ctx", None):
+            srmra_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
