@@ -128,9 +128,17 @@ struct PhaseTimer {
 srmra_status run_iteration(srmra_ctx* c, int ll_index) {
   cudaError_t e = cudaSuccess;
   { PhaseTimer t(c, SRMRA_PHASE_PREP); launch_prep_iter(c); }
-  { PhaseTimer t(c, SRMRA_PHASE_PASS1); launch_pass1_f32(c); }
+  const bool tc = c->prec != SRMRA_FP32;
+  {
+    PhaseTimer t(c, SRMRA_PHASE_PASS1);
+    if (tc)
+      e = launch_pass1_tc(c);
+    else
+      launch_pass1_f32(c);
+  }
+  if (e != cudaSuccess) return cuda_fail(c, e, "pass 1 launch");
   { PhaseTimer t(c, SRMRA_PHASE_COMBINE); launch_lse_combine(c, c->plan.p1_groups); }
-  { PhaseTimer t(c, SRMRA_PHASE_PASS2); e = launch_pass2_f32(c); }
+  { PhaseTimer t(c, SRMRA_PHASE_PASS2); e = tc ? launch_pass2_tc(c) : launch_pass2_f32(c); }
   if (e != cudaSuccess) return cuda_fail(c, e, "pass 2 launch");
   { PhaseTimer t(c, SRMRA_PHASE_FINAL); launch_finalize(c, ll_index); }
   e = cudaGetLastError();
@@ -194,8 +202,8 @@ srmra_status srmra_create(const srmra_params* p, const float* y, int32_t y_is_de
   if (p->N < 1) return fail(nullptr, SRMRA_EINVAL, "need N >= 1");
   if (!(p->sigma > 0.0) || !std::isfinite(p->sigma))
     return fail(nullptr, SRMRA_EINVAL, "need sigma > 0");
-  if (p->prec != SRMRA_FP32)
-    return fail(nullptr, SRMRA_EINVAL, "precision form not available in this build");
+  if (p->prec != SRMRA_FP32 && p->prec != SRMRA_BF16 && p->prec != SRMRA_BF16X3)
+    return fail(nullptr, SRMRA_EINVAL, "unknown precision form");
 
   std::vector<double> r1, r2;
   {
@@ -228,12 +236,17 @@ srmra_status srmra_create(const srmra_params* p, const float* y, int32_t y_is_de
   g.S = g.L * g.L;
   g.Spad = (int)round_up(g.S, SPAD);
   g.ldy = (int)round_up(g.l2, 16);
+  g.ldk = (int)round_up(g.l2, 64);
   g.N = p->N;
   g.Npad = round_up(g.N, NPAD);
   g.sigma = p->sigma;
 
 
-  plan_simt(c);
+  const bool tc = c->prec != SRMRA_FP32;
+  if (tc)
+    plan_tc(c);
+  else
+    plan_simt(c);
   const Plan& pl = c->plan;
   Allocator A{c, 0, alloc_limit(), &c->owned};
   auto bail = [&](cudaError_t err, const char* what) {
@@ -247,7 +260,18 @@ srmra_status srmra_create(const srmra_params* p, const float* y, int32_t y_is_de
     if (e2 != cudaSuccess) return bail(e2, "allocate " #ptr); \
   } while (0)
   AL(c->Yc, g.Npad * g.ldy);
-  AL(c->YcT, g.Npad * g.ldy);
+  if (tc) {
+    AL(c->Yh, g.Npad * g.ldk);
+    AL(c->YTh, g.Npad * g.l2);
+    AL(c->Ah, (int64_t)g.Spad * g.ldk);
+    if (c->prec == SRMRA_BF16X3) {
+      AL(c->Yl, g.Npad * g.ldk);
+      AL(c->Al, (int64_t)g.Spad * g.ldk);
+    }
+  } else {
+    AL(c->YcT, g.Npad * g.ldy);
+    AL(c->AxT, (int64_t)g.ldy * g.Spad);
+  }
   AL(c->ybar, g.Npad);
   AL(c->yy, g.Npad);
   AL(c->x, g.S);
@@ -256,7 +280,6 @@ srmra_status srmra_create(const srmra_params* p, const float* y, int32_t y_is_de
   AL(c->sub, 2 * g.K * g.K);
   AL(c->colb, g.Spad);
   AL(c->colm, g.Spad);
-  AL(c->AxT, (int64_t)g.ldy * g.Spad);
   AL(c->pm, (int64_t)pl.p1_groups * g.Npad);
   AL(c->ps, (int64_t)pl.p1_groups * g.Npad);
   AL(c->lse2, g.Npad);
@@ -280,6 +303,13 @@ srmra_status srmra_create(const srmra_params* p, const float* y, int32_t y_is_de
     }
   }
   launch_center_obs(c, y_is_device ? y : ytmp);
+  if (tc) {
+    e = prep_obs_tc(c);
+    if (e != cudaSuccess) {
+      if (ytmp) cudaFree(ytmp);
+      return bail(e, "prepare tensor-core operands");
+    }
+  }
   if (x0) {
     e = cudaMemcpyAsync(c->x, x0, sizeof(float) * (size_t)g.S, cudaMemcpyHostToDevice,
                         c->stream);

@@ -327,6 +327,8 @@ void launch_prep_iter(srmra_ctx* c) {
     k_templates_T<<<grid, 256, 0, c->stream>>>(c->x, c->sub, g.L, g.K, g.l, g.S, g.Spad,
                                                 g.l2, c->AxT);
     c->launches++;
+  } else {
+    launch_templates_tc(c);
   }
 }
 

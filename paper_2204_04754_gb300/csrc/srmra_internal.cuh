@@ -2,6 +2,8 @@
 // launchers shared by the host driver (api.cu) and the kernel files.
 #pragma once
 
+#include <cuda.h>
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -35,7 +37,8 @@ struct Geom {
   int L, K, l, l2;  // L_high, factor, L_low, L_low^2
   int S;            // L^2 shifts
   int Spad;         // S rounded up to SPAD
-  int ldy;          // pitch (pixels) of a centred observation row, l2 rounded up to 8
+  int ldy;          // pitch (pixels) of a centred observation row, l2 rounded up to 16
+  int ldk;          // pitch of the bf16 operand rows (tensor-core form), l2 rounded up to 64
   int64_t N;        // observations
   int64_t Npad;     // N rounded up to NPAD
   double sigma;
@@ -79,6 +82,12 @@ struct srmra_ctx {
   float* YcT = nullptr;    // [ldy][Npad]  the same, pixel-major (fp32 kernels)
   float* ybar = nullptr;   // [Npad]       mean of each observation
   double* yy = nullptr;    // [Npad]       ||y'_i||^2
+  __nv_bfloat16* Yh = nullptr;   // [Npad][ldk] bf16(y')            (tensor-core form)
+  __nv_bfloat16* Yl = nullptr;   // [Npad][ldk] bf16(y' - Yh)       (split form only)
+  __nv_bfloat16* YTh = nullptr;  // [l2][Npad]  Yh transposed (M-step operand)
+  __nv_bfloat16* Ah = nullptr;   // [Spad][ldk] centred templates, bf16 hi
+  __nv_bfloat16* Al = nullptr;   // [Spad][ldk] bf16 lo (split form only)
+  CUtensorMap tmY128, tmYl128, tmYT, tmA128, tmAl128, tmA256, tmAl256;
 
   // --- estimate theta_t
   float* x = nullptr;      // [L*L]
@@ -126,6 +135,13 @@ void launch_lse_combine(srmra_ctx* c, int groups);
 void launch_finalize(srmra_ctx* c, int ll_index);
 void launch_dct_denoise(srmra_ctx* c, double sigma_bm, double thr);
 LogitScalars logit_scalars(const Geom& g);
+
+// ---- k_tc.cu (tensor-core forms)
+void plan_tc(srmra_ctx* c);
+cudaError_t prep_obs_tc(srmra_ctx* c);
+void launch_templates_tc(srmra_ctx* c);
+cudaError_t launch_pass1_tc(srmra_ctx* c);
+cudaError_t launch_pass2_tc(srmra_ctx* c);
 
 // ---- k_simt.cu (float32 form)
 void plan_simt(srmra_ctx* c);

@@ -1,0 +1,117 @@
+"""GPU parity of the tensor-core forms (bf16 and split-bf16 'bf16x3') against the
+FP64 oracle, through the C ABI.  The mixed form targets a relative error of 1e-4 on
+x and rho per iteration; plain bf16 is reported against a looser bound (its logit
+error is O(1e-3 * ||y|| ||x|| / sigma^2), which moves near-tied posteriors)."""
+import os
+
+import numpy as np
+import pytest
+
+from oracle import fft_oracle as FO
+from oracle import srmra_oracle as O
+from paper_2204_04754_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+TOL = {"bf16x3": 1e-4, "bf16": 2e-2}
+
+
+def rel(a, b):
+    a = np.asarray(a, np.float64)
+    b = np.asarray(b, np.float64)
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+@pytest.fixture(scope="module")
+def S():
+    from paper_2204_04754_gb300 import srmra
+    if not os.path.exists(srmra.LIB_PATH):
+        from paper_2204_04754_gb300 import build
+        build.build()
+    srmra.lib()
+    return srmra
+
+
+def one_step(S, p, prec, steps=2, oracle="dense"):
+    yscale = (p.y.astype(np.float64) ** 2).sum(axis=(1, 2)) / (2 * p.sigma ** 2)
+    s = S.Solver(p.L, p.K, p.sigma, p.y, prec=prec, x0=p.x0, rho1=p.rho1_0, rho2=p.rho2_0)
+    worst = dict(x=0.0, rho=0.0, ll=0.0, lse=0.0)
+    for _ in range(steps):
+        x, r1, r2, _, _ = s.state()
+        ll = s.em_iter(1)[0]
+        fn = O.em_iter if oracle == "dense" else FO.em_iter_fft
+        xo, r1o, r2o, llo, aux = fn(p.y, x, r1, r2, p.sigma, p.K)
+        xg, r1g, r2g, _, _ = s.state()
+        lse, c = s.estep()
+        worst["x"] = max(worst["x"], rel(xg, xo))
+        worst["rho"] = max(worst["rho"], rel(r1g, r1o), rel(r2g, r2o))
+        worst["ll"] = max(worst["ll"], abs(ll - llo) / (abs(llo) + yscale.sum()))
+        worst["lse"] = max(worst["lse"], float(np.max(np.abs(lse - aux["lse"]) /
+                                                      (1.0 + np.abs(aux["lse"]) + yscale))))
+        assert abs(r1g.sum() - 1) < 1e-12 and np.all(np.isfinite(xg))
+    s.close()
+    print(prec, p.L, p.K, p.N, p.sigma, worst)
+    return worst
+
+
+CASES = [
+    (16, 2, 500, 0.1),
+    (12, 3, 333, 0.4),     # ragged shift tile, l^2 = 16
+    (12, 2, 257, 0.3),     # l^2 = 36
+    (8, 1, 130, 0.5),      # K = 1
+    (20, 4, 129, 0.6),     # l = 5
+    (6, 6, 40, 0.3),       # l = 1
+    (64, 2, 700, 0.3),     # l = 32: four pixel chunks
+    (48, 1, 300, 0.8),     # l^2 = 2304
+    (32, 2, 1000, 1.0),    # low SNR
+]
+
+
+@pytest.mark.parametrize("L,K,N,sigma", CASES)
+def test_em_step_parity_bf16x3(S, L, K, N, sigma):
+    p = synth.make_problem(L, K, N, sigma, seed=synth.seed_for(3, L * 7 + K))
+    w = one_step(S, p, "bf16x3")
+    tol = TOL["bf16x3"]
+    assert w["x"] < tol and w["rho"] < tol and w["ll"] < tol and w["lse"] < tol
+
+
+@pytest.mark.parametrize("L,K,N,sigma", [(16, 2, 500, 0.5), (64, 2, 700, 1.0),
+                                         (12, 3, 333, 0.8)])
+def test_em_step_bf16(S, L, K, N, sigma):
+    p = synth.make_problem(L, K, N, sigma, seed=synth.seed_for(3, L * 7 + K))
+    w = one_step(S, p, "bf16")
+    tol = TOL["bf16"]
+    assert w["x"] < tol and w["rho"] < tol
+
+
+def test_precision_workload_subsample_bf16x3(S):
+    """L=96, K=3, sigma=0.2 (the precision workload's shapes) on 6000 observations:
+    one iteration element-wise against the FFT oracle."""
+    p = synth.workload_problem("precision_L96_K3_N5e4_s0.2", N=6000)
+    w = one_step(S, p, "bf16x3", steps=1, oracle="fft")
+    assert w["x"] < TOL["bf16x3"] and w["rho"] < TOL["bf16x3"] and w["lse"] < TOL["bf16x3"]
+
+
+@pytest.mark.parametrize("name", ["precision_L96_K3_N5e4_s0.2", "precision_L96_K3_N5e4_s1.0"])
+def test_precision_workload_full_size_sampled(S, name):
+    """Full size (N = 5e4): the per-observation log-likelihood lse_i of a sample of
+    observations against the oracle's direct formula, plus sum_i lse_i = LL and
+    rho on the simplex."""
+    p = synth.workload_problem(name)
+    s = S.Solver(p.L, p.K, p.sigma, p.y, prec="bf16x3", x0=p.x0, rho1=p.rho1_0,
+                 rho2=p.rho2_0)
+    ll = s.em_iter(1)[0]
+    lse, c = s.estep()
+    x, r1, r2, _, _ = s.state()
+    s.close()
+    rng = np.random.default_rng(0)
+    idx = np.sort(rng.choice(p.N, size=64, replace=False))
+    _, lse_o, _ = O.estep(p.y[idx], p.x0, p.rho1_0, p.rho2_0, p.sigma, p.K)
+    yscale = (p.y[idx].astype(np.float64) ** 2).sum(axis=(1, 2)) / (2 * p.sigma ** 2)
+    err = np.max(np.abs(lse[idx] - lse_o) / (1 + np.abs(lse_o) + yscale))
+    print(name, "sampled lse err", err)
+    assert err < 1e-4
+    assert abs(lse.sum() - ll) < 1e-9 * abs(ll)
+    assert abs(r1.sum() - 1) < 1e-12 and abs(r2.sum() - 1) < 1e-12
+    assert abs(c.sum() - p.N) < 1e-3 * p.N
+    assert np.all(np.isfinite(x))
