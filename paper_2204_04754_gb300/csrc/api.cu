@@ -262,7 +262,7 @@ srmra_status srmra_create(const srmra_params* p, const float* y, int32_t y_is_de
   AL(c->Yc, g.Npad * g.ldy);
   if (tc) {
     AL(c->Yh, g.Npad * g.ldk);
-    AL(c->YTh, g.Npad * g.l2);
+    AL(c->YTf, g.Npad * g.l2);
     AL(c->Ah, (int64_t)g.Spad * g.ldk);
     if (c->prec == SRMRA_BF16X3) {
       AL(c->Yl, g.Npad * g.ldk);

@@ -173,57 +173,79 @@ __global__ void __launch_bounds__(256) k_lse_combine(
   if (threadIdx.x == 0) llpart[blockIdx.x] = tot;
 }
 
-// M-step totals (single block, fixed-order float64 reductions):
-//   c_s = sum of the partial weight sums, zb_s likewise;
-//   rho (Eq. rho_EM): joint c_s / sum c, marginals rho1, rho2;
-//   coverage A_r = sum_t c_{(r,t)} and ZB_r = sum_t zb_{(r,t)} per sub-image;
+// c_s = sum of the partial weight sums over the observation ranges, zb_s likewise
+// (float64, fixed order).
+__global__ void k_fin_sums(const float* __restrict__ cp, const float* __restrict__ zbp,
+                           int nparts, int Spad, int S, double* __restrict__ cfin) {
+  const int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= S) return;
+  double c = 0.0, z = 0.0;
+  for (int p = 0; p < nparts; ++p) {
+    c += (double)cp[(int64_t)p * Spad + s];
+    z += (double)zbp[(int64_t)p * Spad + s];
+  }
+  cfin[s] = c;
+  cfin[Spad + s] = z;
+}
+
+__device__ __forceinline__ double warp_sum_f64(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// M-step totals (one block, warp-level float64 reductions in a fixed order):
+//   rho (Eq. rho_EM): joint c_s / sum c, marginals rho1 (rows), rho2 (columns);
+//   coverage A_r = sum_t c_{(r,t)} and ZB_r = sum_t zb_{(r,t)} per sub-image r;
 //   LL(theta_t) = sum of the lse-combine block partials.
 __global__ void __launch_bounds__(1024) k_fin_counts(
-    const float* __restrict__ cp, const float* __restrict__ zbp, int nparts, int Spad, int S,
-    int L, int K, int l, const double* __restrict__ llpart, int ll_blocks,
-    double* __restrict__ rho1, double* __restrict__ rho2, double* __restrict__ Ar,
-    double* __restrict__ cfin, double* __restrict__ ll_out, int* __restrict__ status) {
+    const double* __restrict__ cfin, int Spad, int S, int L, int K, int l,
+    const double* __restrict__ llpart, int ll_blocks, double* __restrict__ rho1,
+    double* __restrict__ rho2, double* __restrict__ Ar, double* __restrict__ ll_out,
+    int* __restrict__ status) {
   __shared__ double red[1024];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   double loc = 0.0;
-  for (int s = threadIdx.x; s < S; s += 1024) {
-    double c = 0.0, z = 0.0;
-    for (int p = 0; p < nparts; ++p) {
-      c += (double)cp[(int64_t)p * Spad + s];
-      z += (double)zbp[(int64_t)p * Spad + s];
-    }
-    cfin[s] = c;
-    cfin[Spad + s] = z;
-    loc += c;
-  }
-  const double ctot = block_sum_f64<1024>(loc, red);  // also orders the cfin writes
-  for (int j = threadIdx.x; j < 2 * L; j += 1024) {
+  for (int s = threadIdx.x; s < S; s += 1024) loc += cfin[s];
+  const double ctot = block_sum_f64<1024>(loc, red);
+  for (int j = warp; j < 2 * L; j += 32) {  // one warp per row (rho1) / column (rho2)
     double acc = 0.0;
-    if (j < L) {
-      for (int s2 = 0; s2 < L; ++s2) acc += cfin[j * L + s2];
-      rho1[j] = acc / ctot;
-    } else {
-      const int s2 = j - L;
-      for (int s1 = 0; s1 < L; ++s1) acc += cfin[s1 * L + s2];
-      rho2[s2] = acc / ctot;
+    if (j < L)
+      for (int k = lane; k < L; k += 32) acc += cfin[j * L + k];
+    else
+      for (int k = lane; k < L; k += 32) acc += cfin[k * L + (j - L)];
+    acc = warp_sum_f64(acc);
+    if (lane == 0) {
+      if (j < L)
+        rho1[j] = acc / ctot;
+      else
+        rho2[j - L] = acc / ctot;
     }
   }
   const int l2 = l * l;
-  for (int r = threadIdx.x; r < K * K; r += 1024) {
+  for (int r = warp; r < K * K; r += 32) {  // one warp per sub-image
     const int r1 = r / K, r2 = r % K;
     double a = 0.0, z = 0.0;
-    for (int t = 0; t < l2; ++t) {
+    for (int t = lane; t < l2; t += 32) {
       const int s1 = mod_pos((t / l) * K - r1, L), s2 = mod_pos((t % l) * K - r2, L);
       a += cfin[s1 * L + s2];
       z += cfin[Spad + s1 * L + s2];
     }
-    Ar[r] = a;
-    Ar[K * K + r] = z;
+    a = warp_sum_f64(a);
+    z = warp_sum_f64(z);
+    if (lane == 0) {
+      Ar[r] = a;
+      Ar[K * K + r] = z;
+    }
   }
-  if (threadIdx.x == 0) {
+  if (warp == 0) {
     double ll = 0.0;
-    for (int b = 0; b < ll_blocks; ++b) ll += llpart[b];
-    *ll_out = ll;
-    if (!isfinite(ll) || !(ctot > 0.0) || !isfinite(ctot)) atomicOr(status, STATUS_NUMERIC);
+    for (int b = lane; b < ll_blocks; b += 32) ll += llpart[b];
+    ll = warp_sum_f64(ll);
+    if (lane == 0) {
+      *ll_out = ll;
+      if (!isfinite(ll) || !(ctot > 0.0) || !isfinite(ctot)) atomicOr(status, STATUS_NUMERIC);
+    }
   }
 }
 
@@ -294,7 +316,21 @@ __global__ void __launch_bounds__(64) k_dct8(float* __restrict__ x, int L, doubl
   *px = (float)o;
 }
 
+// out = sum_{k<n} in[k] in float64, one warp, fixed order.
+__global__ void k_sum_f64(const double* __restrict__ in, int n, double* __restrict__ out) {
+  double v = 0.0;
+  for (int k = threadIdx.x; k < n; k += 32) v += in[k];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  if (threadIdx.x == 0) *out = v;
+}
+
 }  // namespace
+
+cudaError_t launch_sum_f64(const double* in, int n, double* out, cudaStream_t stream) {
+  k_sum_f64<<<1, 32, 0, stream>>>(in, n, out);
+  return cudaGetLastError();
+}
 
 LogitScalars logit_scalars(const Geom& g) {
   LogitScalars s;
@@ -342,14 +378,16 @@ void launch_lse_combine(srmra_ctx* c, int groups) {
 
 void launch_finalize(srmra_ctx* c, int ll_index) {
   const Geom& g = c->g;
-  k_fin_counts<<<1, 1024, 0, c->stream>>>(c->cp, c->zbp, c->plan.nparts_c, g.Spad, g.S, g.L,
-                                          g.K, g.l, c->llpart, c->plan.ll_blocks, c->rho1,
-                                          c->rho2, c->Ar, c->cfin, c->ll_hist + ll_index,
-                                          c->status);
+  k_fin_sums<<<(unsigned)ceil_div(g.S, 256), 256, 0, c->stream>>>(c->cp, c->zbp,
+                                                                  c->plan.nparts_c, g.Spad,
+                                                                  g.S, c->cfin);
+  k_fin_counts<<<1, 1024, 0, c->stream>>>(c->cfin, g.Spad, g.S, g.L, g.K, g.l, c->llpart,
+                                          c->plan.ll_blocks, c->rho1, c->rho2, c->Ar,
+                                          c->ll_hist + ll_index, c->status);
   const int warps = g.L * g.L;
   k_fin_x<<<(unsigned)ceil_div(warps, 8), 256, 0, c->stream>>>(
       c->Zp, c->plan.nparts_z, g.Spad, g.ldy, g.L, g.K, g.l, c->Ar, c->x, c->status);
-  c->launches += 2;
+  c->launches += 3;
 }
 
 void launch_dct_denoise(srmra_ctx* c, double sigma_bm, double thr) {

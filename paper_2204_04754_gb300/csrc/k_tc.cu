@@ -8,10 +8,14 @@
 // Pass 1: D[i, s] = Y'[i, :] . T'[s, :] for a 128-observation x 256-shift tile in TMEM,
 //   the epilogue warps keep the running (max, sum) of 2^logit2 per observation.
 // Pass 2: D[s, i] = T'[s, :] . Y'[i, :] for 128 shifts x 128 observations, the epilogue
-//   turns it into weights w = 2^(logit2 - lse2[i]) (bf16, written to shared memory in
-//   the layout tcgen05 reads), and a second MMA accumulates Z'[s, p] += sum_i w[s,i]
+//   turns it into weights w = 2^(logit2 - lse2[i]), written to shared memory in the
+//   layout tcgen05 reads, and a second MMA accumulates Z'[s, p] += sum_i w[s,i]
 //   Y'^T[p, i] for a 256-pixel chunk in TMEM (Eq. x_EM); c[s] = sum_i w[s,i] and
-//   zb[s] = sum_i w[s,i] ybar_i use the same bf16-rounded weights (Eq. rho_EM).
+//   zb[s] = sum_i w[s,i] ybar_i use the same rounded weights (Eq. rho_EM).  This second
+//   contraction runs on fp16 operands (same instruction kind and rate as bf16, 8x finer
+//   rounding): the weights are scaled by 2^12 before rounding, which keeps weights down
+//   to ~1e-8 out of the fp16 subnormal range, and the scale is removed exactly
+//   afterwards.
 //
 // Every CTA has three roles: warp 0 issues TMA loads into a ring of 32 KB shared-memory
 // slots, warp 1 issues tcgen05.mma (one thread) and owns the TMEM allocation, warps 2-5
@@ -33,6 +37,8 @@ constexpr int SLOT = 32768;
 constexpr int P1_SLOTS = 6;
 constexpr int P2_SLOTS = 5;
 constexpr int TC_THREADS = 192;
+constexpr float W_SCALE = 4096.f;        // 2^12, weights scaled before fp16 rounding
+constexpr float W_UNSCALE = 1.f / 4096.f;
 
 struct TcP1Args {
   int nk;         // 64-wide k-blocks of the contraction over pixels
@@ -384,7 +390,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
   } else if (warp == 1) {
     if (lane == 0) {
       constexpr uint32_t idS = idesc_bf16_f32(128, 128);
-      constexpr uint32_t idZ = idesc_bf16_f32(128, 256);
+      constexpr uint32_t idZ = idesc_f16_f32(128, 256);
       uint32_t it = 0, sc = 0, pz = 0, uc = 0;
       bool ok = true;
       auto wait_slot = [&]() -> uint8_t* {
@@ -519,13 +525,12 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
               const float ybi = a.ybar[i];
               const float dd = ybi - cm;
               const float val = fmaf(v[e + h], a.a2, cb - a.lse2[i]) - a.c2 * dd * dd;
-              const float w = (i < a.N) ? exp2f(val) : 0.f;
-              const __nv_bfloat16 wb = __float2bfloat16_rn(w);
-              w2[h] = __bfloat162float(wb);
+              const float w = (i < a.N) ? exp2f(val) * W_SCALE : 0.f;
+              w2[h] = __half2float(__float2half_rn(w));
               cacc += w2[h];
               zacc = fmaf(w2[h], ybi, zacc);
             }
-            const __nv_bfloat162 pr = __floats2bfloat162_rn(w2[0], w2[1]);
+            const __half2 pr = __floats2half2_rn(w2[0], w2[1]);
             packed[e >> 1] = *reinterpret_cast<const uint32_t*>(&pr);
           }
 #pragma unroll
@@ -559,15 +564,16 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
 #pragma unroll
           for (int e = 0; e < 32; e += 4)
             if (p0 + e < a.ldy)
-              *reinterpret_cast<float4*>(zrow + p0 + e) = make_float4(v[e], v[e + 1], v[e + 2],
-                                                                      v[e + 3]);
+              *reinterpret_cast<float4*>(zrow + p0 + e) =
+                  make_float4(v[e] * W_UNSCALE, v[e + 1] * W_UNSCALE, v[e + 2] * W_UNSCALE,
+                              v[e + 3] * W_UNSCALE);
         }
       }
       tc_fence_before();
       mbar_arrive(zempty);
       if (chunk == 0) {
-        a.cp[(int64_t)split * a.Spad + s] = cacc;
-        a.zbp[(int64_t)split * a.Spad + s] = zacc;
+        a.cp[(int64_t)split * a.Spad + s] = cacc * W_UNSCALE;
+        a.zbp[(int64_t)split * a.Spad + s] = zacc * W_UNSCALE;
       }
       ++uc;
     }
@@ -598,22 +604,22 @@ __global__ void k_split_obs(const float* __restrict__ Yc, int ldy, int l2, int64
   if (Yl) Yl[idx] = __float2bfloat16_rn(v - __bfloat162float(h));
 }
 
-// YT[p][i] = Yh[i][p] for p < l2 (bf16, 32x32 tiles).
-__global__ void k_transpose_bf16(const __nv_bfloat16* __restrict__ in, int64_t R, int ld_in,
-                                 int C, __nv_bfloat16* __restrict__ out) {
-  __shared__ __nv_bfloat16 tile[32][34];
+// YT[p][i] = fp16(y'_i[p]) for p < l2 (32x32 tiles): the M-step operand.
+__global__ void k_transpose_f16(const float* __restrict__ in, int64_t R, int ld_in, int C,
+                                __half* __restrict__ out) {
+  __shared__ float tile[32][33];
   const int64_t r0 = (int64_t)blockIdx.y * 32;
   const int c0 = blockIdx.x * 32;
   for (int k = threadIdx.y; k < 32; k += 8) {
     const int64_t r = r0 + k;
     const int c = c0 + threadIdx.x;
-    tile[k][threadIdx.x] = (r < R && c < C) ? in[r * ld_in + c] : __float2bfloat16_rn(0.f);
+    tile[k][threadIdx.x] = (r < R && c < C) ? in[r * ld_in + c] : 0.f;
   }
   __syncthreads();
   for (int k = threadIdx.y; k < 32; k += 8) {
     const int c = c0 + k;
     const int64_t r = r0 + threadIdx.x;
-    if (c < C && r < R) out[(int64_t)c * R + r] = tile[threadIdx.x][k];
+    if (c < C && r < R) out[(int64_t)c * R + r] = __float2half_rn(tile[threadIdx.x][k]);
   }
 }
 
@@ -656,17 +662,18 @@ PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
   return fn;
 }
 
-// 2D bf16 tensor map with 128-byte swizzle: `rows` rows of `inner` elements, row pitch
+// 2D 16-bit (bf16 or fp16) tensor map with 128-byte swizzle: `rows` rows of `inner` elements, row pitch
 // `pitch` elements, box of 64 x box_rows.
 bool make_map(CUtensorMap* m, const void* base, uint64_t inner, uint64_t rows, uint64_t pitch,
-              uint32_t box_rows) {
+              uint32_t box_rows,
+              CUtensorMapDataType dt = CU_TENSOR_MAP_DATA_TYPE_BFLOAT16) {
   auto enc = encode_fn();
   if (!enc) return false;
   cuuint64_t dims[2] = {inner, rows};
   cuuint64_t strides[1] = {pitch * 2};
   cuuint32_t box[2] = {64, box_rows};
   cuuint32_t es[2] = {1, 1};
-  return enc(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(base), dims, strides, box,
+  return enc(m, dt, 2, const_cast<void*>(base), dims, strides, box,
              es, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
              CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
@@ -712,13 +719,14 @@ cudaError_t prep_obs_tc(srmra_ctx* c) {
   k_split_obs<<<(unsigned)ceil_div(n, 256), 256, 0, c->stream>>>(
       c->Yc, g.ldy, g.l2, g.Npad, g.ldk, c->Yh, c->prec == SRMRA_BF16X3 ? c->Yl : nullptr);
   dim3 grid((unsigned)ceil_div(g.l2, 32), (unsigned)ceil_div(g.Npad, 32));
-  k_transpose_bf16<<<grid, dim3(32, 8), 0, c->stream>>>(c->Yh, g.Npad, g.ldk, g.l2, c->YTh);
+  k_transpose_f16<<<grid, dim3(32, 8), 0, c->stream>>>(c->Yc, g.Npad, g.ldy, g.l2, c->YTf);
   c->launches += 2;
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   // tensor maps over the fixed operands
   bool ok = make_map(&c->tmY128, c->Yh, g.ldk, g.Npad, g.ldk, 128) &&
-            make_map(&c->tmYT, c->YTh, g.Npad, g.l2, g.Npad, 256) &&
+            make_map(&c->tmYT, c->YTf, g.Npad, g.l2, g.Npad, 256,
+                     CU_TENSOR_MAP_DATA_TYPE_FLOAT16) &&
             make_map(&c->tmA128, c->Ah, g.ldk, g.Spad, g.ldk, 128) &&
             make_map(&c->tmA256, c->Ah, g.ldk, g.Spad, g.ldk, 256);
   if (ok && c->prec == SRMRA_BF16X3)

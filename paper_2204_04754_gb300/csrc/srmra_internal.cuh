@@ -4,6 +4,7 @@
 
 #include <cuda.h>
 #include <cuda_bf16.h>
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -84,7 +85,7 @@ struct srmra_ctx {
   double* yy = nullptr;    // [Npad]       ||y'_i||^2
   __nv_bfloat16* Yh = nullptr;   // [Npad][ldk] bf16(y')            (tensor-core form)
   __nv_bfloat16* Yl = nullptr;   // [Npad][ldk] bf16(y' - Yh)       (split form only)
-  __nv_bfloat16* YTh = nullptr;  // [l2][Npad]  Yh transposed (M-step operand)
+  __half* YTf = nullptr;         // [l2][Npad]  fp16(y') pixel-major (M-step operand)
   __nv_bfloat16* Ah = nullptr;   // [Spad][ldk] centred templates, bf16 hi
   __nv_bfloat16* Al = nullptr;   // [Spad][ldk] bf16 lo (split form only)
   CUtensorMap tmY128, tmYl128, tmYT, tmA128, tmAl128, tmA256, tmAl256;
@@ -135,6 +136,7 @@ void launch_lse_combine(srmra_ctx* c, int groups);
 void launch_finalize(srmra_ctx* c, int ll_index);
 void launch_dct_denoise(srmra_ctx* c, double sigma_bm, double thr);
 LogitScalars logit_scalars(const Geom& g);
+cudaError_t launch_sum_f64(const double* in, int n, double* out, cudaStream_t stream);
 
 // ---- k_tc.cu (tensor-core forms)
 void plan_tc(srmra_ctx* c);
