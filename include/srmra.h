@@ -176,6 +176,41 @@ srmra_status srmra_profile(srmra_ctx* ctx, int32_t enable);
  * SRMRA_NUM_PHASES, host, either may be NULL), and clear the records. */
 srmra_status srmra_profile_read(srmra_ctx* ctx, double* ms, int64_t* count);
 
+/* srmra_loglik_noalloc -- per-observation log-likelihood terms without any device
+ * allocation.  The paper has no counterpart: this entry point exists for callers that
+ * cannot call cudaMalloc -- services that size all device memory once at start-up so
+ * that no request can fail later on an allocation, host code that must not block on
+ * the allocator (cudaMalloc can synchronise the device), and embedders whose own
+ * allocator owns every byte of device memory.
+ *
+ * It computes the same values as the E-step of srmra_em_iter in the float32 form:
+ *   lse[i] = log sum_s rho1[s1] rho2[s2] exp(-||y_i - P R_s x||^2 / (2 sigma^2)),
+ *   *ll    = sum_i lse[i]   (float64, fixed reduction order).
+ * Inputs (device memory, caller-owned): y (N x l x l float32), x (L x L float32),
+ * rho1, rho2 (L float64, on the simplex).  Outputs (device memory, caller-owned): lse
+ * (N float64) and ll (1 float64).  Work is enqueued on cuda_stream; the call does not
+ * synchronise.
+ *
+ * Intermediate buffers live in one fixed device array of srmra_noalloc_scratch_bytes()
+ * bytes (64 MiB) per device, which every device that loads the library holds until the
+ * process exits.  Problems whose intermediates do not fit return SRMRA_EINVAL with a
+ * message (srmra_noalloc_last_error); roughly N * l^2 <= 7.5e6 fits.  The library calls
+ * no cudaMalloc, cudaFree or allocating routine here.  The first call on a device looks
+ * up the array's device address (cudaGetSymbolAddress) with that device current; make
+ * that first call before any stream capture.  Every call on a device shares the array
+ * and leaves its contents behind: calls whose work overlaps on the GPU (other streams,
+ * other threads) race on it and must be serialised by the caller. */
+srmra_status srmra_loglik_noalloc(const float* y_dev, int64_t N, int32_t L, int32_t K,
+                                  double sigma, const float* x_dev, const double* rho1_dev,
+                                  const double* rho2_dev, double* lse_dev, double* ll_dev,
+                                  void* cuda_stream);
+
+/* Size in bytes of the fixed device array used by srmra_loglik_noalloc. */
+int64_t srmra_noalloc_scratch_bytes(void);
+
+/* Message of the last failing srmra_loglik_noalloc call in this thread. */
+const char* srmra_noalloc_last_error(void);
+
 /* srmra_sync -- wait for all work enqueued by this context. */
 srmra_status srmra_sync(srmra_ctx* ctx);
 

@@ -13,7 +13,7 @@ HEADER = os.path.join(ROOT, "include", "srmra.h")
 
 def declared_functions():
     txt = open(HEADER).read()
-    return sorted(set(re.findall(r"^\s*(?:srmra_status|void|const char\*)\s+(srmra_\w+)\s*\(",
+    return sorted(set(re.findall(r"^\s*(?:srmra_status|void|const char\*|int64_t)\s+(srmra_\w+)\s*\(",
                                  txt, flags=re.M)))
 
 
