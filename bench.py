@@ -64,17 +64,25 @@ def fp32_peak_tflops(sm_mhz: float) -> float:
     return NUM_SMS * FP32_LANES_PER_SM * 2 * sm_mhz * 1e6 / 1e12
 
 
-def traffic_from_profiles(kernel: str, workload: str):
-    """DRAM bytes per launch recorded from an ncu capture in profiles/ (or None).
-    Lines of the form: `traffic <kernel> <workload> <bytes_per_launch>`."""
+KERNEL_SOURCE = {"fp32": "k_simt.cu", "bf16": "k_tc.cu", "bf16x3": "k_tc.cu"}
+
+
+def traffic_from_profiles(kernel: str, workload: str, prec: str):
+    """DRAM bytes per launch recorded from an ncu capture in profiles/traffic.txt, or
+    None.  Lines: `traffic <kernel> <workload> <bytes_per_launch> <source sha1 prefix>`;
+    a line counts only while the kernel's source file still has that hash."""
+    import hashlib
     path = os.path.join(ROOT, "profiles", "traffic.txt")
-    if not os.path.exists(path):
+    src = os.path.join(ROOT, "paper_2204_04754_gb300", "csrc", KERNEL_SOURCE[prec])
+    if not os.path.exists(path) or not os.path.exists(src):
         return None
+    with open(src, "rb") as f:
+        digest = hashlib.sha1(f.read()).hexdigest()
     with open(path) as f:
         for line in f:
             parts = line.split()
-            if len(parts) == 4 and parts[0] == "traffic" and parts[1] == kernel \
-                    and parts[2] == workload:
+            if len(parts) == 5 and parts[0] == "traffic" and parts[1] == kernel \
+                    and parts[2] == workload and digest.startswith(parts[4]):
                 return float(parts[3])
     return None
 
@@ -281,7 +289,7 @@ def main():
     kern = {"pass1": f"k_p1_{prec}", "pass2": f"k_p2_{prec}"}[dom]
     roof = {"bound": bound, "kernel": kern, "achieved": achieved, "peak": peak,
             "unit": "TFLOP/s", "frac": achieved / peak,
-            "traffic": traffic_from_profiles(kern, args.workload),
+            "traffic": traffic_from_profiles(kern, args.workload, prec),
             "algorithmic_flops_per_launch": per_pair_flops * pairs_per_step,
             "avg_launch_ms": avg_launch_s * 1e3, "peak_source": peak_note}
 
