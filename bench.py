@@ -42,6 +42,11 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--requests", type=int, default=12, help="serve: trace length")
+    ap.add_argument("--serve-slots", type=int, default=16)
+    ap.add_argument("--serve-budget-gb", type=float, default=120.0)
+    ap.add_argument("--no-mixed", action="store_true",
+                    help="skip the bf16x3-vs-fp32 comparison block")
     return ap.parse_args()
 
 
@@ -174,7 +179,12 @@ def run_reference(args, rank):
     if rank != 0:
         return
     w = synth.WORKLOADS[args.workload]
-    p = synth.workload_problem(args.workload)
+    if args.workload in ("batched_64", "serve"):
+        sp = synth.batched_instances(1)[0] if args.workload == "batched_64" else \
+            dict(L=96, K=2, N=10_000, sigma=0.5, seed=synth.seed_for(5, 0))
+        p = synth.make_problem(sp["L"], sp["K"], sp["N"], sp["sigma"], sp["seed"])
+    else:
+        p = synth.workload_problem(args.workload)
     cal = cpu_oracle_rate(p, 3.0)
     n_sub = cal["n_sub"]
     from oracle import srmra_oracle as O
@@ -204,6 +214,211 @@ def run_reference(args, rank):
     print(json.dumps(out), flush=True)
 
 
+def reduce_max(value: float, dist, device) -> float:
+    """Maximum of `value` over all ranks (the job's time is its slowest rank's)."""
+    import torch
+    if dist is None:
+        return float(value)
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(units_per_rank_step: float, steps: int, world: int, max_ms: float) -> float:
+    """Whole-job units per second: every rank processes its own replica (weak scaling)."""
+    return world * units_per_rank_step * steps / (max_ms / 1e3)
+
+
+def time_steps(run_step, steps, stream, torch, flush):
+    """Device time (ms) of each step, L2 flushed before every step (outside the events)."""
+    evs = []
+    for _ in range(steps):
+        flush.zero_()
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        run_step()
+        b.record(stream)
+        evs.append((a, b))
+    torch.cuda.synchronize()
+    return [a.elapsed_time(b) for a, b in evs]
+
+
+def mixed_block(p, w, steps, warmup, srmra, torch, stream, flush, fp32_value):
+    """The same workload in the split-bf16 tensor-core form: pairs/s and speedup over the
+    fp32 form; and the error at which that speedup holds: one EM iteration of each form
+    from the same state (the fp32 run's state after the warm-up), compared."""
+    import numpy as np
+    s3 = srmra.Solver(p.L, p.K, p.sigma, p.y, prec="bf16x3", x0=p.x0, rho1=p.rho1_0,
+                      rho2=p.rho2_0, stream=stream.cuda_stream)
+    s3.solve(warmup, w["F"], sigma_bm1=1.0, loglik=False)
+    ms = time_steps(lambda: s3.solve(1, w["F"], sigma_bm1=0.0, loglik=False), steps,
+                    stream, torch, flush)
+    s1 = srmra.Solver(p.L, p.K, p.sigma, p.y, prec="fp32", x0=p.x0, rho1=p.rho1_0,
+                      rho2=p.rho2_0, stream=stream.cuda_stream)
+    s1.solve(warmup, w["F"], sigma_bm1=1.0, loglik=False)
+    st = s1.state()
+    s3.set_state(*st)
+    s1.em_iter(1, loglik=False)
+    s3.em_iter(1, loglik=False)
+    (x1, r11, r21, _, _), (x3, r13, r23, _, _) = s1.state(), s3.state()
+    s1.close()
+    s3.close()
+    value = p.N * p.L * p.L * steps / (sum(ms) / 1e3)
+    rel = lambda a, b: float(np.linalg.norm(a.astype(np.float64) - b) / np.linalg.norm(b))
+    return {"precision": "bf16x3", "value": value, "unit": "pairs/s",
+            "ms_per_step": sum(ms) / steps, "speedup_vs_fp32": value / fp32_value,
+            "one_step_rel_diff_vs_fp32": {"x": rel(x3, x1), "rho1": rel(r13, r11),
+                                          "rho2": rel(r23, r21)},
+            "note": "per-iteration parity with the FP64 oracle (<= 1e-4) is tested in "
+                    "tests/test_gpu_tc.py"}
+
+
+def run_batched(args, rank, world, local):
+    """64 uneven problems advanced together: grouped launches in a CUDA graph."""
+    import numpy as np
+    import torch
+    from paper_2204_04754_gb300 import srmra, synth
+    torch.cuda.set_device(local)
+    w = synth.WORKLOADS[args.workload]
+    prec = args.prec or w["prec"]
+    specs = synth.batched_instances(w["count"], seed=synth.seed_for(4) + 1000 * rank)
+    stream = torch.cuda.current_stream()
+    probs = [synth.make_problem(sp["L"], sp["K"], sp["N"], sp["sigma"], sp["seed"])
+             for sp in specs]
+    solvers = [srmra.Solver(p.L, p.K, p.sigma, p.y, prec=prec, x0=p.x0, rho1=p.rho1_0,
+                            rho2=p.rho2_0, stream=stream.cuda_stream) for p in probs]
+    t0 = time.perf_counter()
+    batch = srmra.Batch(solvers, autotune=True)
+    tune_s = time.perf_counter() - t0
+    batch.solve(args.warmup, w["F"], sigma_bm1=1.0)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    l0 = sum(s.launches for s in solvers)
+    clocks = ClockSampler(local)
+    clocks.start()
+    ms = time_steps(lambda: batch.solve(1, w["F"], sigma_bm1=0.0), args.steps, stream, torch,
+                    flush)
+    clk = clocks.stop()
+    launches = sum(s.launches for s in solvers) - l0
+    # per-pass device times: one more iteration enqueued without the graph (events
+    # recorded inside a captured graph cannot be timed)
+    probe = srmra.Batch(solvers, autotune=False, graph=False)
+    probe.solve(1, w["F"], sigma_bm1=0.0)
+    p1_ms, p2_ms = probe.pass_ms()
+    probe.close()
+    total_ms = float(sum(ms))
+    pairs = sum(p.N * p.L * p.L for p in probs)
+    alg2 = sum(4 * p.l * p.l * p.N * p.L * p.L for p in probs)
+    peaks, peak_src = load_peaks()
+    peak = float(peaks["bf16_tflops_sustained"])
+    achieved = alg2 / (p2_ms / 1e3) / 1e12
+    out = {"metric": METRIC, "value": world * pairs * args.steps / (total_ms / 1e3),
+           "unit": "pairs/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+           "ms_per_step": total_ms / args.steps, "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": prec, "data": "synthetic (64 seeded problems)",
+           "config": {"workload": args.workload, "problems": len(probs),
+                      "L_high": sorted({p.L for p in probs}), "K": sorted({p.K for p in probs}),
+                      "N_total": int(sum(p.N for p in probs)), "F": w["F"],
+                      "step": "one projected-EM iteration of all problems (grouped launches, "
+                              "CUDA graph replay)",
+                      "l2": "256 MiB buffer zeroed before every timed step",
+                      "autotuner": batch.tuning(), "autotune_seconds": tune_s,
+                      "parallelism": f"{world} independent replica(s)"},
+           "roofline": {"bound": "tensor", "kernel": f"k_p2_tc grouped ({prec})",
+                        "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                        "frac": achieved / peak, "traffic": None,
+                        "algorithmic_flops_per_launch": alg2, "avg_launch_ms": p2_ms,
+                        "peak_source": f"dense bf16, sustained, of {peak_src}"},
+           "phases_ms_last_step": {"pass1_grouped": p1_ms, "pass2_grouped": p2_ms},
+           "gpu_launches": launches, "clocks": clk}
+    batch.close()
+    for s_ in solvers:
+        s_.close()
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    _ = np
+
+
+def run_serve(args, rank, local):
+    """Poisson arrivals of projected-EM solve requests (L in {64,96,128}, K in {2,4},
+    N in {1e4, 5e4, 1e5}, sigma ~ U[0.2, 1], 30 projected iterations) served with
+    continuous batching.  Latency = completion - planned arrival (queueing included)."""
+    import numpy as np
+    import torch
+    from paper_2204_04754_gb300 import srmra, synth
+    if rank != 0:
+        return
+    torch.cuda.set_device(local)
+    w = synth.WORKLOADS[args.workload]
+    prec = args.prec or w["prec"]
+    rng = np.random.Generator(np.random.PCG64(synth.seed_for(5)))
+    n = args.requests
+    arrivals = np.cumsum(rng.exponential(1.0 / w["rate"], size=n))
+    specs = []
+    for k in range(n):
+        L = int(rng.choice([64, 96, 128]))
+        K = int(rng.choice([2, 4]))
+        N = int(rng.choice([10_000, 50_000, 100_000]))
+        sigma = float(rng.uniform(0.2, 1.0))
+        specs.append((L, K, N, sigma))
+    t0 = time.perf_counter()
+    probs = [synth.make_problem(L, K, N, sg, seed=synth.seed_for(5, k))
+             for k, (L, K, N, sg) in enumerate(specs)]
+    gen_s = time.perf_counter() - t0
+    stream = torch.cuda.current_stream()
+    free, total = torch.cuda.mem_get_info()
+    budget = int(min(free * 0.8, args.serve_budget_gb * 2 ** 30))
+    srv = srmra.Server(budget, max_active=args.serve_slots, prec=prec, stream=stream.cuda_stream)
+    # warm the kernels and graph machinery on a tiny request (not part of the trace)
+    wp = synth.make_problem(64, 4, 2000, 0.5, seed=synth.seed_for(5, 999))
+    wid = srv.submit(wp.L, wp.K, wp.sigma, wp.y, 2, F=w["F"])
+    while srv.step()[0] > 0:
+        pass
+    srv.result(wid, wp.L)
+    ids = {}
+    done = {}
+    pending = list(range(n))
+    steps = 0
+    clocks = ClockSampler(local)
+    clocks.start()
+    start = time.perf_counter()
+    while len(done) < n:
+        now = time.perf_counter() - start
+        while pending and arrivals[pending[0]] <= now:
+            k = pending.pop(0)
+            p = probs[k]
+            ids[k] = srv.submit(p.L, p.K, p.sigma, p.y, w["iters"], F=w["F"])
+        running, queued, finished = srv.step()
+        steps += 1
+        if finished:
+            tnow = time.perf_counter() - start
+            for k, rid in ids.items():
+                if k not in done and srv.result(rid, probs[k].L)["state"] == 2:
+                    done[k] = tnow
+        if running == 0 and queued == 0 and pending:
+            wait = arrivals[pending[0]] - (time.perf_counter() - start)
+            if wait > 0:
+                time.sleep(min(wait, 0.05))
+    makespan = time.perf_counter() - start
+    clk = clocks.stop()
+    lat = np.array([1e3 * (done[k] - arrivals[k]) for k in range(n)])
+    pairs = sum(p.N * p.L * p.L * w["iters"] for p in probs)
+    srv.close()
+    out = {"metric": "serve p99 latency", "value": float(np.percentile(lat, 99)), "unit": "ms",
+           "n_gpus": 1, "steps": steps, "warmup": 1, "higher_is_better": False,
+           "scaling": "weak", "vs_baseline": None, "dtype": prec,
+           "data": "synthetic (seeded requests)",
+           "config": {"workload": args.workload, "requests": n, "rate_per_s": w["rate"],
+                      "iters_per_request": w["iters"], "F": w["F"],
+                      "mix": "L {64,96,128} x K {2,4} x N {1e4,5e4,1e5}, sigma U[0.2,1]",
+                      "slots": args.serve_slots, "budget_bytes": budget,
+                      "data_generation_s": gen_s},
+           "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+           "max_ms": float(lat.max()), "solves_per_s": n / makespan,
+           "pairs_per_s": pairs / makespan, "makespan_s": makespan, "clocks": clk}
+    print(json.dumps(out), flush=True)
+
+
 def main():
     args = parse()
     rank = int(os.environ.get("RANK", "0"))
@@ -211,6 +426,12 @@ def main():
     local = int(os.environ.get("LOCAL_RANK", "0"))
     if args.impl == "reference":
         run_reference(args, rank)
+        return
+    if args.workload.startswith("batched"):
+        run_batched(args, rank, world, local)
+        return
+    if args.workload.startswith("serve"):
+        run_serve(args, rank, local)
         return
 
     import numpy as np
@@ -262,13 +483,11 @@ def main():
     phase_ms, phase_n = s.profile_read()
     s.profile(False)
     if dist:
-        t = torch.tensor([total_ms], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
+        total_ms = reduce_max(total_ms, dist, "cuda")
         dist.barrier()
 
     pairs_per_step = p.N * p.L * p.L
-    value = world * pairs_per_step * args.steps / (total_ms / 1e3)
+    value = job_throughput(pairs_per_step, args.steps, world, total_ms)
 
     # roofline of the dominant kernel (phase), from the live CUDA events
     peaks, peak_src = load_peaks()
@@ -309,6 +528,9 @@ def main():
 
     if rank == 0 and not args.no_e2e:
         out["e2e"] = e2e_run(p, prec, w, srmra, torch)
+    if rank == 0 and prec == "fp32" and not args.no_mixed:
+        out["bf16x3"] = mixed_block(p, w, args.steps, args.warmup, srmra, torch, stream, flush,
+                                    value)
     if rank == 0 and world == 1 and not args.no_cpu:
         cb = cpu_oracle_rate(p, args.cpu_seconds)
         cb.pop("n_sub", None)

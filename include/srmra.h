@@ -70,6 +70,8 @@ typedef enum { SRMRA_FP32 = 0, SRMRA_BF16 = 1, SRMRA_BF16X3 = 2 } srmra_precisio
 
 /* flags */
 #define SRMRA_FLAG_CHECK_NUMERIC 1u /* scan x, rho, LL for NaN/Inf after each iteration */
+#define SRMRA_FLAG_NO_CLUSTER 2u    /* tensor-core forms: recompute the weights per pixel
+                                       chunk instead of sharing them across a cluster */
 
 typedef struct {
   int32_t L_high;  /* L >= 2 */
@@ -123,6 +125,19 @@ srmra_status srmra_em_iter(srmra_ctx* ctx, int32_t n_iters, double* loglik_out);
 srmra_status srmra_project(srmra_ctx* ctx, double sigma_bm, srmra_denoiser_fn fn,
                            void* user);
 
+/* Built-in denoiser variants (srmra_set_denoiser). */
+#define SRMRA_DENOISE_HARD 0 /* keep an AC coefficient iff |c| > threshold * sigma_BM */
+#define SRMRA_DENOISE_SOFT 1 /* c <- sign(c) max(|c| - t, 0): the prox of t ||AC||_1, a
+                                convex prox as in Sec. 4's Assumption 2 */
+
+/* srmra_set_denoiser -- choose the built-in denoiser used by srmra_project,
+ * srmra_solve and batches: mode SRMRA_DENOISE_HARD (default) or _SOFT, threshold
+ * multiplier of sigma_BM (default 2.7), and spin != 0 to average the block denoiser
+ * over all 64 offsets of the 8 x 8 block grid (cycle spinning; allocates 64 L^2
+ * float64 of device memory once).  The paper's BM3D (Sec. 5) is not part of the
+ * method; any other denoiser can be passed as a callback. */
+srmra_status srmra_set_denoiser(srmra_ctx* ctx, int32_t mode, double threshold, int32_t spin);
+
 /* srmra_solve -- Algorithm 2 (projected EM) for `iters` EM iterations: after every
  * iteration whose 1-based global count t+1 is a multiple of F, apply D(x, sigma_BM)
  * (fn, or the built-in DCT denoiser if fn == NULL) and set sigma_BM <- decay * sigma_BM
@@ -155,6 +170,115 @@ srmra_status srmra_get_estep(srmra_ctx* ctx, double* lse, double* c);
 
 /* srmra_launch_count -- number of CUDA kernels this context has launched so far. */
 srmra_status srmra_launch_count(const srmra_ctx* ctx, int64_t* count);
+
+/* ---- Batches: many independent problems advanced together (one GPU). ----
+ * A batch groups contexts of the same precision form and CUDA stream.  Each EM
+ * iteration (Sec. 2) of a batch runs ONE grouped persistent launch of pass 1 and ONE of
+ * pass 2 over the work units of all its problems (tensor-core forms; the float32 form
+ * launches per problem), plus the small per-problem kernels; the whole iteration,
+ * including the projection step of Algorithm 2, is captured once into a CUDA graph and
+ * replayed.  Problems keep their own data, estimate and schedule; results do not depend
+ * on which other problems share the batch beyond float32 rounding of the chosen work
+ * decomposition. */
+typedef struct srmra_batch srmra_batch; /* opaque; owned by the library */
+
+#define SRMRA_BATCH_AUTOTUNE 1u /* time candidate work decompositions, keep the fastest */
+#define SRMRA_BATCH_NO_GRAPH 2u /* enqueue kernels directly instead of a CUDA graph */
+
+/* srmra_batch_create -- build a batch over ctxs[0..count-1] (distinct, same precision,
+ * same stream).  The contexts stay owned by the caller and must outlive the batch; a
+ * context may belong to several batches but batches that share a context must not run
+ * concurrently.  With SRMRA_BATCH_AUTOTUNE the work decomposition of the grouped
+ * launches (shift groups of pass 1 x {1,2}, observation ranges of pass 2 x {1,2},
+ * problem order {as given, most expensive unit first}) is timed on the device and the
+ * fastest is kept (the problems' estimates are not changed by the timing runs).
+ * Errors: EINVAL, ENOMEM, ECUDA.  Message: srmra_batch_last_error(NULL). */
+srmra_status srmra_batch_create(srmra_ctx** ctxs, int32_t count, uint32_t flags,
+                                srmra_batch** out);
+
+/* srmra_batch_solve -- `iters` iterations of Algorithm 2 for every problem of the batch:
+ * each problem projects with the built-in denoiser after every iteration whose 1-based
+ * count (its own t+1) is a multiple of F (F = 0: plain EM) and then decays its sigma_BM
+ * by `decay`.  sigma_bm1 > 0 resets every problem's sigma_BM first.  loglik_last: host
+ * array of `count` float64 (order of srmra_batch_create) receiving LL(theta) of each
+ * problem's last iteration, or NULL.  Synchronises the stream. */
+srmra_status srmra_batch_solve(srmra_batch* b, int32_t iters, int32_t F, double sigma_bm1,
+                               double decay, double* loglik_last);
+
+/* (srmra_batch_solve with F < 0 uses every problem's own schedule, see
+ * srmra_set_schedule, instead of one F and decay for all.) */
+
+/* srmra_set_schedule -- the Algorithm 2 schedule a batch uses for this problem when it
+ * is solved with F < 0: projection every F iterations (F = 0: none), current sigma_BM,
+ * and the decay factor applied after each projection (Eq. decaying_function). */
+srmra_status srmra_set_schedule(srmra_ctx* ctx, int32_t F, double sigma_bm, double decay);
+
+/* srmra_estimate_device_bytes -- device memory srmra_create would allocate for these
+ * parameters (no device memory is touched; for admission control). */
+srmra_status srmra_estimate_device_bytes(const srmra_params* p, int64_t* bytes);
+
+/* srmra_device_bytes -- device memory held by a context. */
+srmra_status srmra_device_bytes(const srmra_ctx* ctx, int64_t* bytes);
+
+/* srmra_batch_tuning -- the decomposition chosen by the autotuner (scales 1 or 2, order
+ * 0 = as given, 1 = most expensive first) and its timed milliseconds per pass pair. */
+srmra_status srmra_batch_tuning(const srmra_batch* b, int32_t* p1_scale, int32_t* p2_scale,
+                                int32_t* order, double* ms);
+
+/* srmra_batch_pass_ms -- device time (CUDA events) of the grouped pass-1 and pass-2
+ * launches of the batch's most recent iteration.  Synchronises the stream. */
+srmra_status srmra_batch_pass_ms(srmra_batch* b, double* ms_pass1, double* ms_pass2);
+
+void srmra_batch_destroy(srmra_batch* b);
+const char* srmra_batch_last_error(const srmra_batch* b);
+
+/* srmra_em_iter_batch -- n_iters plain EM iterations (no projection) of every context,
+ * through a transient batch (no autotuning, no graph). */
+srmra_status srmra_em_iter_batch(srmra_ctx** ctxs, int32_t count, int32_t n_iters);
+
+/* ---- Serving: continuous batching of solve requests on one GPU. ----
+ * srmra_server_submit queues a request (a full projected-EM solve of one problem: y on
+ * the host, copied at submission; optional x0; iteration count; Algorithm 2 schedule F,
+ * sigma_BM_1, decay).  Each srmra_server_step admits queued requests in arrival order
+ * while a slot is free and their device memory (srmra_estimate_device_bytes) fits the
+ * budget -- their observations, x and rho then stay on the device until they retire --,
+ * advances every running request by one EM iteration (+ scheduled projection) as one
+ * batch (grouped launches, CUDA graph re-captured only when the set of requests
+ * changes), and retires the requests that reached their iteration count (estimate
+ * copied to the host, device memory released).  Requests submitted while others run
+ * join at the next iteration boundary.  A request's arithmetic is independent of the
+ * other requests, so its result equals srmra_create + srmra_solve of the same problem.
+ * Submission may come from another thread than the one calling srmra_server_step. */
+typedef struct srmra_server srmra_server;
+
+srmra_status srmra_server_create(int64_t device_budget_bytes, int32_t max_active,
+                                 int32_t prec, void* cuda_stream, srmra_server** out);
+
+/* y: N x l x l float32 host array (p->N, p->L_high, p->K, p->sigma; p->prec is replaced by
+ * the server's form); x0: L x L float32 host or NULL (mean-upsampled init).  ENOMEM if
+ * the request alone exceeds the budget.  *request_id identifies it. */
+srmra_status srmra_server_submit(srmra_server* s, const srmra_params* p, const float* y,
+                                 const float* x0, int32_t iters, int32_t F, double sigma_bm1,
+                                 double decay, int64_t* request_id);
+
+/* One admission + iteration + retirement round; reports the numbers of running and
+ * queued requests afterwards and of requests that finished in this step. */
+srmra_status srmra_server_step(srmra_server* s, int32_t* n_running, int32_t* n_queued,
+                               int32_t* n_finished);
+
+/* state: 0 queued, 1 running, 2 done, 3 failed (the call then returns the failure).
+ * When done, x (L*L float32), rho1, rho2 (L float64) and the last iteration's
+ * log-likelihood are copied out (any pointer may be NULL).  times_ms (3 doubles or
+ * NULL): submit->admit, admit->done, submit->done in milliseconds (-1 if not yet). */
+srmra_status srmra_server_result(srmra_server* s, int64_t id, int32_t* state, float* x,
+                                 double* rho1, double* rho2, double* loglik_last,
+                                 double* times_ms);
+
+/* Device memory reserved by running requests, and the budget. */
+srmra_status srmra_server_memory(srmra_server* s, int64_t* used, int64_t* budget);
+
+void srmra_server_destroy(srmra_server* s);
+const char* srmra_server_last_error(const srmra_server* s);
 
 /* Phases of one iteration, for srmra_profile_read. */
 enum {

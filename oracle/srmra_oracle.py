@@ -238,14 +238,30 @@ def dct_matrix(B: int = 8) -> np.ndarray:
     return C
 
 
-def dct_denoise(x: np.ndarray, sigma_bm: float, thr: float = 2.7, B: int = 8):
-    """D(x, sigma_BM): per BxB block, X = C x C^T, zero AC coefficients with
-    |X| <= thr*sigma_BM, keep DC, invert.  Returns (x_denoised, margin) where margin is
-    min over AC coefficients of | |X| - thr*sigma_BM | (distance to a threshold flip)."""
+def dct_denoise(x: np.ndarray, sigma_bm: float, thr: float = 2.7, B: int = 8,
+                mode: str = "hard", spin: bool = False):
+    """D(x, sigma_BM): per BxB block, X = C x C^T, threshold the AC coefficients at
+    t = thr*sigma_BM, keep DC, invert.
+      mode 'hard': keep an AC coefficient iff |X| > t (reading R9);
+      mode 'soft': X <- sign(X) max(|X| - t, 0), the proximal operator of t*||AC(DCT x)||_1
+                   on each block (a convex prox, the setting of Sec. 4's Assumption 2);
+      spin:        average of the block denoiser over all B^2 circular offsets of the block
+                   grid (cycle spinning): D(x) = mean_d R_{-d} D_0(R_d x).
+    Returns (x_denoised, margin) with margin = min over AC coefficients of | |X| - t |
+    (the distance to a hard-threshold flip)."""
     x = np.asarray(x, np.float64)
     L = x.shape[0]
     if L % B:
         raise ValueError("image side must be a multiple of the block size")
+    if spin:
+        acc = np.zeros_like(x)
+        margin = math.inf
+        for d1 in range(B):
+            for d2 in range(B):
+                y, mg = dct_denoise(shift(x, d1, d2), sigma_bm, thr, B, mode, False)
+                acc += shift(y, -d1, -d2)
+                margin = min(margin, mg)
+        return acc / (B * B), margin
     C = dct_matrix(B)
     t = thr * sigma_bm
     out = np.empty_like(x)
@@ -255,10 +271,17 @@ def dct_denoise(x: np.ndarray, sigma_bm: float, thr: float = 2.7, B: int = 8):
     for a in range(0, L, B):
         for b in range(0, L, B):
             X = C @ x[a:a + B, b:b + B] @ C.T
-            keep = np.abs(X) > t
-            keep[0, 0] = True
+            if mode == "hard":
+                keep = np.abs(X) > t
+                keep[0, 0] = True
+                Xd = X * keep
+            elif mode == "soft":
+                Xd = np.sign(X) * np.maximum(np.abs(X) - t, 0.0)
+                Xd[0, 0] = X[0, 0]
+            else:
+                raise ValueError(mode)
             margin = min(margin, float(np.min(np.abs(np.abs(X[ac]) - t))))
-            out[a:a + B, b:b + B] = C.T @ (X * keep) @ C
+            out[a:a + B, b:b + B] = C.T @ Xd @ C
     return out, margin
 
 
@@ -268,7 +291,8 @@ def dct_denoise(x: np.ndarray, sigma_bm: float, thr: float = 2.7, B: int = 8):
 
 
 def projected_em(Y, x0, rho1, rho2, sigma, K, iters, F, sigma_bm1=1.0,
-                 decay=2.0 ** -0.1, chunk=None, em_step=None):
+                 decay=2.0 ** -0.1, chunk=None, em_step=None, mode="hard", spin=False,
+                 thr=2.7):
     """Algorithm 2: repeat {F EM steps (Eqs. weights_EM, x_EM, rho_EM);
     x <- D(x, sigma_BM); sigma_BM <- decay * sigma_BM}, for `iters` EM steps total.
     F = 0 runs plain EM (no projection).  Returns (x, rho1, rho2, history) where
@@ -284,7 +308,7 @@ def projected_em(Y, x0, rho1, rho2, sigma, K, iters, F, sigma_bm1=1.0,
         x, r1, r2, LL, _ = step(x, r1, r2)
         hist["LL"].append(LL)
         if F > 0 and (t + 1) % F == 0:
-            x, mg = dct_denoise(x, sbm)
+            x, mg = dct_denoise(x, sbm, thr=thr, mode=mode, spin=spin)
             hist["sigma_bm"].append(sbm)
             hist["margin"] = min(hist["margin"], mg)
             sbm *= decay

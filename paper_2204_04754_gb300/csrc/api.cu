@@ -55,9 +55,15 @@ struct Allocator {
   int64_t used = 0;
   int64_t limit = alloc_limit();
   std::vector<void*>* owned;
+  bool dry = false;  // count bytes only (admission estimates)
   template <typename T>
   cudaError_t get(T** p, int64_t count) {
     const int64_t bytes = count * (int64_t)sizeof(T);
+    if (dry) {
+      used += round_up(bytes, 256);
+      *p = nullptr;
+      return cudaSuccess;
+    }
     if (limit >= 0 && used + bytes > limit) return cudaErrorMemoryAllocation;
     cudaError_t e = cudaMalloc((void**)p, (size_t)bytes);
     if (e != cudaSuccess) return e;
@@ -161,6 +167,99 @@ srmra_status ensure_ll(srmra_ctx* c, int n) {
   return SRMRA_OK;
 }
 
+// Geometry and work plan of a context; caps receives the partial-buffer capacities
+// (pass-1 groups, Z' slices, c/zb slices) the buffers are sized for.
+void setup_ctx(srmra_ctx* c, const srmra_params* p, int num_sms, int caps[3]) {
+  c->num_sms = num_sms;
+  c->prec = p->prec;
+  c->flags = p->flags;
+  c->no_cluster = (p->flags & SRMRA_FLAG_NO_CLUSTER) != 0;
+  Geom& g = c->g;
+  g.L = p->L_high;
+  g.K = p->K;
+  g.l = g.L / g.K;
+  g.l2 = g.l * g.l;
+  g.S = g.L * g.L;
+  g.Spad = (int)round_up(g.S, SPAD);
+  g.ldy = (int)round_up(g.l2, 16);
+  g.ldk = (int)round_up(g.l2, 64);
+  g.N = p->N;
+  g.Npad = round_up(g.N, NPAD);
+  g.sigma = p->sigma;
+  if (c->prec != SRMRA_FP32) {
+    // size the partial buffers for the finest decomposition the batch tuner may pick
+    plan_tc(c, 2, 2);
+    c->plan.cap_p1_groups = c->plan.p1_groups;
+    c->plan.cap_nsplit = c->plan.p2_nsplit;
+    caps[0] = c->plan.p1_groups;
+    caps[1] = c->plan.nparts_z;
+    caps[2] = c->plan.nparts_c;
+    plan_tc(c, 1, 1);
+  } else {
+    plan_simt(c);
+    caps[0] = c->plan.p1_groups;
+    caps[1] = c->plan.nparts_z;
+    caps[2] = c->plan.nparts_c;
+  }
+}
+
+// Every device buffer of a context (or, with A.dry, just their total size).
+cudaError_t allocate_buffers(srmra_ctx* c, Allocator& A, const int caps[3], const char** what) {
+  const Geom& g = c->g;
+  const Plan& pl = c->plan;
+  const bool tc = c->prec != SRMRA_FP32;
+#define AL(ptr, count)                                   \
+  do {                                                   \
+    cudaError_t e2 = A.get(&(ptr), (int64_t)(count));    \
+    if (e2 != cudaSuccess) {                             \
+      *what = "allocate " #ptr;                          \
+      return e2;                                         \
+    }                                                    \
+  } while (0)
+  AL(c->Yc, g.Npad * g.ldy);
+  if (tc) {
+    AL(c->Yh, g.Npad * g.ldk);
+    AL(c->YTf, g.Npad * g.l2);
+    AL(c->Ah, (int64_t)g.Spad * g.ldk);
+    AL(c->d_ustart, 4);
+    {
+      unsigned char* di = nullptr;
+      AL(di, (int64_t)tc_inst_bytes());
+      c->d_inst = di;
+    }
+    if (c->prec == SRMRA_BF16X3) {
+      AL(c->Yl, g.Npad * g.ldk);
+      AL(c->Al, (int64_t)g.Spad * g.ldk);
+    }
+  } else {
+    AL(c->YcT, g.Npad * g.ldy);
+    AL(c->AxT, (int64_t)g.ldy * g.Spad);
+  }
+  AL(c->ybar, g.Npad);
+  AL(c->yy, g.Npad);
+  AL(c->x, g.S);
+  AL(c->rho1, g.L);
+  AL(c->rho2, g.L);
+  AL(c->sub, 2 * g.K * g.K);
+  AL(c->colb, g.Spad);
+  AL(c->colm, g.Spad);
+  AL(c->pm, (int64_t)caps[0] * g.Npad);
+  AL(c->ps, (int64_t)caps[0] * g.Npad);
+  AL(c->lse2, g.Npad);
+  AL(c->lse, g.Npad);
+  AL(c->llpart, pl.ll_blocks);
+  AL(c->Zp, (int64_t)caps[1] * g.Spad * g.ldy);
+  AL(c->cp, (int64_t)caps[2] * g.Spad);
+  AL(c->zbp, (int64_t)caps[2] * g.Spad);
+  AL(c->cfin, 2 * (int64_t)g.Spad);
+  AL(c->bpart, (int64_t)fin_t_splits(g, c->num_sms) * g.S);
+  AL(c->Ar, 2 * g.K * g.K);
+  AL(c->status, 1);
+  AL(c->d_sched, 1);
+#undef AL
+  return cudaSuccess;
+}
+
 }  // namespace
 
 // Mean-upsampled initial guess x0[q] = mean_i y_i[q1 / K, q2 / K] (nearest neighbour).
@@ -224,73 +323,25 @@ srmra_status srmra_create(const srmra_params* p, const float* y, int32_t y_is_de
   srmra_ctx* c = new (std::nothrow) srmra_ctx();
   if (!c) return fail(nullptr, SRMRA_ENOMEM, "host allocation failed");
   c->device = dev;
-  c->num_sms = prop.multiProcessorCount;
   c->stream = (cudaStream_t)cuda_stream;
-  c->prec = p->prec;
-  c->flags = p->flags;
-  Geom& g = c->g;
-  g.L = p->L_high;
-  g.K = p->K;
-  g.l = g.L / g.K;
-  g.l2 = g.l * g.l;
-  g.S = g.L * g.L;
-  g.Spad = (int)round_up(g.S, SPAD);
-  g.ldy = (int)round_up(g.l2, 16);
-  g.ldk = (int)round_up(g.l2, 64);
-  g.N = p->N;
-  g.Npad = round_up(g.N, NPAD);
-  g.sigma = p->sigma;
-
-
+  int caps[3];
+  setup_ctx(c, p, prop.multiProcessorCount, caps);
+  const Geom& g = c->g;
   const bool tc = c->prec != SRMRA_FP32;
-  if (tc)
-    plan_tc(c);
-  else
-    plan_simt(c);
-  const Plan& pl = c->plan;
   Allocator A{c, 0, alloc_limit(), &c->owned};
-  auto bail = [&](cudaError_t err, const char* what) {
-    srmra_status s2 = cuda_fail(nullptr, err, what);
+  const char* what = nullptr;
+  e = allocate_buffers(c, A, caps, &what);
+  if (e != cudaSuccess) {
+    srmra_status s2 = cuda_fail(nullptr, e, what);
+    srmra_destroy(c);
+    return s2;
+  }
+  c->device_bytes = A.used;
+  auto bail = [&](cudaError_t err, const char* w) {
+    srmra_status s2 = cuda_fail(nullptr, err, w);
     srmra_destroy(c);
     return s2;
   };
-#define AL(ptr, count)                                   \
-  do {                                                   \
-    cudaError_t e2 = A.get(&(ptr), (int64_t)(count));    \
-    if (e2 != cudaSuccess) return bail(e2, "allocate " #ptr); \
-  } while (0)
-  AL(c->Yc, g.Npad * g.ldy);
-  if (tc) {
-    AL(c->Yh, g.Npad * g.ldk);
-    AL(c->YTf, g.Npad * g.l2);
-    AL(c->Ah, (int64_t)g.Spad * g.ldk);
-    if (c->prec == SRMRA_BF16X3) {
-      AL(c->Yl, g.Npad * g.ldk);
-      AL(c->Al, (int64_t)g.Spad * g.ldk);
-    }
-  } else {
-    AL(c->YcT, g.Npad * g.ldy);
-    AL(c->AxT, (int64_t)g.ldy * g.Spad);
-  }
-  AL(c->ybar, g.Npad);
-  AL(c->yy, g.Npad);
-  AL(c->x, g.S);
-  AL(c->rho1, g.L);
-  AL(c->rho2, g.L);
-  AL(c->sub, 2 * g.K * g.K);
-  AL(c->colb, g.Spad);
-  AL(c->colm, g.Spad);
-  AL(c->pm, (int64_t)pl.p1_groups * g.Npad);
-  AL(c->ps, (int64_t)pl.p1_groups * g.Npad);
-  AL(c->lse2, g.Npad);
-  AL(c->lse, g.Npad);
-  AL(c->llpart, pl.ll_blocks);
-  AL(c->Zp, (int64_t)pl.nparts_z * g.Spad * g.ldy);
-  AL(c->cp, (int64_t)pl.nparts_c * g.Spad);
-  AL(c->zbp, (int64_t)pl.nparts_c * g.Spad);
-  AL(c->cfin, 2 * (int64_t)g.Spad);
-  AL(c->Ar, 2 * g.K * g.K);
-  AL(c->status, 1);
   float* ytmp = nullptr;
   if (!y_is_device) {
     e = cudaMalloc((void**)&ytmp, sizeof(float) * (size_t)(g.N * g.l2));
@@ -334,7 +385,6 @@ srmra_status srmra_create(const srmra_params* p, const float* y, int32_t y_is_de
     srmra_destroy(c);
     return SRMRA_ENOMEM;
   }
-#undef AL
   *out = c;
   return SRMRA_OK;
 }
@@ -443,6 +493,60 @@ srmra_status srmra_get_estep(srmra_ctx* c, double* lse, double* cs) {
     CK(c, cudaMemcpyAsync(cs, c->cfin, sizeof(double) * (size_t)c->g.S, cudaMemcpyDeviceToHost,
                           c->stream));
   CK(c, cudaStreamSynchronize(c->stream));
+  return SRMRA_OK;
+}
+
+srmra_status srmra_estimate_device_bytes(const srmra_params* p, int64_t* bytes) {
+  if (!p || !bytes) return fail(nullptr, SRMRA_EINVAL, "params or bytes is NULL");
+  if (p->L_high < 2 || p->K < 1 || p->L_high % p->K != 0 || p->N < 1 ||
+      (p->prec != SRMRA_FP32 && p->prec != SRMRA_BF16 && p->prec != SRMRA_BF16X3))
+    return fail(nullptr, SRMRA_EINVAL, "invalid problem parameters");
+  int dev = 0, sms = 152;
+  if (cudaGetDevice(&dev) == cudaSuccess)
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  cudaGetLastError();
+  srmra_ctx c;
+  int caps[3];
+  setup_ctx(&c, p, sms, caps);
+  Allocator A{&c, 0, -1, &c.owned};
+  A.dry = true;
+  const char* what = nullptr;
+  allocate_buffers(&c, A, caps, &what);
+  *bytes = A.used + 64 * (int64_t)sizeof(double);  // + the log-likelihood history
+  return SRMRA_OK;
+}
+
+srmra_status srmra_device_bytes(const srmra_ctx* c, int64_t* bytes) {
+  if (!c || !bytes) return fail(nullptr, SRMRA_EINVAL, "ctx or bytes is NULL");
+  *bytes = c->device_bytes + (int64_t)c->ll_cap * (int64_t)sizeof(double);
+  return SRMRA_OK;
+}
+
+srmra_status srmra_set_schedule(srmra_ctx* c, int32_t F, double sigma_bm, double decay) {
+  if (!c) return fail(nullptr, SRMRA_EINVAL, "ctx is NULL");
+  if (F < 0 || !(decay > 0.0) || !(sigma_bm >= 0.0))
+    return fail(c, SRMRA_EINVAL, "need F >= 0, sigma_bm >= 0, decay > 0");
+  if (F > 0 && c->g.L % 8 != 0)
+    return fail(c, SRMRA_EINVAL, "built-in denoiser needs L % 8 == 0");
+  c->sched_F = F;
+  c->sigma_bm = sigma_bm;
+  c->sched_decay = decay;
+  return SRMRA_OK;
+}
+
+srmra_status srmra_set_denoiser(srmra_ctx* c, int32_t mode, double threshold, int32_t spin) {
+  if (!c) return fail(nullptr, SRMRA_EINVAL, "ctx is NULL");
+  if ((mode != SRMRA_DENOISE_HARD && mode != SRMRA_DENOISE_SOFT) || !(threshold >= 0.0))
+    return fail(c, SRMRA_EINVAL, "unknown denoiser mode or negative threshold");
+  if (spin && !c->dn_acc) {
+    cudaError_t e = cudaMalloc((void**)&c->dn_acc, sizeof(double) * 64 * (size_t)c->g.S);
+    if (e != cudaSuccess) return cuda_fail(c, e, "allocate cycle-spinning buffer");
+    c->owned.push_back(c->dn_acc);
+    c->device_bytes += (int64_t)sizeof(double) * 64 * c->g.S;
+  }
+  c->dn_mode = mode;
+  c->dn_thr = threshold;
+  c->dn_spin = spin != 0;
   return SRMRA_OK;
 }
 

@@ -249,49 +249,91 @@ __global__ void __launch_bounds__(1024) k_fin_counts(
   }
 }
 
-// x_{t+1}[q] = (b'[q] + ZB_r) / A_r with b'[q] = sum_t Z'[s(r,t)][m + t] summed over the
-// partial slices (Eq. x_EM on sub-image r = q mod K, m = q div K); one warp per pixel.
-// A pixel with A_r = 0 keeps its value (reading of an uncovered pixel).
-__global__ void __launch_bounds__(256) k_fin_x(const float* __restrict__ Zp, int nparts,
-                                               int Spad, int ldy, int L, int K, int l,
-                                               const double* __restrict__ Ar,
-                                               float* __restrict__ x,
-                                               int* __restrict__ status) {
-  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const int lane = threadIdx.x & 31;
-  if (warp >= L * L) return;
-  const int q1 = warp / L, q2 = warp % L;
-  const int r1 = q1 % K, r2 = q2 % K, m1 = q1 / K, m2 = q2 / K;
-  const int l2 = l * l;
-  double acc = 0.0;
-  for (int t = lane; t < l2; t += 32) {
-    const int t1 = t / l, t2 = t % l;
-    const int s = mod_pos(t1 * K - r1, L) * L + mod_pos(t2 * K - r2, L);
-    const int n = ((m1 + t1) % l) * l + (m2 + t2) % l;
-    for (int p = 0; p < nparts; ++p) acc += (double)Zp[((int64_t)p * Spad + s) * ldy + n];
-  }
+// Partial right-hand side of Eq. x_EM on sub-image r (pixel q = r + m K):
+//   b'_r[m] = sum_t Z'[s(r,t)][(m + t) mod l],   s(r,t) = t K - r (mod L, per axis),
+// over a range of lags t and all partial slices.  For a fixed (r, t) the row
+// Z'[s(r,t)] is read contiguously and added at a circular offset, so the loads are
+// coalesced.  Float32 with compensated (Kahan) summation; one partial per t-range.
+__global__ void __launch_bounds__(256) k_fin_b(const float* __restrict__ Zp, int nparts, int Spad,
+                                               int ldy, int L, int K, int l, int t_per,
+                                               float* __restrict__ bpart) {
+  const int r = blockIdx.x, ts = blockIdx.y;
+  const int r1 = r / K, r2 = r % K, l2 = l * l;
+  const int t0 = ts * t_per, t1 = min(l2, t0 + t_per);
+  const int total = (t1 - t0) * nparts;  // (lag, slice) pairs of this range
+  for (int m = threadIdx.x; m < l2; m += 256) {
+    const int m1 = m / l, m2 = m % l;
+    float acc = 0.f, comp = 0.f;
+    for (int j0 = 0; j0 < total; j0 += 8) {
+      float v[8];
 #pragma unroll
-  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-  if (lane == 0) {
-    const int r = r1 * K + r2;
-    const double A = Ar[r];
-    if (A > 0.0) {
-      const double v = (acc + Ar[K * K + r]) / A;
-      x[warp] = (float)v;
-      if (!isfinite(v)) atomicOr(status, STATUS_NUMERIC);
+      for (int q = 0; q < 8; ++q) {  // eight independent loads, then the sums in order
+        const int j = j0 + q;
+        v[q] = 0.f;
+        if (j < total) {
+          const int t = t0 + j / nparts, p = j % nparts;
+          const int tt1 = t / l, tt2 = t % l;
+          int a1 = m1 + tt1, a2 = m2 + tt2;
+          a1 -= (a1 >= l) ? l : 0;
+          a2 -= (a2 >= l) ? l : 0;
+          const int s = mod_pos(tt1 * K - r1, L) * L + mod_pos(tt2 * K - r2, L);
+          v[q] = Zp[((int64_t)p * Spad + s) * ldy + a1 * l + a2];
+        }
+      }
+#pragma unroll
+      for (int q = 0; q < 8; ++q) {
+        const float y = v[q] - comp;
+        const float tsum = acc + y;
+        comp = (tsum - acc) - y;
+        acc = tsum;
+      }
     }
+    bpart[((int64_t)ts * K * K + r) * l2 + m] = acc;
   }
 }
 
-// Built-in denoiser: per 8x8 block, orthonormal 2D DCT-II in float64, keep DC and the
-// AC coefficients with |c| > thr, inverse transform.
-__global__ void __launch_bounds__(64) k_dct8(float* __restrict__ x, int L, double thr) {
+// x_{t+1}[q] = (b'[q] + ZB_r) / A_r with b'[q] the fixed-order float64 sum of the
+// lag-range partials (Eq. x_EM); a pixel with A_r = 0 keeps its value (uncovered pixel).
+// One thread per (sub-image r, low-resolution pixel m): the partials are read coalesced.
+__global__ void k_fin_x(const float* __restrict__ bpart, int n_ts, int L, int K, int l,
+                        const double* __restrict__ Ar, float* __restrict__ x,
+                        int* __restrict__ status) {
+  const int l2 = l * l;
+  const int idx = blockIdx.x * blockDim.x + threadIdx.x;  // r * l2 + m
+  if (idx >= K * K * l2) return;
+  const int r = idx / l2, m = idx % l2;
+  double b[4] = {0.0, 0.0, 0.0, 0.0};
+  int ts = 0;
+  for (; ts + 4 <= n_ts; ts += 4) {
+#pragma unroll
+    for (int k = 0; k < 4; ++k) b[k] += (double)bpart[(int64_t)(ts + k) * K * K * l2 + idx];
+  }
+  for (; ts < n_ts; ++ts) b[0] += (double)bpart[(int64_t)ts * K * K * l2 + idx];
+  const double bsum = (b[0] + b[1]) + (b[2] + b[3]);
+  const int q = ((r / K) + (m / l) * K) * L + (r % K) + (m % l) * K;
+  const double A = Ar[r];
+  if (A > 0.0) {
+    const double v = (bsum + Ar[K * K + r]) / A;
+    x[q] = (float)v;
+    if (!isfinite(v)) atomicOr(status, STATUS_NUMERIC);
+  }
+}
+
+// Built-in denoiser: per 8x8 block, orthonormal 2D DCT-II in float64, DC kept, the AC
+// coefficients thresholded at thr: hard (keep iff |c| > thr) or soft
+// (c <- sign(c) max(|c| - thr, 0), the prox of thr * ||AC||_1).  The block grid is
+// offset by (d1, d2): block pixel (u, v) of block (b1, b2) is image pixel
+// ((8 b1 + u - d1) mod L, (8 b2 + v - d2) mod L).  Reads `in`, writes `out` (float or
+// double); one block of 64 threads per 8x8 image block.
+template <typename OutT>
+__device__ __forceinline__ void dct8_block(const float* __restrict__ in, OutT* __restrict__ out,
+                                           int L, double thr, int mode, int d1, int d2) {
   __shared__ double C[8][8], B[8][8], T[8][8];
   const int u = threadIdx.x >> 3, v = threadIdx.x & 7;
   const int b1 = blockIdx.x / (L / 8), b2 = blockIdx.x % (L / 8);
   C[u][v] = (u == 0 ? sqrt(0.125) : 0.5) * cospi((double)((2 * v + 1) * u) / 16.0);
-  float* px = x + (b1 * 8 + u) * L + b2 * 8 + v;
-  B[u][v] = (double)*px;
+  const int p1 = (b1 * 8 + u - d1 + L) % L, p2 = (b2 * 8 + v - d2 + L) % L;
+  B[u][v] = (double)in[p1 * L + p2];
   __syncthreads();
   double a = 0.0;
 #pragma unroll
@@ -301,9 +343,15 @@ __global__ void __launch_bounds__(64) k_dct8(float* __restrict__ x, int L, doubl
   double X = 0.0;
 #pragma unroll
   for (int k = 0; k < 8; ++k) X += T[u][k] * C[v][k];  // (C B) C^T
-  const bool keep = (u == 0 && v == 0) || fabs(X) > thr;
+  double Xd;
+  if (u == 0 && v == 0)
+    Xd = X;
+  else if (mode == 0)
+    Xd = fabs(X) > thr ? X : 0.0;
+  else
+    Xd = (X > 0.0 ? 1.0 : (X < 0.0 ? -1.0 : 0.0)) * fmax(fabs(X) - thr, 0.0);
   __syncthreads();
-  B[u][v] = keep ? X : 0.0;
+  B[u][v] = Xd;
   __syncthreads();
   a = 0.0;
 #pragma unroll
@@ -313,7 +361,29 @@ __global__ void __launch_bounds__(64) k_dct8(float* __restrict__ x, int L, doubl
   double o = 0.0;
 #pragma unroll
   for (int k = 0; k < 8; ++k) o += T[u][k] * C[k][v];  // (C^T X) C
-  *px = (float)o;
+  out[p1 * L + p2] = (OutT)o;
+}
+
+__global__ void __launch_bounds__(64) k_dct8(float* __restrict__ x, int L, double thr, int mode) {
+  dct8_block<float>(x, x, L, thr, mode, 0, 0);
+}
+
+// Cycle spinning: the block denoiser for all 64 grid offsets (blockIdx.y = offset),
+// each offset's full image into acc[offset][L*L] (float64).
+__global__ void __launch_bounds__(64) k_dct8_spin(const float* __restrict__ x, int L,
+                                                  double thr, int mode,
+                                                  double* __restrict__ acc) {
+  const int d = blockIdx.y;
+  dct8_block<double>(x, acc + (int64_t)d * L * L, L, thr, mode, d / 8, d % 8);
+}
+
+// x[q] = mean over the 64 offsets (fixed order).
+__global__ void k_spin_mean(const double* __restrict__ acc, int S, float* __restrict__ x) {
+  const int q = blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= S) return;
+  double m = 0.0;
+  for (int d = 0; d < 64; ++d) m += acc[(int64_t)d * S + q];
+  x[q] = (float)(m / 64.0);
 }
 
 // out = sum_{k<n} in[k] in float64, one warp, fixed order.
@@ -325,7 +395,50 @@ __global__ void k_sum_f64(const double* __restrict__ in, int n, double* __restri
   if (threadIdx.x == 0) *out = v;
 }
 
+// Algorithm 2 step in device memory (for graph replay): project iff F > 0 and the
+// iteration that just finished is the F-th, with threshold thr * sigma_BM.
+__global__ void __launch_bounds__(64) k_dct8_sched(float* __restrict__ x, int L, double thr,
+                                                   int mode, const DevSched* __restrict__ sc) {
+  const int t = sc->t, F = sc->F;
+  if (F <= 0 || (t + 1) % F != 0) return;
+  dct8_block<float>(x, x, L, thr * sc->sigma_bm, mode, 0, 0);
+}
+__global__ void __launch_bounds__(64) k_dct8_spin_sched(const float* __restrict__ x, int L,
+                                                        double thr, int mode,
+                                                        const DevSched* __restrict__ sc,
+                                                        double* __restrict__ acc) {
+  const int t = sc->t, F = sc->F;
+  if (F <= 0 || (t + 1) % F != 0) return;
+  const int d = blockIdx.y;
+  dct8_block<double>(x, acc + (int64_t)d * L * L, L, thr * sc->sigma_bm, mode, d / 8, d % 8);
+}
+__global__ void k_spin_mean_sched(const double* __restrict__ acc, int S, float* __restrict__ x,
+                                  const DevSched* __restrict__ sc) {
+  const int t = sc->t, F = sc->F;
+  if (F <= 0 || (t + 1) % F != 0) return;
+  const int q = blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= S) return;
+  double m = 0.0;
+  for (int d = 0; d < 64; ++d) m += acc[(int64_t)d * S + q];
+  x[q] = (float)(m / 64.0);
+}
+
+// Advance the schedule after an iteration: t <- t + 1, and decay sigma_BM if this
+// iteration projected (Eq. decaying_function).
+__global__ void k_sched_advance(DevSched* sc) {
+  const int t = sc->t, F = sc->F;
+  if (F > 0 && (t + 1) % F == 0) sc->sigma_bm *= sc->decay;
+  sc->t = t + 1;
+}
+
 }  // namespace
+
+// Number of lag ranges of the b' partial sums: about two blocks per SM.
+int fin_t_splits(const Geom& g, int num_sms) {
+  int n = (int)ceil_div(2 * (int64_t)num_sms, (int64_t)g.K * g.K);
+  if (n > g.l2) n = g.l2;
+  return n < 1 ? 1 : n;
+}
 
 cudaError_t launch_sum_f64(const double* in, int n, double* out, cudaStream_t stream) {
   k_sum_f64<<<1, 32, 0, stream>>>(in, n, out);
@@ -384,16 +497,48 @@ void launch_finalize(srmra_ctx* c, int ll_index) {
   k_fin_counts<<<1, 1024, 0, c->stream>>>(c->cfin, g.Spad, g.S, g.L, g.K, g.l, c->llpart,
                                           c->plan.ll_blocks, c->rho1, c->rho2, c->Ar,
                                           c->ll_hist + ll_index, c->status);
-  const int warps = g.L * g.L;
-  k_fin_x<<<(unsigned)ceil_div(warps, 8), 256, 0, c->stream>>>(
-      c->Zp, c->plan.nparts_z, g.Spad, g.ldy, g.L, g.K, g.l, c->Ar, c->x, c->status);
-  c->launches += 3;
+  const int n_ts = fin_t_splits(g, c->num_sms);
+  const int t_per = (int)ceil_div(g.l2, n_ts);
+  k_fin_b<<<dim3((unsigned)(g.K * g.K), (unsigned)n_ts), 256, 0, c->stream>>>(
+      c->Zp, c->plan.nparts_z, g.Spad, g.ldy, g.L, g.K, g.l, t_per, c->bpart);
+  k_fin_x<<<(unsigned)ceil_div(g.S, 256), 256, 0, c->stream>>>(c->bpart, n_ts, g.L, g.K, g.l,
+                                                                c->Ar, c->x, c->status);
+  c->launches += 4;
+}
+
+void launch_dct_sched(srmra_ctx* c, double thr) {
+  const Geom& g = c->g;
+  const unsigned nb = (unsigned)((g.L / 8) * (g.L / 8));
+  if (g.L % 8 == 0) {
+    if (c->dn_spin && c->dn_acc) {
+      k_dct8_spin_sched<<<dim3(nb, 64), 64, 0, c->stream>>>(c->x, g.L, c->dn_thr, c->dn_mode,
+                                                             c->d_sched, c->dn_acc);
+      k_spin_mean_sched<<<(unsigned)ceil_div(g.S, 256), 256, 0, c->stream>>>(c->dn_acc, g.S,
+                                                                              c->x, c->d_sched);
+      c->launches += 2;
+    } else {
+      k_dct8_sched<<<nb, 64, 0, c->stream>>>(c->x, g.L, c->dn_thr, c->dn_mode, c->d_sched);
+      c->launches++;
+    }
+  }
+  (void)thr;
+  k_sched_advance<<<1, 1, 0, c->stream>>>(c->d_sched);
+  c->launches++;
 }
 
 void launch_dct_denoise(srmra_ctx* c, double sigma_bm, double thr) {
   const Geom& g = c->g;
-  k_dct8<<<(g.L / 8) * (g.L / 8), 64, 0, c->stream>>>(c->x, g.L, thr * sigma_bm);
-  c->launches++;
+  const unsigned nb = (unsigned)((g.L / 8) * (g.L / 8));
+  (void)thr;
+  if (c->dn_spin && c->dn_acc) {
+    k_dct8_spin<<<dim3(nb, 64), 64, 0, c->stream>>>(c->x, g.L, c->dn_thr * sigma_bm,
+                                                    c->dn_mode, c->dn_acc);
+    k_spin_mean<<<(unsigned)ceil_div(g.S, 256), 256, 0, c->stream>>>(c->dn_acc, g.S, c->x);
+    c->launches += 2;
+  } else {
+    k_dct8<<<nb, 64, 0, c->stream>>>(c->x, g.L, c->dn_thr * sigma_bm, c->dn_mode);
+    c->launches++;
+  }
 }
 
 }  // namespace srmra

@@ -380,11 +380,15 @@ void launch_pass1_f32(srmra_ctx* c) {
   c->launches++;
 }
 
+cudaError_t simt_set_attributes() {
+  return cudaFuncSetAttribute(k_p2_f32, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)P2_SMEM_BYTES);
+}
+
 cudaError_t launch_pass2_f32(srmra_ctx* c) {
   static bool attr_done = false;
   if (!attr_done) {
-    cudaError_t e = cudaFuncSetAttribute(k_p2_f32, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)P2_SMEM_BYTES);
+    cudaError_t e = simt_set_attributes();
     if (e != cudaSuccess) return e;
     attr_done = true;
   }

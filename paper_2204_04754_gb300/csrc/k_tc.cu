@@ -76,6 +76,28 @@ struct TcP2Args {
   int* status;
 };
 
+// One problem instance of a (possibly grouped) launch: the tensor maps of its operands
+// and the arguments of both passes.  Kept in device memory; TMA reads the maps there.
+struct TcInst {
+  CUtensorMap tmY, tmYl, tmA256, tmAl256, tmA128, tmAl128, tmYT;
+  TcP1Args p1;
+  TcP2Args p2;
+};
+
+// Instance of global work unit u: the largest k with ustart[k] <= u (ustart ascending,
+// ustart[n] = total units).
+__device__ __forceinline__ int find_inst(const int64_t* __restrict__ ustart, int n, int64_t u) {
+  int lo = 0, hi = n - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (ustart[mid] <= u)
+      lo = mid;
+    else
+      hi = mid - 1;
+  }
+  return lo;
+}
+
 __device__ __forceinline__ uint8_t* align1024(uint8_t* p) {
   return (uint8_t*)(((uintptr_t)p + 1023) & ~(uintptr_t)1023);
 }
@@ -88,9 +110,8 @@ __device__ __forceinline__ void raise_timeout(volatile int* abort, int* status) 
 // ------------------------------------------------------------------------------ pass 1
 template <int NPROD>
 __global__ void __launch_bounds__(TC_THREADS, 1)
-    k_p1_tc(const __grid_constant__ CUtensorMap tmY, const __grid_constant__ CUtensorMap tmYl,
-            const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmAl,
-            const TcP1Args a) {
+    k_p1_tc(const TcInst* __restrict__ insts, const int64_t* __restrict__ ustart, int n_inst,
+            int* status) {
   constexpr int SPK = (NPROD == 3) ? 3 : 2;  // ring slots per k-block
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = align1024(smem_raw);
@@ -124,15 +145,18 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
   __syncthreads();
   tc_fence_after();
   const uint32_t tbase = *tptr;
+  const int64_t total = ustart[n_inst];
 
   if (warp == 0) {
     if (lane == 0) {
-      prefetch_tmap(&tmY);
-      prefetch_tmap(&tmA);
       uint32_t it = 0;
       bool ok = true;
-      for (int64_t u = blockIdx.x; ok && u < a.n_units; u += gridDim.x) {
-        const int iblk = (int)(u / a.groups), grp = (int)(u % a.groups);
+      for (int64_t u = blockIdx.x; ok && u < total; u += gridDim.x) {
+        const int ki = find_inst(ustart, n_inst, u);
+        const TcInst* I = insts + ki;
+        const TcP1Args& a = I->p1;
+        const int64_t lu = u - ustart[ki];
+        const int iblk = (int)(lu / a.groups), grp = (int)(lu % a.groups);
         const int tb = grp * a.tpg, te = min(a.n_stiles, tb + a.tpg);
         for (int tile = tb; ok && tile < te; ++tile)
           for (int kb = 0; ok && kb < a.nk; ++kb)
@@ -146,17 +170,17 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
               uint8_t* dst = smem + st * SLOT;
               if (sl == 0) {
                 mbar_expect_tx(&full[st], NPROD == 3 ? 32768 : 16384);
-                tma_load_2d(dst, &tmY, &full[st], kb * 64, iblk * 128);
-                if (NPROD == 3) tma_load_2d(dst + 16384, &tmYl, &full[st], kb * 64, iblk * 128);
+                tma_load_2d(dst, &I->tmY, &full[st], kb * 64, iblk * 128);
+                if (NPROD == 3) tma_load_2d(dst + 16384, &I->tmYl, &full[st], kb * 64, iblk * 128);
               } else {
                 mbar_expect_tx(&full[st], 32768);
-                tma_load_2d(dst, sl == 1 ? &tmA : &tmAl, &full[st], kb * 64, tile * 256);
+                tma_load_2d(dst, sl == 1 ? &I->tmA256 : &I->tmAl256, &full[st], kb * 64, tile * 256);
               }
               ++it;
             }
       }
       if (!ok) {
-        raise_timeout(abort, a.status);
+        raise_timeout(abort, status);
         // let the loads already issued land before the CTA exits
         const uint32_t lo = it > P1_SLOTS ? it - P1_SLOTS : 0;
         int zero = 0;
@@ -169,8 +193,12 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
       constexpr uint32_t idesc = idesc_bf16_f32(128, 256);
       uint32_t it = 0, tcount = 0;
       bool ok = true;
-      for (int64_t u = blockIdx.x; ok && u < a.n_units; u += gridDim.x) {
-        const int grp = (int)(u % a.groups);
+      for (int64_t u = blockIdx.x; ok && u < total; u += gridDim.x) {
+        const int ki = find_inst(ustart, n_inst, u);
+        const TcInst* I = insts + ki;
+        const TcP1Args& a = I->p1;
+        const int64_t lu = u - ustart[ki];
+        const int grp = (int)(lu % a.groups);
         const int tb = grp * a.tpg, te = min(a.n_stiles, tb + a.tpg);
         for (int tile = tb; ok && tile < te; ++tile) {
           const int b = tcount & 1;
@@ -211,7 +239,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         }
       }
       if (!ok) {
-        raise_timeout(abort, a.status);
+        raise_timeout(abort, status);
         mma_commit(drain);  // all issued MMAs complete before TMEM is released
         int zero = 0;
         mbar_wait(drain, 0, (volatile int*)&zero);
@@ -223,8 +251,12 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     const uint32_t lane_addr = tbase + ((uint32_t)(q * 32) << 16);
     uint32_t tcount = 0;
     bool ok = true;
-    for (int64_t u = blockIdx.x; ok && u < a.n_units; u += gridDim.x) {
-      const int iblk = (int)(u / a.groups), grp = (int)(u % a.groups);
+    for (int64_t u = blockIdx.x; ok && u < total; u += gridDim.x) {
+        const int ki = find_inst(ustart, n_inst, u);
+        const TcInst* I = insts + ki;
+        const TcP1Args& a = I->p1;
+        const int64_t lu = u - ustart[ki];
+      const int iblk = (int)(lu / a.groups), grp = (int)(lu % a.groups);
       const int tb = grp * a.tpg, te = min(a.n_stiles, tb + a.tpg);
       const int64_t i = (int64_t)iblk * 128 + row;
       const float yb = a.ybar[i];
@@ -265,7 +297,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         a.ps[grp * a.Npad + i] = rs;
       }
     }
-    if (!ok) raise_timeout(abort, a.status);
+    if (!ok) raise_timeout(abort, status);
   }
   __syncthreads();
   if (warp == 1) {
@@ -277,9 +309,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
 // ------------------------------------------------------------------------------ pass 2
 template <int NPROD>
 __global__ void __launch_bounds__(TC_THREADS, 1)
-    k_p2_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmAl,
-            const __grid_constant__ CUtensorMap tmY, const __grid_constant__ CUtensorMap tmYl,
-            const __grid_constant__ CUtensorMap tmYT, const TcP2Args a) {
+    k_p2_tc(const TcInst* __restrict__ insts, const int64_t* __restrict__ ustart, int n_inst,
+            int* status) {
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = align1024(smem_raw);
   uint8_t* pbuf = smem + P2_SLOTS * SLOT;  // 2 x 32 KB weight tiles (K-major, SW128)
@@ -295,7 +326,6 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
   uint32_t* tptr = (uint32_t*)(drain + 1);
   volatile int* abort = (volatile int*)(tptr + 1);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int per_split = a.n_stiles * a.n_chunks;
 
   if (threadIdx.x == 0) {
     for (int k = 0; k < P2_SLOTS; ++k) {
@@ -322,12 +352,10 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
   __syncthreads();
   tc_fence_after();
   const uint32_t tbase = *tptr;
+  const int64_t total = ustart[n_inst];
 
   if (warp == 0) {
     if (lane == 0) {
-      prefetch_tmap(&tmA);
-      prefetch_tmap(&tmY);
-      prefetch_tmap(&tmYT);
       uint32_t it = 0;
       bool ok = true;
       auto next_slot = [&](uint32_t bytes) -> uint8_t* {
@@ -339,8 +367,13 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         mbar_expect_tx(&full[st], bytes);
         return smem + st * SLOT;
       };
-      for (int64_t u = blockIdx.x; ok && u < a.n_units; u += gridDim.x) {
-        const int split = (int)(u / per_split), rem = (int)(u % per_split);
+      for (int64_t u = blockIdx.x; ok && u < total; u += gridDim.x) {
+        const int ki = find_inst(ustart, n_inst, u);
+        const TcInst* I = insts + ki;
+        const TcP2Args& a = I->p2;
+        const int64_t lu = u - ustart[ki];
+        const int per_split = a.n_stiles * a.n_chunks;
+        const int split = (int)(lu / per_split), rem = (int)(lu % per_split);
         const int stile = rem / a.n_chunks, chunk = rem % a.n_chunks;
         const int jb0 = split * a.iblk_per_split;
         const int nb = min(a.n_iblk, jb0 + a.iblk_per_split) - jb0;
@@ -351,19 +384,19 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
               if (NPROD == 3) {
                 uint8_t* s0 = next_slot(32768);
                 if (!ok) break;
-                tma_load_2d(s0, &tmA, &full[it % P2_SLOTS], kb * 64, stile * 128);
-                tma_load_2d(s0 + 16384, &tmAl, &full[it % P2_SLOTS], kb * 64, stile * 128);
+                tma_load_2d(s0, &I->tmA128, &full[it % P2_SLOTS], kb * 64, stile * 128);
+                tma_load_2d(s0 + 16384, &I->tmAl128, &full[it % P2_SLOTS], kb * 64, stile * 128);
                 ++it;
                 uint8_t* s1 = next_slot(32768);
                 if (!ok) break;
-                tma_load_2d(s1, &tmY, &full[it % P2_SLOTS], kb * 64, ib);
-                tma_load_2d(s1 + 16384, &tmYl, &full[it % P2_SLOTS], kb * 64, ib);
+                tma_load_2d(s1, &I->tmY, &full[it % P2_SLOTS], kb * 64, ib);
+                tma_load_2d(s1 + 16384, &I->tmYl, &full[it % P2_SLOTS], kb * 64, ib);
                 ++it;
               } else {
                 uint8_t* s0 = next_slot(32768);
                 if (!ok) break;
-                tma_load_2d(s0, &tmA, &full[it % P2_SLOTS], kb * 64, stile * 128);
-                tma_load_2d(s0 + 16384, &tmY, &full[it % P2_SLOTS], kb * 64, ib);
+                tma_load_2d(s0, &I->tmA128, &full[it % P2_SLOTS], kb * 64, stile * 128);
+                tma_load_2d(s0 + 16384, &I->tmY, &full[it % P2_SLOTS], kb * 64, ib);
                 ++it;
               }
             }
@@ -373,14 +406,14 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             for (int h = 0; ok && h < 2; ++h) {
               uint8_t* s0 = next_slot(32768);
               if (!ok) break;
-              tma_load_2d(s0, &tmYT, &full[it % P2_SLOTS], ib + h * 64, chunk * 256);
+              tma_load_2d(s0, &I->tmYT, &full[it % P2_SLOTS], ib + h * 64, chunk * 256);
               ++it;
             }
           }
         }
       }
       if (!ok) {
-        raise_timeout(abort, a.status);
+        raise_timeout(abort, status);
         const uint32_t lo = it > P2_SLOTS ? it - P2_SLOTS : 0;
         int zero = 0;
         for (uint32_t k = lo; k < it; ++k)
@@ -401,8 +434,13 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         }
         return smem + st * SLOT;
       };
-      for (int64_t u = blockIdx.x; ok && u < a.n_units; u += gridDim.x) {
-        const int split = (int)(u / per_split);
+      for (int64_t u = blockIdx.x; ok && u < total; u += gridDim.x) {
+        const int ki = find_inst(ustart, n_inst, u);
+        const TcInst* I = insts + ki;
+        const TcP2Args& a = I->p2;
+        const int64_t lu = u - ustart[ki];
+        const int per_split = a.n_stiles * a.n_chunks;
+        const int split = (int)(lu / per_split);
         const int jb0 = split * a.iblk_per_split;
         const int nb = min(a.n_iblk, jb0 + a.iblk_per_split) - jb0;
         for (int j = 0; ok && j <= nb; ++j) {
@@ -482,7 +520,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         ++uc;
       }
       if (!ok) {
-        raise_timeout(abort, a.status);
+        raise_timeout(abort, status);
         mma_commit(drain);
         int zero = 0;
         mbar_wait(drain, 0, (volatile int*)&zero);
@@ -494,8 +532,13 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     const uint32_t lane_addr = tbase + ((uint32_t)(q * 32) << 16);
     uint32_t sc = 0, pz = 0, uc = 0;
     bool ok = true;
-    for (int64_t u = blockIdx.x; ok && u < a.n_units; u += gridDim.x) {
-      const int split = (int)(u / per_split), rem = (int)(u % per_split);
+    for (int64_t u = blockIdx.x; ok && u < total; u += gridDim.x) {
+        const int ki = find_inst(ustart, n_inst, u);
+        const TcInst* I = insts + ki;
+        const TcP2Args& a = I->p2;
+        const int64_t lu = u - ustart[ki];
+        const int per_split = a.n_stiles * a.n_chunks;
+      const int split = (int)(lu / per_split), rem = (int)(lu % per_split);
       const int stile = rem / a.n_chunks, chunk = rem % a.n_chunks;
       const int jb0 = split * a.iblk_per_split;
       const int nb = min(a.n_iblk, jb0 + a.iblk_per_split) - jb0;
@@ -577,7 +620,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
       }
       ++uc;
     }
-    if (!ok) raise_timeout(abort, a.status);
+    if (!ok) raise_timeout(abort, status);
   }
   __syncthreads();
   if (warp == 1) {
@@ -585,6 +628,400 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     tmem_dealloc(tbase, 512);
   }
 }
+
+// ------------------------------------------------------------------------------ pass 2,
+// cluster form.  A cluster of G CTAs (G = 2..4) shares one 128-shift tile and one range
+// of observation blocks; CTA `rank` owns pixel chunk cg*G + rank of Z'.  In each round
+// every CTA computes the logits of ITS OWN 128-observation block (no CTA recomputes
+// another's), turns them into the fp16 weight tile, and the tile reaches the other CTAs
+// through distributed shared memory: each CTA's producer reserves a ring slot for every
+// peer's tile and mails the slot index to that peer; the peer writes its tile into its
+// own reserved slot and bulk-copies it into the slots the others reserved, completing
+// on their ring barriers.  Each CTA then accumulates Z'[s, its chunk] over the G blocks
+// of the round.  The weights of one (shift tile, observation block) are thus computed
+// once instead of once per pixel chunk.
+constexpr int P2C_SLOTS = 7;
+constexpr int MBOX_DEPTH = 4;
+
+template <int NPROD>
+__global__ void __launch_bounds__(TC_THREADS, 1)
+    k_p2c_tc(const TcInst* __restrict__ insts, const int64_t* __restrict__ ustart, int n_inst,
+             int G, int* status) {
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* smem = align1024(smem_raw);
+  uint64_t* full = (uint64_t*)(smem + P2C_SLOTS * SLOT);
+  uint64_t* empty = full + P2C_SLOTS;
+  uint64_t* sfull = empty + P2C_SLOTS;
+  uint64_t* sempty = sfull + 2;
+  uint64_t* zfull = sempty + 2;
+  uint64_t* zempty = zfull + 1;
+  uint64_t* mfull = zempty + 1;  // [MBOX_DEPTH]: one barrier per mailbox row
+  uint64_t* drain = mfull + MBOX_DEPTH;
+  uint32_t* mbox = (uint32_t*)(drain + 1);  // [MBOX_DEPTH][4] reserved slot indices
+  uint32_t* tptr = mbox + MBOX_DEPTH * 4;
+  volatile int* abort = (volatile int*)(tptr + 1);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const uint32_t rank = cluster_rank();
+  const int64_t cid = blockIdx.x / G, ncl = gridDim.x / G;
+
+  if (threadIdx.x == 0) {
+    for (int k = 0; k < P2C_SLOTS; ++k) {
+      mbar_init(&full[k], 1);
+      mbar_init(&empty[k], 1);
+    }
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(&sfull[b], 1);
+      mbar_init(&sempty[b], 128);
+    }
+    mbar_init(zfull, 1);
+    mbar_init(zempty, 128);
+    for (int k = 0; k < MBOX_DEPTH; ++k) mbar_init(&mfull[k], G);
+    mbar_init(drain, 1);
+    *abort = 0;
+    fence_mbar_init();
+  }
+  if (warp == 1) {
+    tmem_alloc(tptr, 512);
+    tmem_relinquish();
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  cluster_sync_all();  // every CTA's barriers exist before any peer arrives on them
+  const uint32_t tbase = *tptr;
+  const int64_t total = ustart[n_inst];
+
+  if (warp == 0) {
+    if (lane == 0) {
+      uint32_t it = 0, sent[4] = {0, 0, 0, 0};
+      bool ok = true;
+      auto reserve = [&](bool expect_copy) -> int {
+        const int st = it % P2C_SLOTS;
+        if (!mbar_wait(&empty[st], ((it / P2C_SLOTS) & 1) ^ 1, abort)) {
+          ok = false;
+          return -1;
+        }
+        if (expect_copy) mbar_expect_tx(&full[st], 32768);
+        return st;
+      };
+      for (int64_t u = cid; ok && u < total; u += ncl) {
+        const int ki = find_inst(ustart, n_inst, u);
+        const TcInst* I = insts + ki;
+        const TcP2Args& a = I->p2;
+        const int64_t lu = u - ustart[ki];
+        const int ncg = (a.n_chunks + G - 1) / G;
+        const int per_split = a.n_stiles * ncg;
+        const int split = (int)(lu / per_split), rem = (int)(lu % per_split);
+        const int stile = rem / ncg, chunk = (rem % ncg) * G + (int)rank;
+        const bool cvalid = chunk < a.n_chunks;
+        const int jb0 = split * a.iblk_per_split;
+        const int nb = min(a.n_iblk, jb0 + a.iblk_per_split) - jb0;
+        const int rounds = (nb + G - 1) / G;
+        // software-pipelined order: logits of round j, then the weights of round j - 1
+        for (int j = 0; ok && j <= rounds; ++j) {
+          const int r0 = j * G, nq = j < rounds ? min(G, nb - r0) : 0;
+          if ((int)rank < nq) {  // logits of this CTA's own block
+            const int ib = (jb0 + r0 + (int)rank) * 128;
+            for (int kb = 0; ok && kb < a.nk; ++kb) {
+              if (NPROD == 3) {
+                int st = reserve(true);
+                if (!ok) break;
+                tma_load_2d(smem + st * SLOT, &I->tmA128, &full[st], kb * 64, stile * 128);
+                tma_load_2d(smem + st * SLOT + 16384, &I->tmAl128, &full[st], kb * 64,
+                            stile * 128);
+                ++it;
+                st = reserve(true);
+                if (!ok) break;
+                tma_load_2d(smem + st * SLOT, &I->tmY, &full[st], kb * 64, ib);
+                tma_load_2d(smem + st * SLOT + 16384, &I->tmYl, &full[st], kb * 64, ib);
+                ++it;
+              } else {
+                const int st = reserve(true);
+                if (!ok) break;
+                tma_load_2d(smem + st * SLOT, &I->tmA128, &full[st], kb * 64, stile * 128);
+                tma_load_2d(smem + st * SLOT + 16384, &I->tmY, &full[st], kb * 64, ib);
+                ++it;
+              }
+            }
+          }
+          const int rp = (j - 1) * G, nqp = j >= 1 ? min(G, nb - rp) : 0;
+          for (int kq = 0; ok && kq < nqp; ++kq) {
+            // a slot for the weight tile of block rp + kq, filled by CTA kq
+            const int st = reserve(kq != (int)rank);
+            if (!ok) break;
+            // row sent % DEPTH of peer kq's mailbox, and that row's own barrier, so the
+            // arrivals of different rounds can never complete each other's phases
+            const uint32_t row = sent[kq] % MBOX_DEPTH;
+            st_cluster_u32(mapa(smem_u32(mbox + row * 4 + rank), kq), (uint32_t)st);
+            mbar_arrive_cluster(mapa(smem_u32(&mfull[row]), kq));
+            ++sent[kq];
+            ++it;
+            if (cvalid) {
+              const int ib = (jb0 + rp + kq) * 128;
+              for (int h = 0; ok && h < 2; ++h) {
+                const int s2 = reserve(false);
+                if (!ok) break;
+                mbar_expect_tx(&full[s2], 32768);
+                tma_load_2d(smem + s2 * SLOT, &I->tmYT, &full[s2], ib + h * 64, chunk * 256);
+                ++it;
+              }
+            }
+          }
+        }
+      }
+      if (!ok) {
+        raise_timeout(abort, status);
+        const uint32_t lo = it > P2C_SLOTS ? it - P2C_SLOTS : 0;
+        int zero = 0;
+        for (uint32_t k = lo; k < it; ++k)
+          mbar_wait(&full[k % P2C_SLOTS], (k / P2C_SLOTS) & 1, (volatile int*)&zero);
+      }
+    }
+  } else if (warp == 1) {
+    if (lane == 0) {
+      constexpr uint32_t idS = idesc_bf16_f32(128, 128);
+      constexpr uint32_t idZ = idesc_f16_f32(128, 256);
+      uint32_t it = 0, sc = 0, uc = 0;
+      bool ok = true;
+      auto wait_slot = [&]() -> int {
+        const int st = it % P2C_SLOTS;
+        if (!mbar_wait(&full[st], (it / P2C_SLOTS) & 1, abort)) {
+          ok = false;
+          return -1;
+        }
+        return st;
+      };
+      for (int64_t u = cid; ok && u < total; u += ncl) {
+        const int ki = find_inst(ustart, n_inst, u);
+        const TcInst* I = insts + ki;
+        const TcP2Args& a = I->p2;
+        const int64_t lu = u - ustart[ki];
+        const int ncg = (a.n_chunks + G - 1) / G;
+        const int per_split = a.n_stiles * ncg;
+        const int rem = (int)(lu % per_split);
+        const int chunk = (rem % ncg) * G + (int)rank;
+        const bool cvalid = chunk < a.n_chunks;
+        const int split = (int)(lu / per_split);
+        const int jb0 = split * a.iblk_per_split;
+        const int nb = min(a.n_iblk, jb0 + a.iblk_per_split) - jb0;
+        bool first_z = true;
+        const int rounds = (nb + G - 1) / G;
+        for (int j = 0; ok && j <= rounds; ++j) {
+          const int r0 = j * G, nq = j < rounds ? min(G, nb - r0) : 0;
+          if ((int)rank < nq) {
+            const int b = sc & 1;
+            if (!mbar_wait(&sempty[b], ((sc >> 1) & 1) ^ 1, abort)) {
+              ok = false;
+              break;
+            }
+            tc_fence_after();
+            const uint32_t d = tbase + (uint32_t)(b * 128);
+            for (int kb = 0; ok && kb < a.nk; ++kb) {
+              const int stA = wait_slot();
+              if (!ok) break;
+              uint8_t* sA = smem + stA * SLOT;
+              uint8_t* sY = sA + 16384;
+              int stY = stA;
+              if (NPROD == 3) {
+                ++it;
+                stY = wait_slot();
+                if (!ok) break;
+                sY = smem + stY * SLOT;
+              }
+              tc_fence_after();
+              const uint64_t dA = desc_sw128(sA), dY = desc_sw128(sY);
+#pragma unroll
+              for (int k4 = 0; k4 < 4; ++k4) {
+                mma_bf16(d, desc_advance(dA, k4), desc_advance(dY, k4), idS,
+                         (kb > 0 || k4 > 0) ? 1u : 0u);
+                if (NPROD == 3) {
+                  const uint64_t dAl = desc_sw128(sA + 16384), dYl = desc_sw128(sY + 16384);
+                  mma_bf16(d, desc_advance(dA, k4), desc_advance(dYl, k4), idS, 1u);
+                  mma_bf16(d, desc_advance(dAl, k4), desc_advance(dY, k4), idS, 1u);
+                }
+              }
+              mma_commit(&empty[stA]);
+              if (NPROD == 3) mma_commit(&empty[stY]);
+              ++it;
+            }
+            if (!ok) break;
+            mma_commit(&sfull[b]);
+            ++sc;
+          }
+          const int nqp = j >= 1 ? min(G, nb - (j - 1) * G) : 0;
+          for (int kq = 0; ok && kq < nqp; ++kq) {
+            const int stP = wait_slot();
+            if (!ok) break;
+            ++it;
+            if (cvalid) {
+              if (first_z && !mbar_wait(zempty, (uc & 1) ^ 1, abort)) {
+                ok = false;
+                break;
+              }
+              tc_fence_after();
+              const uint32_t dZ = tbase + 256u;
+              for (int h = 0; ok && h < 2; ++h) {
+                const int stT = wait_slot();
+                if (!ok) break;
+                tc_fence_after();
+                const uint64_t dP = desc_sw128(smem + stP * SLOT + h * 16384);
+                const uint64_t dT = desc_sw128(smem + stT * SLOT);
+#pragma unroll
+                for (int k4 = 0; k4 < 4; ++k4)
+                  mma_bf16(dZ, desc_advance(dP, k4), desc_advance(dT, k4), idZ,
+                           (!first_z || h > 0 || k4 > 0) ? 1u : 0u);
+                mma_commit(&empty[stT]);
+                ++it;
+              }
+              first_z = false;
+            }
+            mma_commit(&empty[stP]);
+          }
+        }
+        if (!ok) break;
+        if (cvalid) {
+          mma_commit(zfull);
+          ++uc;
+        }
+      }
+      if (!ok) {
+        raise_timeout(abort, status);
+        mma_commit(drain);
+        int zero = 0;
+        mbar_wait(drain, 0, (volatile int*)&zero);
+      }
+    }
+  } else {
+    const int q = warp & 3;
+    const int row = q * 32 + lane;
+    const uint32_t lane_addr = tbase + ((uint32_t)(q * 32) << 16);
+    uint32_t sc = 0, mr = 0, uc = 0;
+    bool ok = true;
+    for (int64_t u = cid; ok && u < total; u += ncl) {
+      const int ki = find_inst(ustart, n_inst, u);
+      const TcInst* I = insts + ki;
+      const TcP2Args& a = I->p2;
+      const int64_t lu = u - ustart[ki];
+      const int ncg = (a.n_chunks + G - 1) / G;
+      const int per_split = a.n_stiles * ncg;
+      const int split = (int)(lu / per_split), rem = (int)(lu % per_split);
+      const int stile = rem / ncg, cgrp = rem % ncg;
+      const int chunk = cgrp * G + (int)rank;
+      const bool cvalid = chunk < a.n_chunks;
+      const int jb0 = split * a.iblk_per_split;
+      const int nb = min(a.n_iblk, jb0 + a.iblk_per_split) - jb0;
+      const int s = stile * 128 + row;
+      const float cb = a.colb[s], cm = a.colm[s];
+      float cacc = 0.f, zacc = 0.f;
+      for (int r0 = 0; ok && r0 < nb; r0 += G) {
+        const int nq = min(G, nb - r0);
+        if ((int)rank >= nq) continue;
+        const int64_t ib = (int64_t)(jb0 + r0 + (int)rank) * 128;
+        const int b = sc & 1;
+        ok = __all_sync(0xffffffffu, mbar_wait(&sfull[b], (sc >> 1) & 1, abort));
+        if (ok)
+          ok = __all_sync(0xffffffffu,
+                          mbar_wait_cluster(&mfull[mr % MBOX_DEPTH], (mr / MBOX_DEPTH) & 1, abort));
+        if (!ok) break;
+        tc_fence_after();
+        const uint32_t* mrow = mbox + (mr % MBOX_DEPTH) * 4;
+        const int own = (int)mrow[rank];
+        uint8_t* prow = smem + own * SLOT + row * 128;
+#pragma unroll 1
+        for (int c = 0; c < 4; ++c) {
+          float v[32];
+          tmem_ld32(lane_addr + (uint32_t)(b * 128 + c * 32), v);
+          tmem_ld_wait();
+          uint32_t packed[16];
+#pragma unroll
+          for (int e = 0; e < 32; e += 2) {
+            float w2[2];
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+              const int64_t i = ib + c * 32 + e + h;
+              const float ybi = a.ybar[i];
+              const float dd = ybi - cm;
+              const float val = fmaf(v[e + h], a.a2, cb - a.lse2[i]) - a.c2 * dd * dd;
+              const float w = (i < a.N) ? exp2f(val) * W_SCALE : 0.f;
+              w2[h] = __half2float(__float2half_rn(w));
+              cacc += w2[h];
+              zacc = fmaf(w2[h], ybi, zacc);
+            }
+            const __half2 pr = __floats2half2_rn(w2[0], w2[1]);
+            packed[e >> 1] = *reinterpret_cast<const uint32_t*>(&pr);
+          }
+#pragma unroll
+          for (int g4 = 0; g4 < 4; ++g4) {
+            const int col16 = c * 4 + g4;
+            const int kb2 = col16 >> 3, cc = col16 & 7;
+            *reinterpret_cast<uint4*>(prow + kb2 * 16384 + ((cc ^ (row & 7)) << 4)) =
+                make_uint4(packed[4 * g4], packed[4 * g4 + 1], packed[4 * g4 + 2],
+                           packed[4 * g4 + 3]);
+          }
+        }
+        tc_fence_before();
+        mbar_arrive(&sempty[b]);
+        fence_proxy_async_smem();
+        named_bar(1, 128);
+        if (row == 0) {
+          const uint8_t* src = smem + own * SLOT;
+          for (int j = 0; j < G; ++j) {
+            if (j == (int)rank) continue;
+            const int dst = (int)mrow[j];
+            bulk_copy_to_peer(mapa(smem_u32(smem + dst * SLOT), j), src, 32768,
+                              mapa(smem_u32(&full[dst]), j));
+          }
+          bulk_commit();
+          bulk_wait_read0();
+          mbar_arrive(&full[own]);
+        }
+        ++sc;
+        ++mr;
+      }
+      if (!ok) break;
+      if (cvalid) {
+        ok = __all_sync(0xffffffffu, mbar_wait(zfull, uc & 1, abort));
+        if (!ok) break;
+        tc_fence_after();
+        float* zrow = a.Zp + ((int64_t)split * a.Spad + s) * a.ldy;
+#pragma unroll 1
+        for (int c = 0; c < 8; ++c) {
+          float v[32];
+          tmem_ld32(lane_addr + (uint32_t)(256 + c * 32), v);
+          tmem_ld_wait();
+          const int p0 = chunk * 256 + c * 32;
+          if (p0 < a.ldy) {
+#pragma unroll
+            for (int e = 0; e < 32; e += 4)
+              if (p0 + e < a.ldy)
+                *reinterpret_cast<float4*>(zrow + p0 + e) =
+                    make_float4(v[e] * W_UNSCALE, v[e + 1] * W_UNSCALE, v[e + 2] * W_UNSCALE,
+                                v[e + 3] * W_UNSCALE);
+          }
+        }
+        tc_fence_before();
+        mbar_arrive(zempty);
+        ++uc;
+      }
+      if (cgrp == 0) {
+        const int64_t part = (int64_t)split * G + rank;
+        a.cp[part * a.Spad + s] = cacc * W_UNSCALE;
+        a.zbp[part * a.Spad + s] = zacc * W_UNSCALE;
+      }
+    }
+    if (!ok) raise_timeout(abort, status);
+  }
+  __syncthreads();
+  if (warp == 1) {
+    tc_fence_after();
+    tmem_dealloc(tbase, 512);
+  }
+  cluster_sync_all();  // no CTA leaves while a peer may still copy into it
+}
+
+// ring + bookkeeping (25 mbarriers, mailbox, TMEM address, abort flag: < 512 bytes)
+constexpr size_t P2C_SMEM = 1024 + P2C_SLOTS * SLOT + 512;
+static_assert(P2C_SMEM <= 232448, "exceeds the shared memory of one CTA");
 
 constexpr size_t P1_SMEM = 1024 + P1_SLOTS * SLOT + 256;
 constexpr size_t P2_SMEM = 1024 + P2_SLOTS * SLOT + 2 * SLOT + 256;
@@ -686,31 +1123,68 @@ cudaError_t set_smem(K kernel, size_t bytes) {
 
 }  // namespace
 
-void plan_tc(srmra_ctx* c) {
+// Work decomposition of the tensor-core passes.  s1 multiplies the number of shift
+// groups of pass 1 and s2 the number of observation ranges of pass 2: finer units
+// balance a grouped launch better at the price of more partial sums.  The result is
+// clamped to the capacities the context's buffers were sized for.
+void plan_tc(srmra_ctx* c, int s1, int s2) {
   const Geom& g = c->g;
   Plan& p = c->plan;
   const int sms = c->num_sms;
   const int n_st1 = g.Spad / 256;
   const int iblk1 = (int)(g.Npad / 128);
-  int G = (int)ceil_div(4 * (int64_t)sms, iblk1);
-  G = G < 1 ? 1 : (G > n_st1 ? n_st1 : G);
-  p.p1_tiles_per_group = (int)ceil_div(n_st1, G);
+  int groups = (int)ceil_div(4 * (int64_t)sms, iblk1) * s1;
+  groups = groups < 1 ? 1 : (groups > n_st1 ? n_st1 : groups);
+  if (p.cap_p1_groups > 0 && groups > p.cap_p1_groups) groups = p.cap_p1_groups;
+  p.p1_tiles_per_group = (int)ceil_div(n_st1, groups);
   p.p1_groups = (int)ceil_div(n_st1, p.p1_tiles_per_group);
 
   const int n_st2 = g.Spad / 128;
   const int chunks = (int)ceil_div(g.l2, 256);
   const int n_iblk = (int)(g.Npad / 128);
   const int64_t per_split = (int64_t)n_st2 * chunks;
-  int ns = (int)((4 * (int64_t)sms + per_split / 2) / per_split);
+  int ns = (int)((4 * (int64_t)sms + per_split / 2) / per_split) * s2;
   ns = ns < 1 ? 1 : (ns > n_iblk ? n_iblk : ns);
-  if (ns > 32) ns = 32;
+  if (ns > 64) ns = 64;
+  if (p.cap_nsplit > 0 && ns > p.cap_nsplit) ns = p.cap_nsplit;
   p.p2_iblk_per_split = (int)ceil_div(n_iblk, ns);
   p.p2_nsplit = (int)ceil_div(n_iblk, p.p2_iblk_per_split);
-  p.p2_gc = 1;
-  p.p2_chunk_groups = chunks;
+  // cluster size of pass 2: CTAs that share each weight tile, one pixel chunk each
+  int G = 1;
+  if (chunks > 1 && !c->no_cluster) {
+    if (chunks % 4 == 0)
+      G = 4;
+    else if (chunks % 3 == 0)
+      G = 3;
+    else if (chunks % 2 == 0)
+      G = 2;
+    else
+      G = chunks < 4 ? chunks : 4;
+  }
+  p.p2_gc = G;
+  p.p2_chunk_groups = (int)ceil_div(chunks, G);
   p.nparts_z = p.p2_nsplit;
-  p.nparts_c = p.p2_nsplit;
+  p.nparts_c = p.p2_nsplit * G;
   p.ll_blocks = (int)ceil_div(g.Npad, 256);
+}
+
+cudaError_t tc_replan(srmra_ctx* c, int s1, int s2) {
+  plan_tc(c, s1, s2);
+  return tc_upload_inst(c);
+}
+
+cudaError_t tc_set_attributes(int prec) {
+  cudaError_t e;
+  if (prec == SRMRA_BF16X3) {
+    e = set_smem(k_p1_tc<3>, P1_SMEM);
+    if (e == cudaSuccess) e = set_smem(k_p2_tc<3>, P2_SMEM);
+    if (e == cudaSuccess) e = set_smem(k_p2c_tc<3>, P2C_SMEM);
+  } else {
+    e = set_smem(k_p1_tc<1>, P1_SMEM);
+    if (e == cudaSuccess) e = set_smem(k_p2_tc<1>, P2_SMEM);
+    if (e == cudaSuccess) e = set_smem(k_p2c_tc<1>, P2C_SMEM);
+  }
+  return e;
 }
 
 cudaError_t prep_obs_tc(srmra_ctx* c) {
@@ -734,7 +1208,7 @@ cudaError_t prep_obs_tc(srmra_ctx* c) {
          make_map(&c->tmAl128, c->Al, g.ldk, g.Spad, g.ldk, 128) &&
          make_map(&c->tmAl256, c->Al, g.ldk, g.Spad, g.ldk, 256);
   if (!ok) return cudaErrorInvalidValue;
-  return cudaSuccess;
+  return tc_upload_inst(c);
 }
 
 void launch_templates_tc(srmra_ctx* c) {
@@ -746,11 +1220,22 @@ void launch_templates_tc(srmra_ctx* c) {
   c->launches++;
 }
 
-cudaError_t launch_pass1_tc(srmra_ctx* c) {
+namespace {
+
+// Fills the descriptor of one context (arguments of both passes and its tensor maps).
+void fill_inst(const srmra_ctx* c, TcInst* I) {
   const Geom& g = c->g;
   const Plan& p = c->plan;
   const LogitScalars ls = logit_scalars(g);
-  TcP1Args a;
+  memset(I, 0, sizeof(TcInst));
+  I->tmY = c->tmY128;
+  I->tmYl = (c->prec == SRMRA_BF16X3) ? c->tmYl128 : c->tmY128;
+  I->tmA256 = c->tmA256;
+  I->tmAl256 = (c->prec == SRMRA_BF16X3) ? c->tmAl256 : c->tmA256;
+  I->tmA128 = c->tmA128;
+  I->tmAl128 = (c->prec == SRMRA_BF16X3) ? c->tmAl128 : c->tmA128;
+  I->tmYT = c->tmYT;
+  TcP1Args& a = I->p1;
   a.nk = (int)ceil_div(g.l2, 64);
   a.n_stiles = g.Spad / 256;
   a.groups = p.p1_groups;
@@ -766,78 +1251,166 @@ cudaError_t launch_pass1_tc(srmra_ctx* c) {
   a.pm = c->pm;
   a.ps = c->ps;
   a.status = c->status;
-  const unsigned grid = (unsigned)(a.n_units < c->num_sms ? a.n_units : c->num_sms);
-  cudaError_t e;
-  if (c->prec == SRMRA_BF16X3) {
-    static bool once = false;
-    if (!once) {
-      e = set_smem(k_p1_tc<3>, P1_SMEM);
-      if (e != cudaSuccess) return e;
-      once = true;
-    }
-    k_p1_tc<3><<<grid, TC_THREADS, P1_SMEM, c->stream>>>(c->tmY128, c->tmYl128, c->tmA256,
-                                                         c->tmAl256, a);
-  } else {
-    static bool once = false;
-    if (!once) {
-      e = set_smem(k_p1_tc<1>, P1_SMEM);
-      if (e != cudaSuccess) return e;
-      once = true;
-    }
-    k_p1_tc<1><<<grid, TC_THREADS, P1_SMEM, c->stream>>>(c->tmY128, c->tmY128, c->tmA256,
-                                                         c->tmA256, a);
+  TcP2Args& b = I->p2;
+  b.nk = a.nk;
+  b.n_stiles = g.Spad / 128;
+  b.n_chunks = (int)ceil_div(g.l2, 256);
+  b.n_iblk = (int)(g.Npad / 128);
+  b.iblk_per_split = p.p2_iblk_per_split;
+  // work units of pass 2: (shift tile, chunk group, observation range); a chunk group is
+  // one pixel chunk for the per-chunk kernel and G chunks for the cluster kernel
+  b.n_units = (int64_t)b.n_stiles * p.p2_chunk_groups * p.p2_nsplit;
+  b.N = g.N;
+  b.Spad = g.Spad;
+  b.ldy = g.ldy;
+  b.ybar = c->ybar;
+  b.colb = c->colb;
+  b.colm = c->colm;
+  b.lse2 = c->lse2;
+  b.a2 = ls.a2;
+  b.c2 = ls.c2;
+  b.Zp = c->Zp;
+  b.cp = c->cp;
+  b.zbp = c->zbp;
+  b.status = c->status;
+}
+
+// Co-resident clusters of G CTAs of the clustered pass-2 kernel (queried once per G).
+template <int NPROD>
+int max_clusters(int G, int num_sms) {
+  static int cache[5] = {0, 0, 0, 0, 0};
+  if (cache[G] > 0) return cache[G];
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)(G * (num_sms / G)), 1, 1);
+  cfg.blockDim = dim3(TC_THREADS, 1, 1);
+  cfg.dynamicSmemBytes = P2C_SMEM;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = (unsigned)G;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  int n = 0;
+  if (cudaOccupancyMaxActiveClusters(&n, k_p2c_tc<NPROD>, &cfg) != cudaSuccess || n < 1) {
+    cudaGetLastError();
+    n = num_sms / G / 2 > 0 ? num_sms / G / 2 : 1;
   }
-  c->launches++;
+  cache[G] = n;
+  return n;
+}
+
+template <int NPROD>
+cudaError_t launch_cluster_p2(int G, const TcInst* d_insts, const int64_t* d_ustart, int n,
+                              int64_t total, int* status, cudaStream_t stream, int num_sms) {
+  static bool attr = false;
+  if (!attr) {
+    cudaError_t e = set_smem(k_p2c_tc<NPROD>, P2C_SMEM);
+    if (e != cudaSuccess) return e;
+    attr = true;
+  }
+  int ncl = max_clusters<NPROD>(G, num_sms);
+  if (total < ncl) ncl = (int)total;
+  if (ncl < 1) return cudaSuccess;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)(G * ncl), 1, 1);
+  cfg.blockDim = dim3(TC_THREADS, 1, 1);
+  cfg.dynamicSmemBytes = P2C_SMEM;
+  cfg.stream = stream;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeClusterDimension;
+  at[0].val.clusterDim.x = (unsigned)G;
+  at[0].val.clusterDim.y = 1;
+  at[0].val.clusterDim.z = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, k_p2c_tc<NPROD>, d_insts, d_ustart, n, G, status);
+}
+
+template <int NPROD>
+cudaError_t launch_group(int pass, const TcInst* d_insts, const int64_t* d_ustart, int n,
+                         int64_t total, int* status, cudaStream_t stream, int num_sms) {
+  static bool attr1 = false, attr2 = false;
+  cudaError_t e = cudaSuccess;
+  const unsigned grid = (unsigned)(total < num_sms ? total : num_sms);
+  if (grid == 0) return cudaSuccess;
+  if (pass == 1) {
+    if (!attr1) {
+      e = set_smem(k_p1_tc<NPROD>, P1_SMEM);
+      if (e != cudaSuccess) return e;
+      attr1 = true;
+    }
+    k_p1_tc<NPROD><<<grid, TC_THREADS, P1_SMEM, stream>>>(d_insts, d_ustart, n, status);
+  } else {
+    if (!attr2) {
+      e = set_smem(k_p2_tc<NPROD>, P2_SMEM);
+      if (e != cudaSuccess) return e;
+      attr2 = true;
+    }
+    k_p2_tc<NPROD><<<grid, TC_THREADS, P2_SMEM, stream>>>(d_insts, d_ustart, n, status);
+  }
   return cudaGetLastError();
 }
 
-cudaError_t launch_pass2_tc(srmra_ctx* c) {
-  const Geom& g = c->g;
-  const Plan& p = c->plan;
-  const LogitScalars ls = logit_scalars(g);
-  TcP2Args a;
-  a.nk = (int)ceil_div(g.l2, 64);
-  a.n_stiles = g.Spad / 128;
-  a.n_chunks = (int)ceil_div(g.l2, 256);
-  a.n_iblk = (int)(g.Npad / 128);
-  a.iblk_per_split = p.p2_iblk_per_split;
-  a.n_units = (int64_t)a.n_stiles * a.n_chunks * p.p2_nsplit;
-  a.N = g.N;
-  a.Spad = g.Spad;
-  a.ldy = g.ldy;
-  a.ybar = c->ybar;
-  a.colb = c->colb;
-  a.colm = c->colm;
-  a.lse2 = c->lse2;
-  a.a2 = ls.a2;
-  a.c2 = ls.c2;
-  a.Zp = c->Zp;
-  a.cp = c->cp;
-  a.zbp = c->zbp;
-  a.status = c->status;
-  const unsigned grid = (unsigned)(a.n_units < c->num_sms ? a.n_units : c->num_sms);
-  cudaError_t e;
-  if (c->prec == SRMRA_BF16X3) {
-    static bool once = false;
-    if (!once) {
-      e = set_smem(k_p2_tc<3>, P2_SMEM);
-      if (e != cudaSuccess) return e;
-      once = true;
-    }
-    k_p2_tc<3><<<grid, TC_THREADS, P2_SMEM, c->stream>>>(c->tmA128, c->tmAl128, c->tmY128,
-                                                         c->tmYl128, c->tmYT, a);
-  } else {
-    static bool once = false;
-    if (!once) {
-      e = set_smem(k_p2_tc<1>, P2_SMEM);
-      if (e != cudaSuccess) return e;
-      once = true;
-    }
-    k_p2_tc<1><<<grid, TC_THREADS, P2_SMEM, c->stream>>>(c->tmA128, c->tmA128, c->tmY128,
-                                                         c->tmY128, c->tmYT, a);
-  }
+}  // namespace
+
+size_t tc_inst_bytes() { return sizeof(TcInst); }
+
+void tc_fill_inst(const srmra_ctx* c, void* host_dst) { fill_inst(c, (TcInst*)host_dst); }
+
+int64_t tc_units(const srmra_ctx* c, int pass) {
+  TcInst I;
+  fill_inst(c, &I);
+  return pass == 1 ? I.p1.n_units : I.p2.n_units;
+}
+
+cudaError_t tc_launch_group_p2(int G, int prec, const void* d_insts, const int64_t* d_ustart,
+                               int n, int64_t total, int* status, cudaStream_t stream,
+                               int num_sms) {
+  const TcInst* insts = (const TcInst*)d_insts;
+  if (G <= 1)
+    return tc_launch_group(2, prec, d_insts, d_ustart, n, total, status, stream, num_sms);
+  if (prec == SRMRA_BF16X3)
+    return launch_cluster_p2<3>(G, insts, d_ustart, n, total, status, stream, num_sms);
+  return launch_cluster_p2<1>(G, insts, d_ustart, n, total, status, stream, num_sms);
+}
+
+cudaError_t tc_launch_group(int pass, int prec, const void* d_insts, const int64_t* d_ustart,
+                            int n, int64_t total, int* status, cudaStream_t stream,
+                            int num_sms) {
+  const TcInst* insts = (const TcInst*)d_insts;
+  if (prec == SRMRA_BF16X3)
+    return launch_group<3>(pass, insts, d_ustart, n, total, status, stream, num_sms);
+  return launch_group<1>(pass, insts, d_ustart, n, total, status, stream, num_sms);
+}
+
+// The context's own descriptor (a group of one) in device memory, uploaded once.
+cudaError_t tc_upload_inst(srmra_ctx* c) {
+  c->h_inst.resize(sizeof(TcInst) + 64);
+  TcInst* I = (TcInst*)(((uintptr_t)c->h_inst.data() + 63) & ~(uintptr_t)63);
+  fill_inst(c, I);
+  c->h_ustart[0] = 0;
+  c->h_ustart[1] = I->p1.n_units;
+  c->h_ustart[2] = 0;
+  c->h_ustart[3] = I->p2.n_units;
+  cudaError_t e = cudaMemcpyAsync(c->d_inst, I, sizeof(TcInst), cudaMemcpyHostToDevice,
+                                  c->stream);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(c->d_ustart, c->h_ustart, sizeof(c->h_ustart), cudaMemcpyHostToDevice,
+                        c->stream);
+  return e;
+}
+
+cudaError_t launch_pass1_tc(srmra_ctx* c) {
   c->launches++;
-  return cudaGetLastError();
+  return tc_launch_group(1, c->prec, c->d_inst, c->d_ustart, 1, c->h_ustart[1], c->status,
+                         c->stream, c->num_sms);
+}
+
+cudaError_t launch_pass2_tc(srmra_ctx* c) {
+  c->launches++;
+  return tc_launch_group_p2(c->plan.p2_gc, c->prec, c->d_inst, c->d_ustart + 2, 1,
+                            c->h_ustart[3], c->status, c->stream, c->num_sms);
 }
 
 }  // namespace srmra

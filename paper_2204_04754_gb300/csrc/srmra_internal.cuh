@@ -55,6 +55,15 @@ struct LogitScalars {
   float c2;
 };
 
+// Algorithm 2 schedule of one context kept in device memory while a batch replays its
+// iteration graph.
+struct DevSched {
+  int t;             // EM iterations done
+  int F;             // projection cadence (0 = none)
+  double sigma_bm;   // current denoiser level
+  double decay;      // sigma_BM <- decay * sigma_BM after each projection
+};
+
 struct Plan {
   int p1_groups = 1;        // shift groups per observation tile in pass 1
   int p1_tiles_per_group = 1;
@@ -65,6 +74,8 @@ struct Plan {
   int nparts_c = 1;         // number of partial c / zb slices
   int nparts_z = 1;         // number of partial Z slices
   int ll_blocks = 1;        // blocks of the lse-combine kernel
+  int cap_p1_groups = 0;    // capacity of the pass-1 partial buffers (0 = unbounded)
+  int cap_nsplit = 0;       // capacity of the pass-2 partial buffers (0 = unbounded)
 };
 
 }  // namespace srmra
@@ -89,6 +100,10 @@ struct srmra_ctx {
   __nv_bfloat16* Ah = nullptr;   // [Spad][ldk] centred templates, bf16 hi
   __nv_bfloat16* Al = nullptr;   // [Spad][ldk] bf16 lo (split form only)
   CUtensorMap tmY128, tmYl128, tmYT, tmA128, tmAl128, tmA256, tmAl256;
+  void* d_inst = nullptr;           // this context's launch descriptor (tensor-core form)
+  int64_t* d_ustart = nullptr;      // [4] unit prefix sums of pass 1 and pass 2
+  int64_t h_ustart[4] = {0, 0, 0, 0};
+  std::vector<unsigned char> h_inst;
 
   // --- estimate theta_t
   float* x = nullptr;      // [L*L]
@@ -110,14 +125,24 @@ struct srmra_ctx {
   float* Zp = nullptr;     // [nparts_z][Spad][ldy] partial sum_i w y'_i
   float* cp = nullptr;     // [nparts_c][Spad] partial sum_i w
   float* zbp = nullptr;    // [nparts_c][Spad] partial sum_i w ybar_i
-  double* cfin = nullptr;  // [Spad] c_s of the last E-step
+  double* cfin = nullptr;  // [2*Spad] c_s and zb_s of the last E-step
+  float* bpart = nullptr;  // [fin_t_splits][K*K][l2] partial b' per lag range
   double* Ar = nullptr;    // [K*K] coverage per sub-image, then ZB per sub-image [K*K]
   double* ll_hist = nullptr;  // [ll_cap]
   int ll_cap = 0;
   int* status = nullptr;   // device status word
+  srmra::DevSched* d_sched = nullptr;  // Algorithm 2 schedule for graph replay
   bool have_estep = false;
 
   int64_t launches = 0;
+  int64_t device_bytes = 0;   // device memory held by this context
+  bool no_cluster = false;    // force the per-chunk pass-2 kernel (SRMRA_FLAG_NO_CLUSTER)
+  int sched_F = 0;            // Algorithm 2 cadence used by batches with F < 0
+  int dn_mode = 0;            // built-in denoiser: 0 hard, 1 soft threshold
+  bool dn_spin = false;       // average over the 64 block-grid offsets
+  double dn_thr = 2.7;        // threshold multiplier of sigma_BM
+  double* dn_acc = nullptr;   // [64][L*L] per-offset results (cycle spinning)
+  double sched_decay = 0.93303299153680741598;  // 2^{-1/10}
   std::string err;
   // per-phase timing (srmra_profile)
   bool profiling = false;
@@ -135,18 +160,34 @@ void launch_prep_iter(srmra_ctx* c);           // sub-image stats, column terms,
 void launch_lse_combine(srmra_ctx* c, int groups);
 void launch_finalize(srmra_ctx* c, int ll_index);
 void launch_dct_denoise(srmra_ctx* c, double sigma_bm, double thr);
+void launch_dct_sched(srmra_ctx* c, double thr);  // projection from the device schedule
 LogitScalars logit_scalars(const Geom& g);
 cudaError_t launch_sum_f64(const double* in, int n, double* out, cudaStream_t stream);
+int fin_t_splits(const Geom& g, int num_sms);
 
 // ---- k_tc.cu (tensor-core forms)
-void plan_tc(srmra_ctx* c);
+void plan_tc(srmra_ctx* c, int s1 = 1, int s2 = 1);
+cudaError_t tc_replan(srmra_ctx* c, int s1, int s2);
+cudaError_t tc_set_attributes(int prec);
 cudaError_t prep_obs_tc(srmra_ctx* c);
 void launch_templates_tc(srmra_ctx* c);
 cudaError_t launch_pass1_tc(srmra_ctx* c);
 cudaError_t launch_pass2_tc(srmra_ctx* c);
+cudaError_t tc_upload_inst(srmra_ctx* c);
+size_t tc_inst_bytes();
+void tc_fill_inst(const srmra_ctx* c, void* host_dst);
+int64_t tc_units(const srmra_ctx* c, int pass);
+cudaError_t tc_launch_group(int pass, int prec, const void* d_insts, const int64_t* d_ustart,
+                            int n, int64_t total, int* status, cudaStream_t stream,
+                            int num_sms);
+// pass 2 for instances with cluster size G (G = 1: the per-chunk kernel)
+cudaError_t tc_launch_group_p2(int G, int prec, const void* d_insts, const int64_t* d_ustart,
+                               int n, int64_t total, int* status, cudaStream_t stream,
+                               int num_sms);
 
 // ---- k_simt.cu (float32 form)
 void plan_simt(srmra_ctx* c);
+cudaError_t simt_set_attributes();
 void launch_pass1_f32(srmra_ctx* c);
 cudaError_t launch_pass2_f32(srmra_ctx* c);
 

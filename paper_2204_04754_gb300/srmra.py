@@ -71,6 +71,27 @@ def lib() -> ctypes.CDLL:
         "srmra_profile": (c_int32, [c_void_p, c_int32]),
         "srmra_profile_read": (c_int32, [c_void_p, c_void_p, c_void_p]),
         "srmra_destroy": (None, [c_void_p]),
+        "srmra_batch_create": (c_int32, [c_void_p, c_int32, c_uint32, P(c_void_p)]),
+        "srmra_batch_solve": (c_int32, [c_void_p, c_int32, c_int32, c_double, c_double,
+                                        c_void_p]),
+        "srmra_batch_tuning": (c_int32, [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]),
+        "srmra_batch_destroy": (None, [c_void_p]),
+        "srmra_batch_pass_ms": (c_int32, [c_void_p, c_void_p, c_void_p]),
+        "srmra_batch_last_error": (c_char_p, [c_void_p]),
+        "srmra_em_iter_batch": (c_int32, [c_void_p, c_int32, c_int32]),
+        "srmra_set_schedule": (c_int32, [c_void_p, c_int32, c_double, c_double]),
+        "srmra_set_denoiser": (c_int32, [c_void_p, c_int32, c_double, c_int32]),
+        "srmra_estimate_device_bytes": (c_int32, [P(srmra_params), P(c_int64)]),
+        "srmra_device_bytes": (c_int32, [c_void_p, P(c_int64)]),
+        "srmra_server_create": (c_int32, [c_int64, c_int32, c_int32, c_void_p, P(c_void_p)]),
+        "srmra_server_submit": (c_int32, [c_void_p, P(srmra_params), c_void_p, c_void_p,
+                                          c_int32, c_int32, c_double, c_double, P(c_int64)]),
+        "srmra_server_step": (c_int32, [c_void_p, P(c_int32), P(c_int32), P(c_int32)]),
+        "srmra_server_result": (c_int32, [c_void_p, c_int64, P(c_int32), c_void_p, c_void_p,
+                                          c_void_p, c_void_p, c_void_p]),
+        "srmra_server_memory": (c_int32, [c_void_p, P(c_int64), P(c_int64)]),
+        "srmra_server_destroy": (None, [c_void_p]),
+        "srmra_server_last_error": (c_char_p, [c_void_p]),
         "srmra_last_error": (c_char_p, [c_void_p]),
         "srmra_version": (c_char_p, []),
     }
@@ -171,6 +192,50 @@ def srmra_version() -> str:
     return lib().srmra_version().decode()
 
 
+SRMRA_BATCH_AUTOTUNE = 1
+SRMRA_BATCH_NO_GRAPH = 2
+
+
+def _bcheck(st: int, batch=None):
+    if st != SRMRA_OK:
+        msg = lib().srmra_batch_last_error(batch)
+        raise SrmraError(st, msg.decode() if msg else "")
+
+
+def _ctx_array(ctxs):
+    arr = (c_void_p * len(ctxs))(*ctxs)
+    return arr
+
+
+def srmra_batch_create(ctxs, flags: int = 0) -> int:
+    out = c_void_p()
+    arr = _ctx_array(ctxs)
+    _bcheck(lib().srmra_batch_create(arr, len(ctxs), flags, byref(out)), None)
+    return out.value
+
+
+def srmra_batch_solve(batch: int, iters: int, F: int, sigma_bm1: float, decay: float,
+                      loglik_last=None) -> None:
+    _bcheck(lib().srmra_batch_solve(batch, iters, F, sigma_bm1, decay, _ptr(loglik_last)),
+            batch)
+
+
+def srmra_batch_tuning(batch: int):
+    a, b, c = c_int32(), c_int32(), c_int32()
+    ms = c_double()
+    _bcheck(lib().srmra_batch_tuning(batch, byref(a), byref(b), byref(c), byref(ms)), batch)
+    return dict(p1_scale=a.value, p2_scale=b.value, order=c.value, ms=ms.value)
+
+
+def srmra_batch_destroy(batch: int) -> None:
+    lib().srmra_batch_destroy(batch)
+
+
+def srmra_em_iter_batch(ctxs, n_iters: int) -> None:
+    arr = _ctx_array(ctxs)
+    _bcheck(lib().srmra_em_iter_batch(arr, len(ctxs), n_iters), None)
+
+
 # ----------------------------------------------------------------------------- wrapper
 
 class Solver:
@@ -218,6 +283,11 @@ class Solver:
             fn = DENOISER_FN(denoiser)
             self._fn = fn
         srmra_project(self.ctx, sigma_bm, fn, None)
+
+    def set_denoiser(self, mode: str = "hard", threshold: float = 2.7, spin: bool = False):
+        """Built-in denoiser: 'hard' or 'soft' threshold, optional cycle spinning."""
+        m = {"hard": 0, "soft": 1}[mode]
+        _check(lib().srmra_set_denoiser(self.ctx, m, float(threshold), int(bool(spin))), self.ctx)
 
     def state(self):
         x = np.empty((self.L, self.L), np.float32)
@@ -268,3 +338,108 @@ class Solver:
 
     def __exit__(self, *a):
         self.close()
+
+
+class Batch:
+    """Several :class:`Solver` problems advanced together (grouped launches, CUDA graph)."""
+
+    def __init__(self, solvers, autotune: bool = False, graph: bool = True):
+        self.solvers = list(solvers)
+        flags = (SRMRA_BATCH_AUTOTUNE if autotune else 0) | (0 if graph else SRMRA_BATCH_NO_GRAPH)
+        self.handle = srmra_batch_create([s.ctx for s in self.solvers], flags)
+
+    def solve(self, iters: int, F: int, sigma_bm1: float = 1.0, decay: float = 2.0 ** -0.1):
+        out = np.empty(len(self.solvers))
+        srmra_batch_solve(self.handle, iters, F, sigma_bm1, decay, out)
+        return out
+
+    def tuning(self):
+        return srmra_batch_tuning(self.handle)
+
+    def pass_ms(self):
+        """Device ms of the grouped pass 1 and pass 2 of the most recent iteration."""
+        a, b = c_double(), c_double()
+        _bcheck(lib().srmra_batch_pass_ms(self.handle, byref(a), byref(b)), self.handle)
+        return a.value, b.value
+
+    def close(self):
+        if getattr(self, "handle", None):
+            srmra_batch_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def srmra_estimate_device_bytes(L: int, K: int, N: int, sigma: float, prec: str = "fp32") -> int:
+    out = c_int64()
+    p = srmra_params(L, K, N, sigma, PRECISIONS[prec], 0)
+    _check(lib().srmra_estimate_device_bytes(byref(p), byref(out)), None)
+    return out.value
+
+
+class Server:
+    """Continuous-batching request server (see include/srmra.h)."""
+
+    def __init__(self, budget_bytes: int, max_active: int, prec: str = "bf16x3",
+                 stream: int = 0):
+        out = c_void_p()
+        self.prec = prec
+        st = lib().srmra_server_create(int(budget_bytes), int(max_active), PRECISIONS[prec],
+                                       c_void_p(stream or None), byref(out))
+        self._scheck(st, None)
+        self.handle = out.value
+
+    def _scheck(self, st, h):
+        if st != SRMRA_OK:
+            msg = lib().srmra_server_last_error(h)
+            raise SrmraError(st, msg.decode() if msg else "")
+
+    def submit(self, L, K, sigma, y, iters: int, F: int = 1, sigma_bm1: float = 1.0,
+               decay: float = 2.0 ** -0.1, x0=None) -> int:
+        y = np.ascontiguousarray(y, np.float32)
+        x0 = None if x0 is None else np.ascontiguousarray(x0, np.float32)
+        p = srmra_params(int(L), int(K), int(y.shape[0]), float(sigma), PRECISIONS[self.prec], 0)
+        rid = c_int64()
+        self._scheck(lib().srmra_server_submit(self.handle, byref(p), _ptr(y), _ptr(x0),
+                                               int(iters), int(F), float(sigma_bm1),
+                                               float(decay), byref(rid)), self.handle)
+        return rid.value
+
+    def step(self):
+        a, b, c = c_int32(), c_int32(), c_int32()
+        self._scheck(lib().srmra_server_step(self.handle, byref(a), byref(b), byref(c)),
+                     self.handle)
+        return a.value, b.value, c.value
+
+    def result(self, rid: int, L: int):
+        state = c_int32()
+        x = np.empty((L, L), np.float32)
+        r1 = np.empty(L)
+        r2 = np.empty(L)
+        ll = c_double()
+        t = np.empty(3)
+        st = lib().srmra_server_result(self.handle, rid, byref(state), _ptr(x), _ptr(r1),
+                                       _ptr(r2), byref(ll), _ptr(t))
+        self._scheck(st, self.handle)
+        return dict(state=state.value, x=x, rho1=r1, rho2=r2, loglik=ll.value,
+                    queue_ms=t[0], run_ms=t[1], latency_ms=t[2])
+
+    def memory(self):
+        u, b = c_int64(), c_int64()
+        self._scheck(lib().srmra_server_memory(self.handle, byref(u), byref(b)), self.handle)
+        return u.value, b.value
+
+    def close(self):
+        if getattr(self, "handle", None):
+            lib().srmra_server_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -164,6 +164,10 @@ WORKLOADS = {
 }
 
 
+WORKLOADS["batched_64"] = dict(count=64, iters=30, F=1, config=4, prec="bf16x3")
+WORKLOADS["serve"] = dict(rate=50.0, iters=30, F=1, config=5, prec="bf16x3")
+
+
 def workload_problem(name: str, N: int | None = None, instance: int = 0) -> Problem:
     """Build the seeded problem of a named workload (optionally with fewer observations)."""
     w = WORKLOADS[name]

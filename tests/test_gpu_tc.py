@@ -115,3 +115,20 @@ def test_precision_workload_full_size_sampled(S, name):
     assert abs(r1.sum() - 1) < 1e-12 and abs(r2.sum() - 1) < 1e-12
     assert abs(c.sum() - p.N) < 1e-3 * p.N
     assert np.all(np.isfinite(x))
+
+
+@pytest.mark.parametrize("L,K,N,sigma", [(64, 2, 900, 0.3), (48, 1, 400, 0.8), (96, 4, 600, 0.5)])
+def test_cluster_and_per_chunk_pass2_agree(S, L, K, N, sigma):
+    """The cluster form of pass 2 (weights computed once per observation block and
+    shared through distributed shared memory) and the per-chunk form (weights
+    recomputed for every pixel chunk) give the same iteration."""
+    p = synth.make_problem(L, K, N, sigma, seed=synth.seed_for(3, 900 + L))
+    out = []
+    for flags in (0, 2):  # 2 = SRMRA_FLAG_NO_CLUSTER
+        s = S.Solver(p.L, p.K, p.sigma, p.y, prec="bf16x3", x0=p.x0, rho1=p.rho1_0,
+                     rho2=p.rho2_0, flags=flags)
+        s.solve(2, 1)
+        out.append(s.state())
+        s.close()
+    assert rel(out[0][0], out[1][0]) < 1e-6
+    assert rel(out[0][1], out[1][1]) < 1e-6 and rel(out[0][2], out[1][2]) < 1e-6

@@ -357,3 +357,45 @@ def test_error_metric_brute_force_vs_fft():
     e2 = FO.error_metric_fft(O.shift(xh, 2, 9), x)
     assert abs(e1 - e2) < 1e-12 and e1 > 0.01
     assert abs(O.snr(np.ones((4, 4)), 0.5) - 4.0) < 1e-15
+
+
+def test_soft_threshold_is_the_l1_prox_and_nonexpansive():
+    """Soft mode = prox of t*||AC coefficients||_1 per block: optimality conditions in the
+    DCT domain hold, and the map is non-expansive (Assumption 2 of Sec. 4)."""
+    rng = np.random.default_rng(8)
+    C = O.dct_matrix(8)
+    t = 0.3
+    x = rng.uniform(0, 1, (16, 16))
+    z, _ = O.dct_denoise(x, t / 2.7, mode="soft")
+    for a in (0, 8):
+        for b in (0, 8):
+            X = C @ x[a:a + 8, b:b + 8] @ C.T
+            Zc = C @ z[a:a + 8, b:b + 8] @ C.T
+            assert abs(X[0, 0] - Zc[0, 0]) < 1e-12
+            m = np.ones((8, 8), bool)
+            m[0, 0] = False
+            nz = m & (np.abs(Zc) > 1e-12)
+            np.testing.assert_allclose(X[nz] - Zc[nz], t * np.sign(Zc[nz]), atol=1e-12)
+            assert np.all(np.abs(X[m & ~nz]) <= t + 1e-12)
+    for _ in range(5):
+        a_ = rng.uniform(0, 1, (16, 16))
+        b_ = a_ + 0.1 * rng.standard_normal((16, 16))
+        da, _ = O.dct_denoise(a_, 0.1, mode="soft")
+        db, _ = O.dct_denoise(b_, 0.1, mode="soft")
+        assert np.linalg.norm(da - db) <= np.linalg.norm(a_ - b_) + 1e-12
+
+
+def test_cycle_spinning_is_translation_equivariant():
+    """Averaging over all block offsets makes the denoiser commute with every circular
+    shift (exactly, up to rounding); threshold 0 is still the identity."""
+    rng = np.random.default_rng(9)
+    x = rng.uniform(0, 1, (16, 16))
+    for mode in ("hard", "soft"):
+        d0, _ = O.dct_denoise(x, 0.1, mode=mode, spin=True)
+        d1, _ = O.dct_denoise(O.shift(x, 3, 5), 0.1, mode=mode, spin=True)
+        np.testing.assert_allclose(d1, O.shift(d0, 3, 5), atol=1e-13)
+        np.testing.assert_allclose(O.dct_denoise(x, 0.0, mode=mode, spin=True)[0], x,
+                                   atol=1e-13)
+    plain, _ = O.dct_denoise(x, 0.1)
+    shifted, _ = O.dct_denoise(O.shift(x, 3, 5), 0.1)
+    assert np.linalg.norm(shifted - O.shift(plain, 3, 5)) > 1e-3  # the plain one is not
