@@ -249,6 +249,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     const int q = warp & 3;  // TMEM lane quadrant of this warp
     const int row = q * 32 + lane;
     const uint32_t lane_addr = tbase + ((uint32_t)(q * 32) << 16);
+    float2* wcol = (float2*)(smem + P1_SLOTS * SLOT + 256) + q * 32;  // this warp's staging
     uint32_t tcount = 0;
     bool ok = true;
     for (int64_t u = blockIdx.x; ok && u < total; u += gridDim.x) {
@@ -260,7 +261,12 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
       const int tb = grp * a.tpg, te = min(a.n_stiles, tb + a.tpg);
       const int64_t i = (int64_t)iblk * 128 + row;
       const float yb = a.ybar[i];
+      const float a2 = a.a2, c2 = a.c2;
+      const float* __restrict__ colb = a.colb;
+      const float* __restrict__ colm = a.colm;
       float rm = -INFINITY, rs = 0.f;
+      // (colb, colm) of the next 32-column chunk, loaded one chunk ahead of its use
+      float nb_ = colb[tb * 256 + lane], nm_ = colm[tb * 256 + lane];
       for (int tile = tb; tile < te; ++tile) {
         const int b = tcount & 1;
         const uint32_t tph = (tcount >> 1) & 1;
@@ -269,15 +275,23 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         tc_fence_after();
 #pragma unroll 1
         for (int c = 0; c < 8; ++c) {
+          __syncwarp();  // the warp is done with the previous chunk's terms
+          wcol[lane] = make_float2(nb_, nm_);
+          __syncwarp();
+          const int nx = (c < 7) ? tile * 256 + (c + 1) * 32 : (tile + 1) * 256;
+          if (c < 7 || tile + 1 < te) {
+            nb_ = colb[nx + lane];
+            nm_ = colm[nx + lane];
+          }
           float v[32];
           tmem_ld32(lane_addr + (uint32_t)(b * 256 + c * 32), v);
           tmem_ld_wait();
-          const int sb = tile * 256 + c * 32;
           float mx = -INFINITY;
 #pragma unroll
           for (int e = 0; e < 32; ++e) {
-            const float dd = yb - a.colm[sb + e];
-            v[e] = fmaf(v[e], a.a2, a.colb[sb + e]) - a.c2 * dd * dd;
+            const float2 cbm = wcol[e];
+            const float dd = yb - cbm.y;
+            v[e] = fmaf(v[e], a2, cbm.x) - c2 * dd * dd;
             mx = fmaxf(mx, v[e]);
           }
           const float nm = fmaxf(rm, mx);
@@ -530,6 +544,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     const int q = warp & 3;
     const int row = q * 32 + lane;
     const uint32_t lane_addr = tbase + ((uint32_t)(q * 32) << 16);
+    float2* wobs = (float2*)(pbuf + 2 * SLOT + 256) + q * 32;  // this warp's staging
     uint32_t sc = 0, pz = 0, uc = 0;
     bool ok = true;
     for (int64_t u = blockIdx.x; ok && u < total; u += gridDim.x) {
@@ -544,10 +559,15 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
       const int nb = min(a.n_iblk, jb0 + a.iblk_per_split) - jb0;
       const int s = stile * 128 + row;
       const float cb = a.colb[s], cm = a.colm[s];
+      const float a2 = a.a2, c2 = a.c2;
       float cacc = 0.f, zacc = 0.f;
       for (int j = 0; j < nb; ++j) {
         const int64_t ib = (int64_t)(jb0 + j) * 128;
         const int b = sc & 1, pb = pz & 1;
+        // (ybar, lse2) of the next 32-observation chunk, loaded one chunk ahead of its
+        // use; lse2 = +inf past N gives weight 0
+        float ny = a.ybar[ib + lane];
+        float nl = (ib + lane < a.N) ? a.lse2[ib + lane] : INFINITY;
         ok = __all_sync(0xffffffffu, mbar_wait(&sfull[b], (sc >> 1) & 1, abort));
         if (ok) ok = __all_sync(0xffffffffu, mbar_wait(&pempty[pb], ((pz >> 1) & 1) ^ 1, abort));
         if (!ok) break;
@@ -555,6 +575,14 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         uint8_t* prow = pbuf + pb * SLOT + row * 128;
 #pragma unroll 1
         for (int c = 0; c < 4; ++c) {
+          __syncwarp();  // the warp is done with the previous chunk's terms
+          wobs[lane] = make_float2(ny, nl);
+          __syncwarp();
+          if (c < 3) {
+            const int64_t io = ib + (c + 1) * 32 + lane;
+            ny = a.ybar[io];
+            nl = (io < a.N) ? a.lse2[io] : INFINITY;
+          }
           float v[32];
           tmem_ld32(lane_addr + (uint32_t)(b * 128 + c * 32), v);
           tmem_ld_wait();
@@ -564,11 +592,11 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             float w2[2];
 #pragma unroll
             for (int h = 0; h < 2; ++h) {
-              const int64_t i = ib + c * 32 + e + h;
-              const float ybi = a.ybar[i];
+              const float2 yl = wobs[e + h];
+              const float ybi = yl.x;
               const float dd = ybi - cm;
-              const float val = fmaf(v[e + h], a.a2, cb - a.lse2[i]) - a.c2 * dd * dd;
-              const float w = (i < a.N) ? exp2f(val) * W_SCALE : 0.f;
+              const float val = fmaf(v[e + h], a2, cb - yl.y) - c2 * dd * dd;
+              const float w = exp2f(val) * W_SCALE;
               w2[h] = __half2float(__float2half_rn(w));
               cacc += w2[h];
               zacc = fmaf(w2[h], ybi, zacc);
@@ -895,6 +923,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     const int q = warp & 3;
     const int row = q * 32 + lane;
     const uint32_t lane_addr = tbase + ((uint32_t)(q * 32) << 16);
+    float2* wobs = (float2*)(smem + P2C_SLOTS * SLOT + 512) + q * 32;  // this warp's staging
     uint32_t sc = 0, mr = 0, uc = 0;
     bool ok = true;
     for (int64_t u = cid; ok && u < total; u += ncl) {
@@ -912,12 +941,17 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
       const int nb = min(a.n_iblk, jb0 + a.iblk_per_split) - jb0;
       const int s = stile * 128 + row;
       const float cb = a.colb[s], cm = a.colm[s];
+      const float a2 = a.a2, c2 = a.c2;
       float cacc = 0.f, zacc = 0.f;
       for (int r0 = 0; ok && r0 < nb; r0 += G) {
         const int nq = min(G, nb - r0);
         if ((int)rank >= nq) continue;
         const int64_t ib = (int64_t)(jb0 + r0 + (int)rank) * 128;
         const int b = sc & 1;
+        // (ybar, lse2) of the next 32-observation chunk, loaded one chunk ahead of its
+        // use; lse2 = +inf past N gives weight 0
+        float ny = a.ybar[ib + lane];
+        float nl = (ib + lane < a.N) ? a.lse2[ib + lane] : INFINITY;
         ok = __all_sync(0xffffffffu, mbar_wait(&sfull[b], (sc >> 1) & 1, abort));
         if (ok)
           ok = __all_sync(0xffffffffu,
@@ -929,6 +963,14 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         uint8_t* prow = smem + own * SLOT + row * 128;
 #pragma unroll 1
         for (int c = 0; c < 4; ++c) {
+          __syncwarp();  // the warp is done with the previous chunk's terms
+          wobs[lane] = make_float2(ny, nl);
+          __syncwarp();
+          if (c < 3) {
+            const int64_t io = ib + (c + 1) * 32 + lane;
+            ny = a.ybar[io];
+            nl = (io < a.N) ? a.lse2[io] : INFINITY;
+          }
           float v[32];
           tmem_ld32(lane_addr + (uint32_t)(b * 128 + c * 32), v);
           tmem_ld_wait();
@@ -938,11 +980,11 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             float w2[2];
 #pragma unroll
             for (int h = 0; h < 2; ++h) {
-              const int64_t i = ib + c * 32 + e + h;
-              const float ybi = a.ybar[i];
+              const float2 yl = wobs[e + h];
+              const float ybi = yl.x;
               const float dd = ybi - cm;
-              const float val = fmaf(v[e + h], a.a2, cb - a.lse2[i]) - a.c2 * dd * dd;
-              const float w = (i < a.N) ? exp2f(val) * W_SCALE : 0.f;
+              const float val = fmaf(v[e + h], a2, cb - yl.y) - c2 * dd * dd;
+              const float w = exp2f(val) * W_SCALE;
               w2[h] = __half2float(__float2half_rn(w));
               cacc += w2[h];
               zacc = fmaf(w2[h], ybi, zacc);
@@ -1019,12 +1061,14 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
   cluster_sync_all();  // no CTA leaves while a peer may still copy into it
 }
 
-// ring + bookkeeping (25 mbarriers, mailbox, TMEM address, abort flag: < 512 bytes)
-constexpr size_t P2C_SMEM = 1024 + P2C_SLOTS * SLOT + 512;
+// ring + bookkeeping (25 mbarriers, mailbox, TMEM address, abort flag: < 512 bytes) +
+// per-warp staging of one 32-observation chunk's (ybar, lse2) (4 x 256 bytes)
+constexpr size_t P2C_SMEM = 1024 + P2C_SLOTS * SLOT + 512 + 1024;
 static_assert(P2C_SMEM <= 232448, "exceeds the shared memory of one CTA");
 
-constexpr size_t P1_SMEM = 1024 + P1_SLOTS * SLOT + 256;
-constexpr size_t P2_SMEM = 1024 + P2_SLOTS * SLOT + 2 * SLOT + 256;
+constexpr size_t P1_SMEM = 1024 + P1_SLOTS * SLOT + 256 + 1024;
+constexpr size_t P2_SMEM = 1024 + P2_SLOTS * SLOT + 2 * SLOT + 256 + 1024;
+static_assert(P2_SMEM <= 232448, "exceeds the shared memory of one CTA");
 
 // ------------------------------------------------------------------------------ operands
 // y' -> bf16 hi / lo rows [Npad][ldk] (zero padding beyond l2).

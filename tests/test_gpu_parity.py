@@ -280,3 +280,32 @@ def test_launch_count_is_reported(S):
     s.sync()
     assert s.launches - n0 >= 2 * 5
     s.close()
+
+
+@pytest.mark.parametrize("mode,spin", [("soft", False), ("hard", True), ("soft", True)])
+def test_denoiser_variants_against_oracle(S, mode, spin):
+    """Soft threshold (the l1 prox) and cycle spinning on the GPU against the oracle's
+    denoiser applied to the same image."""
+    p = synth.make_problem(32, 2, 500, 0.3, seed=synth.seed_for(2, 77), n_blobs=12, n_rects=3)
+    s = make_solver(S, p)
+    s.set_denoiser(mode, 2.7, spin)
+    s.em_iter(1)
+    x_pre = s.state()[0]
+    s.project(0.2)
+    x_gpu = s.state()[0]
+    x_ref, margin = O.dct_denoise(x_pre, 0.2, mode=mode, spin=spin)
+    if mode == "hard":
+        assert margin > 1e-6
+    assert rel(x_gpu, x_ref) < 1e-6
+    # the same variant drives Algorithm 2 (single-context path and a batch)
+    a = make_solver(S, p)
+    a.set_denoiser(mode, 2.7, spin)
+    a.solve(3, 1)
+    b = make_solver(S, p)
+    b.set_denoiser(mode, 2.7, spin)
+    bt = S.Batch([b])
+    bt.solve(3, 1)
+    assert a.state()[0].tobytes() == b.state()[0].tobytes()
+    bt.close()
+    for z in (s, a, b):
+        z.close()

@@ -130,5 +130,7 @@ def test_cluster_and_per_chunk_pass2_agree(S, L, K, N, sigma):
         s.solve(2, 1)
         out.append(s.state())
         s.close()
-    assert rel(out[0][0], out[1][0]) < 1e-6
-    assert rel(out[0][1], out[1][1]) < 1e-6 and rel(out[0][2], out[1][2]) < 1e-6
+    # the weight sums are grouped differently (one partial per CTA of the cluster), so
+    # the two agree to float32 rounding, well inside the mixed form's 1e-4 target
+    assert rel(out[0][0], out[1][0]) < 1e-5
+    assert rel(out[0][1], out[1][1]) < 1e-5 and rel(out[0][2], out[1][2]) < 1e-5
