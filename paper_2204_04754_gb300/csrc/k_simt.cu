@@ -28,6 +28,27 @@ __device__ __forceinline__ void st4(float* p, float4 v) {
   *reinterpret_cast<float4*>(p) = v;
 }
 
+// Packed pairs of float32 in one 64-bit register (element 0 in the low half, i.e. the
+// memory order of a float2).  fma.rn.f32x2 rounds each half exactly like fmaf, so the
+// packed loops give the same bits as scalar ones with half the issued instructions.
+using f2 = unsigned long long;
+__device__ __forceinline__ void ffma2(f2& d, f2 a, f2 b) {
+  asm("fma.rn.f32x2 %0, %1, %2, %0;" : "+l"(d) : "l"(a), "l"(b));
+}
+__device__ __forceinline__ f2 dup2(float x) {
+  f2 r;
+  asm("mov.b64 %0, {%1, %1};" : "=l"(r) : "f"(x));
+  return r;
+}
+__device__ __forceinline__ float lo2(f2 v) { return __uint_as_float((unsigned)(v & 0xffffffffull)); }
+__device__ __forceinline__ float hi2(f2 v) { return __uint_as_float((unsigned)(v >> 32)); }
+__device__ __forceinline__ ulonglong2 ld4p(const float* p) {
+  return *reinterpret_cast<const ulonglong2*>(p);
+}
+__device__ __forceinline__ void st4p(float* p, f2 a, f2 b) {
+  *reinterpret_cast<ulonglong2*>(p) = make_ulonglong2(a, b);
+}
+
 // ----------------------------------------------------------------------------- pass 1
 // Tile 128 observations x 128 shifts, 256 threads, 8x8 outputs per thread, k-step 8.
 // Operands are pixel-major: YcT[k][i], AxT[k][s].
@@ -46,25 +67,20 @@ __global__ void __launch_bounds__(256, 2)
   const int te = min(n_tiles, tb + tiles_per_group);
   const int lk = tid >> 5, lc = (tid & 31) * 4;
 
-  float yb[8], rm[8], rs[8];
-#pragma unroll
-  for (int j = 0; j < 4; ++j) {
-    yb[j] = ybar[i0 + ty * 4 + j];
-    yb[4 + j] = ybar[i0 + 64 + ty * 4 + j];
-  }
-#pragma unroll
-  for (int j = 0; j < 8; ++j) {
-    rm[j] = -INFINITY;
-    rs[j] = 0.f;
-  }
+  // The 16 lanes with the same ty share the rows of their 8 observations; lane tx < 8
+  // keeps row tx's ybar and running (max, sum), read by the others through shuffles.
+  const int orow = (tx & 7) < 4 ? ty * 4 + (tx & 7) : 64 + ty * 4 + (tx & 7) - 4;
+  const int lane = tid & 31, lgrp = lane & 16;
+  const float my_yb = ybar[i0 + orow];
+  float my_rm = -INFINITY, my_rs = 0.f;
 
   for (int tile = tb; tile < te; ++tile) {
     const int s0 = tile * 128;
-    float acc[8][8];
+    f2 acc2[8][4];  // acc2[j][c/2] holds the outputs (j, c) and (j, c + 1)
 #pragma unroll
     for (int j = 0; j < 8; ++j)
 #pragma unroll
-      for (int c = 0; c < 8; ++c) acc[j][c] = 0.f;
+      for (int c = 0; c < 4; ++c) acc2[j][c] = 0ull;
 
     float4 ra = ld4(YcT + (int64_t)lk * Npad + i0 + lc);
     float4 rb = ld4(AxT + (int64_t)lk * Spad + s0 + lc);
@@ -82,14 +98,16 @@ __global__ void __launch_bounds__(256, 2)
       for (int kk = 0; kk < 8; ++kk) {
         const float4 a0 = ld4(&As[cur][kk][ty * 4]);
         const float4 a1 = ld4(&As[cur][kk][64 + ty * 4]);
-        const float4 b0 = ld4(&Bs[cur][kk][tx * 4]);
-        const float4 b1 = ld4(&Bs[cur][kk][64 + tx * 4]);
+        const ulonglong2 b0 = ld4p(&Bs[cur][kk][tx * 4]);
+        const ulonglong2 b1 = ld4p(&Bs[cur][kk][64 + tx * 4]);
         const float a[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
-        const float b[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
+        const f2 b[4] = {b0.x, b0.y, b1.x, b1.y};
 #pragma unroll
-        for (int j = 0; j < 8; ++j)
+        for (int j = 0; j < 8; ++j) {
+          const f2 aj = dup2(a[j]);
 #pragma unroll
-          for (int c = 0; c < 8; ++c) acc[j][c] = fmaf(a[j], b[c], acc[j][c]);
+          for (int c = 0; c < 4; ++c) ffma2(acc2[j][c], aj, b[c]);
+        }
       }
       if (more) {
         st4(&As[cur ^ 1][lk][lc], ra);
@@ -110,49 +128,84 @@ __global__ void __launch_bounds__(256, 2)
     }
 #pragma unroll
     for (int j = 0; j < 8; ++j) {
+      const float ybj = __shfl_sync(0xffffffffu, my_yb, lgrp | j);
+      const float rmj = __shfl_sync(0xffffffffu, my_rm, lgrp | j);
+      const float rsj = __shfl_sync(0xffffffffu, my_rs, lgrp | j);
       float v[8];
       float mx = -INFINITY;
 #pragma unroll
       for (int c = 0; c < 8; ++c) {
-        const float d = yb[j] - cm[c];
-        v[c] = fmaf(acc[j][c], a2, cb[c]) - c2 * d * d;
+        const float d = ybj - cm[c];
+        const float acc = (c & 1) ? hi2(acc2[j][c >> 1]) : lo2(acc2[j][c >> 1]);
+        v[c] = fmaf(acc, a2, cb[c]) - c2 * d * d;
         mx = fmaxf(mx, v[c]);
       }
 #pragma unroll
       for (int o = 1; o < 16; o <<= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
-      const float nm = fmaxf(rm[j], mx);
+      const float nm = fmaxf(rmj, mx);
       const float base = (nm == -INFINITY) ? 0.f : nm;
       float sm = 0.f;
 #pragma unroll
       for (int c = 0; c < 8; ++c) sm += exp2f(v[c] - base);
 #pragma unroll
       for (int o = 1; o < 16; o <<= 1) sm += __shfl_xor_sync(0xffffffffu, sm, o);
-      rs[j] = rs[j] * exp2f(rm[j] - base) + sm;
-      rm[j] = nm;
-    }
-  }
-  if (tx == 0) {
-#pragma unroll
-    for (int j = 0; j < 8; ++j) {
-      const int64_t i = i0 + (j < 4 ? ty * 4 + j : 64 + ty * 4 + (j - 4));
-      if (i < N) {
-        pm[grp * Npad + i] = rm[j];
-        ps[grp * Npad + i] = rs[j];
+      const float nrs = rsj * exp2f(rmj - base) + sm;
+      if (tx == j) {
+        my_rm = nm;
+        my_rs = nrs;
       }
     }
+  }
+  if (tx < 8 && i0 + orow < N) {
+    pm[grp * Npad + i0 + orow] = my_rm;
+    ps[grp * Npad + i0 + orow] = my_rs;
   }
 }
 
 // ----------------------------------------------------------------------------- pass 2
 // Cluster of gc CTAs (blockIdx.x = rank), one 64-shift tile (blockIdx.y), one
-// observation range x chunk group (blockIdx.z).  Per round each rank computes the
-// 64x64 weight tile of its own observation block (phase A+B), then every rank
-// accumulates Z' over its 256-pixel chunk for all gc blocks of the round (phase C),
-// reading the other ranks' weight tiles from their shared memory.
-constexpr int P2_SMEM_FLOATS = 2 * 64 * 64 + 2 * 16 * 256;  // P[2] + staging
+// observation range x chunk group (blockIdx.z).  Each round covers gc blocks of 64
+// observations: rank q computes the 64x64 weight tile of block q of the round, and
+// every rank accumulates Z' over its own 256-pixel chunk for all gc blocks of the
+// round, reading the other ranks' weight tiles from their shared memory.
+//
+// The 512 threads of a CTA form two groups that work one round apart:
+//   group A (threads 0-255): logits S[s][i] = <T'_s, y'_i> of the next round's block
+//     (4x4 outputs per thread), then w = 2^(logit2 - lse2) into the weight buffer and
+//     the partial sums c[s], zb[s];
+//   group C (threads 256-511): Z'[s][p] += sum_i w[i][s] y'_i[p] for the current round
+//     (8 shifts x 8 pixels per thread).
+// Two weight buffers alternate between rounds.  One split-phase cluster barrier per
+// round orders them: group A arrives after writing the weights of round p, group C
+// after it has finished reading round p - 1 (whose buffer round p + 1 reuses); group A
+// waits on it before writing a buffer, group C before reading one.  Each group stages
+// its operands through a 3-deep cp.async ring synchronised by its own named barrier.
+constexpr int P2_THREADS = 512;
+constexpr int P2_NST = 3;  // cp.async stages per group
+constexpr int P2_SMEM_FLOATS = 2 * 64 * 64            // weight tiles P[2][64 obs][64 shifts]
+                               + P2_NST * 2 * 16 * 64  // group A: As, Bs [stage][16][64]
+                               + P2_NST * 16 * 256;    // group C: Ys [stage][16][256]
 constexpr size_t P2_SMEM_BYTES = P2_SMEM_FLOATS * sizeof(float);
 
-__global__ void __launch_bounds__(256, 1)
+__device__ __forceinline__ void cp16(float* dst, const float* src, bool valid) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(d), "l"(src),
+               "r"(valid ? 16 : 0)
+               : "memory");
+}
+__device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_wait1() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
+__device__ __forceinline__ void group_bar(int id) {
+  asm volatile("bar.sync %0, 256;" ::"r"(id) : "memory");
+}
+__device__ __forceinline__ void cluster_arrive() {
+  asm volatile("barrier.cluster.arrive.release.aligned;" ::: "memory");
+}
+__device__ __forceinline__ void cluster_wait() {
+  asm volatile("barrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+
+__global__ void __launch_bounds__(P2_THREADS, 1)
     k_p2_f32(const float* __restrict__ YcT, const float* __restrict__ Yc, int64_t Npad,
              const float* __restrict__ AxT, int Spad, int ldy,
              const float* __restrict__ ybar, const float* __restrict__ colb,
@@ -161,11 +214,12 @@ __global__ void __launch_bounds__(256, 1)
              int n_cgroups, float* __restrict__ Zp, float* __restrict__ cp,
              float* __restrict__ zbp) {
   extern __shared__ __align__(16) float smem[];
-  float* const Pbuf = smem;             // [2][64 obs][64 shifts]
-  float* const stg = smem + 2 * 4096;   // phase A: As[2][16][64], Bs[2][16][64]; C: Ys[2][16][256]
+  float* const Pbuf = smem;                              // [2][64 obs][64 shifts]
+  float* const As = smem + 2 * 4096;                     // [P2_NST][16][64] shifts
+  float* const Bs = As + P2_NST * 1024;                  // [P2_NST][16][64] observations
+  float* const Ys = Bs + P2_NST * 1024;                  // [P2_NST][16][256] pixels
   cg::cluster_group cluster = cg::this_cluster();
   const int rank = (int)cluster.block_rank();
-  const int tid = threadIdx.x;
   const int s0 = blockIdx.y * 64;
   const int split = blockIdx.z / n_cgroups, cgrp = blockIdx.z % n_cgroups;
   const int p0 = (cgrp * gc + rank) * 256;
@@ -173,169 +227,173 @@ __global__ void __launch_bounds__(256, 1)
   const int b_end = min(n_iblk, b_begin + iblk_per_split);
   const int nb = max(0, b_end - b_begin);
   const int rounds = (nb + gc - 1) / gc;
+  const int nks = ldy / 16;
 
-  const int ts = tid & 15, ti = tid >> 4;   // phase A/B: 4 shifts x 4 observations
-  const int sg = tid >> 5, pg = tid & 31;   // phase C: 8 shifts x 8 pixels
-  const int lk = tid >> 4, lc = (tid & 15) * 4;
-
-  float z[8][8];
-#pragma unroll
-  for (int a = 0; a < 8; ++a)
-#pragma unroll
-    for (int b = 0; b < 8; ++b) z[a][b] = 0.f;
-  float cacc[4] = {0.f, 0.f, 0.f, 0.f}, zacc[4] = {0.f, 0.f, 0.f, 0.f};
-  float cbA[4], cmA[4];
-#pragma unroll
-  for (int a = 0; a < 4; ++a) {
-    cbA[a] = colb[s0 + ts * 4 + a];
-    cmA[a] = colm[s0 + ts * 4 + a];
-  }
-
-  for (int rd = 0; rd < rounds; ++rd) {
-    float* const P = Pbuf + (rd & 1) * 4096;
-    const int myb = b_begin + rd * gc + rank;
-    if (myb < b_end) {
-      // phase A: S[s][i] = <T'_s, y'_i>, 64 x 64, k-step 16
-      const int64_t ib = (int64_t)myb * 64;
-      float acc[4][4];
-#pragma unroll
-      for (int a = 0; a < 4; ++a)
-#pragma unroll
-        for (int b = 0; b < 4; ++b) acc[a][b] = 0.f;
-      float* const As = stg;
-      float* const Bs = stg + 2048;
-      float4 ra = ld4(AxT + (int64_t)lk * Spad + s0 + lc);
-      float4 rb = ld4(YcT + (int64_t)lk * Npad + ib + lc);
-      st4(As + lk * 64 + lc, ra);
-      st4(Bs + lk * 64 + lc, rb);
-      __syncthreads();
-      int cur = 0;
-      for (int kc = 0; kc < ldy; kc += 16) {
-        const bool more = kc + 16 < ldy;
-        if (more) {
-          ra = ld4(AxT + (int64_t)(kc + 16 + lk) * Spad + s0 + lc);
-          rb = ld4(YcT + (int64_t)(kc + 16 + lk) * Npad + ib + lc);
-        }
-        const float* Ac = As + cur * 1024;
-        const float* Bc = Bs + cur * 1024;
-#pragma unroll
-        for (int kk = 0; kk < 16; ++kk) {
-          const float4 a4 = ld4(Ac + kk * 64 + ts * 4);
-          const float4 b4 = ld4(Bc + kk * 64 + ti * 4);
-          const float av[4] = {a4.x, a4.y, a4.z, a4.w};
-          const float bv[4] = {b4.x, b4.y, b4.z, b4.w};
-#pragma unroll
-          for (int a = 0; a < 4; ++a)
-#pragma unroll
-            for (int b = 0; b < 4; ++b) acc[a][b] = fmaf(av[a], bv[b], acc[a][b]);
-        }
-        if (more) {
-          st4(As + (cur ^ 1) * 1024 + lk * 64 + lc, ra);
-          st4(Bs + (cur ^ 1) * 1024 + lk * 64 + lc, rb);
-        }
-        __syncthreads();
-        cur ^= 1;
-      }
-      // phase B: w = 2^(logit2 - lse2), partial c and zb
-#pragma unroll
-      for (int b = 0; b < 4; ++b) {
-        const int64_t i = ib + ti * 4 + b;
-        const float yb = ybar[i];
-        const float ls = lse2[i];
-        const bool iv = i < N;
-        float w[4];
-#pragma unroll
-        for (int a = 0; a < 4; ++a) {
-          const float d = yb - cmA[a];
-          const float v = fmaf(acc[a][b], a2, cbA[a]) - c2 * d * d - ls;
-          w[a] = (iv && (s0 + ts * 4 + a) < S) ? exp2f(v) : 0.f;
-          cacc[a] += w[a];
-          zacc[a] = fmaf(w[a], yb, zacc[a]);
-        }
-        st4(P + (ti * 4 + b) * 64 + ts * 4, make_float4(w[0], w[1], w[2], w[3]));
-      }
-    }
-    cluster.sync();  // weight tiles of this round are complete in every rank
-
-    // phase C: Z'[s][p] += sum_i w[i][s] y'_i[p] over the round's observation blocks
-    const int nq = min(gc, b_end - (b_begin + rd * gc));
-    const int nchunks = nq * 4;
-    float* const Ys = stg;
-    float4 rY[4];
-    auto loadY = [&](int cidx) {
-      const int q = cidx >> 2, ic = (cidx & 3) * 16;
-      const int64_t ib = (int64_t)(b_begin + rd * gc + q) * 64 + ic;
-#pragma unroll
-      for (int j = 0; j < 4; ++j) {
-        const int row = (tid >> 6) + 4 * j, col = (tid & 63) * 4;
-        const int p = p0 + col;
-        rY[j] = (p < ldy) ? ld4(Yc + (ib + row) * ldy + p) : make_float4(0.f, 0.f, 0.f, 0.f);
-      }
-    };
-    auto storeY = [&](int buf) {
-#pragma unroll
-      for (int j = 0; j < 4; ++j) {
-        const int row = (tid >> 6) + 4 * j, col = (tid & 63) * 4;
-        st4(Ys + buf * 4096 + row * 256 + col, rY[j]);
-      }
-    };
-    if (nchunks > 0) {
-      loadY(0);
-      storeY(0);
-    }
-    __syncthreads();
-    for (int cidx = 0; cidx < nchunks; ++cidx) {
-      const int cur = cidx & 1;
-      if (cidx + 1 < nchunks) loadY(cidx + 1);
-      const int q = cidx >> 2, ic = (cidx & 3) * 16;
-      const float* Pq = cluster.map_shared_rank(P, q) + ic * 64 + sg * 8;
-      const float* Yb = Ys + cur * 4096;
-#pragma unroll
-      for (int k = 0; k < 16; ++k) {
-        const float4 w0 = ld4(Pq + k * 64);
-        const float4 w1 = ld4(Pq + k * 64 + 4);
-        const float4 y0 = ld4(Yb + k * 256 + pg * 4);
-        const float4 y1 = ld4(Yb + k * 256 + 128 + pg * 4);
-        const float wv[8] = {w0.x, w0.y, w0.z, w0.w, w1.x, w1.y, w1.z, w1.w};
-        const float yv[8] = {y0.x, y0.y, y0.z, y0.w, y1.x, y1.y, y1.z, y1.w};
-#pragma unroll
-        for (int a = 0; a < 8; ++a)
-#pragma unroll
-          for (int b = 0; b < 8; ++b) z[a][b] = fmaf(wv[a], yv[b], z[a][b]);
-      }
-      if (cidx + 1 < nchunks) storeY(cur ^ 1);
-      __syncthreads();
-    }
-  }
-  cluster.sync();  // no rank leaves while another may still read its weight tiles
-
-  // partial M-step sums of this (observation range, shift tile, pixel chunk)
-#pragma unroll
-  for (int a = 0; a < 8; ++a) {
-    const int s = s0 + sg * 8 + a;
-    float* zr = Zp + ((int64_t)split * Spad + s) * ldy;
-    const int pa = p0 + pg * 4, pb = p0 + 128 + pg * 4;
-    if (pa < ldy) st4(zr + pa, make_float4(z[a][0], z[a][1], z[a][2], z[a][3]));
-    if (pb < ldy) st4(zr + pb, make_float4(z[a][4], z[a][5], z[a][6], z[a][7]));
-  }
-  if (cgrp == 0) {
-    float* red = stg;  // [16][64] c, then [16][64] zb
-    __syncthreads();
+  if (threadIdx.x < 256) {
+    // ------------------------------------------------------------------ group A
+    const int tid = threadIdx.x;
+    const int ts = tid & 15, ti = tid >> 4;  // 4 shifts x 4 observations
+    const int lk = tid >> 4, lc = (tid & 15) * 4;
+    float cacc[4] = {0.f, 0.f, 0.f, 0.f}, zacc[4] = {0.f, 0.f, 0.f, 0.f};
+    float cbA[4], cmA[4];
 #pragma unroll
     for (int a = 0; a < 4; ++a) {
-      red[ti * 64 + ts * 4 + a] = cacc[a];
-      red[1024 + ti * 64 + ts * 4 + a] = zacc[a];
+      cbA[a] = colb[s0 + ts * 4 + a];
+      cmA[a] = colm[s0 + ts * 4 + a];
     }
-    __syncthreads();
-    if (tid < 64) {
-      float c = 0.f, zb = 0.f;
-      for (int k = 0; k < 16; ++k) {
-        c += red[k * 64 + tid];
-        zb += red[1024 + k * 64 + tid];
+    for (int rd = 0; rd < rounds; ++rd) {
+      const int myb = b_begin + rd * gc + rank;
+      const bool mine = myb < b_end;
+      const int64_t ib = (int64_t)myb * 64;
+      f2 acc2[4][2];  // acc2[a][b/2] holds S entries (a, b) and (a, b + 1)
+#pragma unroll
+      for (int a = 0; a < 4; ++a) acc2[a][0] = acc2[a][1] = 0ull;
+      if (mine) {
+        auto issue = [&](int ks) {
+          const int st = ks % P2_NST;
+          if (ks < nks) {
+            const int k = ks * 16 + lk;
+            cp16(As + st * 1024 + lk * 64 + lc, AxT + (int64_t)k * Spad + s0 + lc, true);
+            cp16(Bs + st * 1024 + lk * 64 + lc, YcT + (int64_t)k * Npad + ib + lc, true);
+          }
+          cp_commit();
+        };
+        group_bar(1);  // the stage buffers of the previous round are no longer read
+        issue(0);
+        issue(1);
+        for (int ks = 0; ks < nks; ++ks) {
+          cp_wait1();
+          group_bar(1);
+          issue(ks + 2);
+          const float* Ac = As + (ks % P2_NST) * 1024;
+          const float* Bc = Bs + (ks % P2_NST) * 1024;
+#pragma unroll
+          for (int kk = 0; kk < 16; ++kk) {
+            const float4 a4 = ld4(Ac + kk * 64 + ts * 4);
+            const ulonglong2 b4 = ld4p(Bc + kk * 64 + ti * 4);
+            const float av[4] = {a4.x, a4.y, a4.z, a4.w};
+#pragma unroll
+            for (int a = 0; a < 4; ++a) {
+              const f2 aa = dup2(av[a]);
+              ffma2(acc2[a][0], aa, b4.x);
+              ffma2(acc2[a][1], aa, b4.y);
+            }
+          }
+        }
       }
-      const int64_t part = (int64_t)split * gc + rank;
-      cp[part * Spad + s0 + tid] = c;
-      zbp[part * Spad + s0 + tid] = zb;
+      if (rd >= 1) cluster_wait();  // every rank has finished reading round rd - 2
+      if (mine) {
+        float* const P = Pbuf + (rd & 1) * 4096;
+#pragma unroll
+        for (int b = 0; b < 4; ++b) {
+          const int64_t i = ib + ti * 4 + b;
+          const float yb = ybar[i];
+          const float ls = lse2[i];
+          const bool iv = i < N;
+          float w[4];
+#pragma unroll
+          for (int a = 0; a < 4; ++a) {
+            const float d = yb - cmA[a];
+            const float acc = (b & 1) ? hi2(acc2[a][b >> 1]) : lo2(acc2[a][b >> 1]);
+            const float v = fmaf(acc, a2, cbA[a]) - c2 * d * d - ls;
+            w[a] = (iv && (s0 + ts * 4 + a) < S) ? exp2f(v) : 0.f;
+            cacc[a] += w[a];
+            zacc[a] = fmaf(w[a], yb, zacc[a]);
+          }
+          st4(P + (ti * 4 + b) * 64 + ts * 4, make_float4(w[0], w[1], w[2], w[3]));
+        }
+      }
+      cluster_arrive();  // the weights of round rd are in place
+    }
+    if (rounds >= 1) cluster_wait();
+    cluster_arrive();
+    cluster_wait();  // no rank leaves while another may still read its weight tiles
+    if (cgrp == 0) {
+      float* red = As;  // [16][64] c, then [16][64] zb (group A's stages are idle now)
+      group_bar(1);
+#pragma unroll
+      for (int a = 0; a < 4; ++a) {
+        red[ti * 64 + ts * 4 + a] = cacc[a];
+        red[1024 + ti * 64 + ts * 4 + a] = zacc[a];
+      }
+      group_bar(1);
+      if (tid < 64) {
+        float c = 0.f, zb = 0.f;
+        for (int k = 0; k < 16; ++k) {
+          c += red[k * 64 + tid];
+          zb += red[1024 + k * 64 + tid];
+        }
+        const int64_t part = (int64_t)split * gc + rank;
+        cp[part * Spad + s0 + tid] = c;
+        zbp[part * Spad + s0 + tid] = zb;
+      }
+    }
+  } else {
+    // ------------------------------------------------------------------ group C
+    const int tid = threadIdx.x - 256;
+    const int sg = tid >> 5, pg = tid & 31;  // 8 shifts x 8 pixels
+    f2 z2[8][4];  // z2[a][b/2] holds Z' entries (a, b) and (a, b + 1)
+#pragma unroll
+    for (int a = 0; a < 8; ++a)
+#pragma unroll
+      for (int b = 0; b < 4; ++b) z2[a][b] = 0ull;
+    for (int rd = 0; rd <= rounds; ++rd) {
+      cluster_arrive();  // finished reading round rd - 1
+      cluster_wait();    // the weights of round rd are in place
+      if (rd == rounds) break;
+      const float* const P = Pbuf + (rd & 1) * 4096;
+      const int nq = min(gc, b_end - (b_begin + rd * gc));
+      const int nchunks = nq * 4;  // 16-observation chunks
+      auto issue = [&](int cidx) {
+        const int st = cidx % P2_NST;
+        if (cidx < nchunks) {
+          const int q = cidx >> 2, ic = (cidx & 3) * 16;
+          const int64_t ib = (int64_t)(b_begin + rd * gc + q) * 64 + ic;
+#pragma unroll
+          for (int j = 0; j < 4; ++j) {
+            const int row = (tid >> 6) + 4 * j, col = (tid & 63) * 4;
+            const int p = p0 + col;
+            const bool v = p < ldy;
+            cp16(Ys + st * 4096 + row * 256 + col, Yc + (ib + row) * ldy + (v ? p : 0), v);
+          }
+        }
+        cp_commit();
+      };
+      group_bar(2);  // the stage buffers of the previous round are no longer read
+      issue(0);
+      issue(1);
+      for (int cidx = 0; cidx < nchunks; ++cidx) {
+        cp_wait1();
+        group_bar(2);
+        issue(cidx + 2);
+        const int q = cidx >> 2, ic = (cidx & 3) * 16;
+        const float* Pq = cluster.map_shared_rank(P, q) + ic * 64 + sg * 8;
+        const float* Yb = Ys + (cidx % P2_NST) * 4096;
+#pragma unroll
+        for (int k = 0; k < 16; ++k) {
+          const float4 w0 = ld4(Pq + k * 64);
+          const float4 w1 = ld4(Pq + k * 64 + 4);
+          const ulonglong2 y0 = ld4p(Yb + k * 256 + pg * 4);
+          const ulonglong2 y1 = ld4p(Yb + k * 256 + 128 + pg * 4);
+          const float wv[8] = {w0.x, w0.y, w0.z, w0.w, w1.x, w1.y, w1.z, w1.w};
+          const f2 yv[4] = {y0.x, y0.y, y1.x, y1.y};
+#pragma unroll
+          for (int a = 0; a < 8; ++a) {
+            const f2 wa = dup2(wv[a]);
+#pragma unroll
+            for (int b = 0; b < 4; ++b) ffma2(z2[a][b], wa, yv[b]);
+          }
+        }
+      }
+    }
+    // partial M-step sums of this (observation range, shift tile, pixel chunk)
+#pragma unroll
+    for (int a = 0; a < 8; ++a) {
+      const int s = s0 + sg * 8 + a;
+      float* zr = Zp + ((int64_t)split * Spad + s) * ldy;
+      const int pa = p0 + pg * 4, pb = p0 + 128 + pg * 4;
+      if (pa < ldy) st4p(zr + pa, z2[a][0], z2[a][1]);
+      if (pb < ldy) st4p(zr + pb, z2[a][2], z2[a][3]);
     }
   }
 }
@@ -398,7 +456,7 @@ cudaError_t launch_pass2_f32(srmra_ctx* c) {
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3((unsigned)p.p2_gc, (unsigned)(g.Spad / P2_BS),
                      (unsigned)(p.p2_nsplit * p.p2_chunk_groups));
-  cfg.blockDim = dim3(256, 1, 1);
+  cfg.blockDim = dim3(P2_THREADS, 1, 1);
   cfg.dynamicSmemBytes = P2_SMEM_BYTES;
   cfg.stream = c->stream;
   cudaLaunchAttribute attr[1];
