@@ -167,7 +167,10 @@ __global__ void __launch_bounds__(256, 2)
 // observation range x chunk group (blockIdx.z).  Each round covers gc blocks of 64
 // observations: rank q computes the 64x64 weight tile of block q of the round, and
 // every rank accumulates Z' over its own 256-pixel chunk for all gc blocks of the
-// round, reading the other ranks' weight tiles from their shared memory.
+// round.  Every rank holds the weight tiles of all gc blocks of a round: the rank that
+// computes a tile stores it into its own shared memory and into every other rank's
+// (remote stores through distributed shared memory, which do not wait for a reply),
+// so the M-step loop reads only local shared memory.
 //
 // The 512 threads of a CTA form two groups that work one round apart:
 //   group A (threads 0-255): logits S[s][i] = <T'_s, y'_i> of the next round's block
@@ -181,10 +184,13 @@ __global__ void __launch_bounds__(256, 2)
 // waits on it before writing a buffer, group C before reading one.  Each group stages
 // its operands through a 3-deep cp.async ring synchronised by its own named barrier.
 constexpr int P2_THREADS = 512;
-constexpr int P2_NST = 3;  // cp.async stages per group
-constexpr int P2_SMEM_FLOATS = 2 * 64 * 64            // weight tiles P[2][64 obs][64 shifts]
-                               + P2_NST * 2 * 16 * 64  // group A: As, Bs [stage][16][64]
-                               + P2_NST * 16 * 256;    // group C: Ys [stage][16][256]
+constexpr int P2_NST = 3;     // cp.async stages per group
+constexpr int P2_MAX_GC = 4;  // cluster width (weight tiles held per round)
+constexpr int P2_KS = 32;     // group A: pixels (k) per stage
+constexpr int P2_SMEM_FLOATS = 2 * P2_MAX_GC * 64 * 64      // P[2][gc][64 obs][64 shifts]
+                               + P2_NST * 2 * P2_KS * 64    // group A: As, Bs [stage][KS][64]
+                               + P2_NST * 16 * 256;         // group C: Ys [stage][16][256]
+static_assert(P2_SMEM_FLOATS * 4 <= 232448, "exceeds the shared memory of one CTA");
 constexpr size_t P2_SMEM_BYTES = P2_SMEM_FLOATS * sizeof(float);
 
 __device__ __forceinline__ void cp16(float* dst, const float* src, bool valid) {
@@ -214,10 +220,10 @@ __global__ void __launch_bounds__(P2_THREADS, 1)
              int n_cgroups, float* __restrict__ Zp, float* __restrict__ cp,
              float* __restrict__ zbp) {
   extern __shared__ __align__(16) float smem[];
-  float* const Pbuf = smem;                              // [2][64 obs][64 shifts]
-  float* const As = smem + 2 * 4096;                     // [P2_NST][16][64] shifts
-  float* const Bs = As + P2_NST * 1024;                  // [P2_NST][16][64] observations
-  float* const Ys = Bs + P2_NST * 1024;                  // [P2_NST][16][256] pixels
+  float* const Pbuf = smem;                              // [2][gc][64 obs][64 shifts]
+  float* const As = smem + 2 * P2_MAX_GC * 4096;         // [P2_NST][KS][64] shifts
+  float* const Bs = As + P2_NST * P2_KS * 64;            // [P2_NST][KS][64] observations
+  float* const Ys = Bs + P2_NST * P2_KS * 64;            // [P2_NST][16][256] pixels
   cg::cluster_group cluster = cg::this_cluster();
   const int rank = (int)cluster.block_rank();
   const int s0 = blockIdx.y * 64;
@@ -227,7 +233,7 @@ __global__ void __launch_bounds__(P2_THREADS, 1)
   const int b_end = min(n_iblk, b_begin + iblk_per_split);
   const int nb = max(0, b_end - b_begin);
   const int rounds = (nb + gc - 1) / gc;
-  const int nks = ldy / 16;
+  const int nks = (ldy + P2_KS - 1) / P2_KS;  // rows past ldy are zero-filled
 
   if (threadIdx.x < 256) {
     // ------------------------------------------------------------------ group A
@@ -252,9 +258,14 @@ __global__ void __launch_bounds__(P2_THREADS, 1)
         auto issue = [&](int ks) {
           const int st = ks % P2_NST;
           if (ks < nks) {
-            const int k = ks * 16 + lk;
-            cp16(As + st * 1024 + lk * 64 + lc, AxT + (int64_t)k * Spad + s0 + lc, true);
-            cp16(Bs + st * 1024 + lk * 64 + lc, YcT + (int64_t)k * Npad + ib + lc, true);
+#pragma unroll
+            for (int h = 0; h < P2_KS / 16; ++h) {
+              const int kr = lk + 16 * h, k = ks * P2_KS + kr;
+              const bool v = k < ldy;
+              const int64_t kc = v ? k : 0;
+              cp16(As + (st * P2_KS + kr) * 64 + lc, AxT + kc * Spad + s0 + lc, v);
+              cp16(Bs + (st * P2_KS + kr) * 64 + lc, YcT + kc * Npad + ib + lc, v);
+            }
           }
           cp_commit();
         };
@@ -265,10 +276,10 @@ __global__ void __launch_bounds__(P2_THREADS, 1)
           cp_wait1();
           group_bar(1);
           issue(ks + 2);
-          const float* Ac = As + (ks % P2_NST) * 1024;
-          const float* Bc = Bs + (ks % P2_NST) * 1024;
+          const float* Ac = As + (ks % P2_NST) * P2_KS * 64;
+          const float* Bc = Bs + (ks % P2_NST) * P2_KS * 64;
 #pragma unroll
-          for (int kk = 0; kk < 16; ++kk) {
+          for (int kk = 0; kk < P2_KS; ++kk) {
             const float4 a4 = ld4(Ac + kk * 64 + ts * 4);
             const ulonglong2 b4 = ld4p(Bc + kk * 64 + ti * 4);
             const float av[4] = {a4.x, a4.y, a4.z, a4.w};
@@ -283,7 +294,7 @@ __global__ void __launch_bounds__(P2_THREADS, 1)
       }
       if (rd >= 1) cluster_wait();  // every rank has finished reading round rd - 2
       if (mine) {
-        float* const P = Pbuf + (rd & 1) * 4096;
+        float* const P = Pbuf + ((rd & 1) * P2_MAX_GC + rank) * 4096;  // this block's tile
 #pragma unroll
         for (int b = 0; b < 4; ++b) {
           const int64_t i = ib + ti * 4 + b;
@@ -300,14 +311,16 @@ __global__ void __launch_bounds__(P2_THREADS, 1)
             cacc[a] += w[a];
             zacc[a] = fmaf(w[a], yb, zacc[a]);
           }
-          st4(P + (ti * 4 + b) * 64 + ts * 4, make_float4(w[0], w[1], w[2], w[3]));
+          const float4 w4 = make_float4(w[0], w[1], w[2], w[3]);
+          for (int q = 0; q < gc; ++q)  // own copy and every other rank's
+            st4(cluster.map_shared_rank(P, q) + (ti * 4 + b) * 64 + ts * 4, w4);
         }
       }
       cluster_arrive();  // the weights of round rd are in place
     }
     if (rounds >= 1) cluster_wait();
     cluster_arrive();
-    cluster_wait();  // no rank leaves while another may still read its weight tiles
+    cluster_wait();  // no rank leaves while another may still access its shared memory
     if (cgrp == 0) {
       float* red = As;  // [16][64] c, then [16][64] zb (group A's stages are idle now)
       group_bar(1);
@@ -341,7 +354,7 @@ __global__ void __launch_bounds__(P2_THREADS, 1)
       cluster_arrive();  // finished reading round rd - 1
       cluster_wait();    // the weights of round rd are in place
       if (rd == rounds) break;
-      const float* const P = Pbuf + (rd & 1) * 4096;
+      const float* const P = Pbuf + (rd & 1) * P2_MAX_GC * 4096;
       const int nq = min(gc, b_end - (b_begin + rd * gc));
       const int nchunks = nq * 4;  // 16-observation chunks
       auto issue = [&](int cidx) {
@@ -367,7 +380,7 @@ __global__ void __launch_bounds__(P2_THREADS, 1)
         group_bar(2);
         issue(cidx + 2);
         const int q = cidx >> 2, ic = (cidx & 3) * 16;
-        const float* Pq = cluster.map_shared_rank(P, q) + ic * 64 + sg * 8;
+        const float* Pq = P + q * 4096 + ic * 64 + sg * 8;
         const float* Yb = Ys + (cidx % P2_NST) * 4096;
 #pragma unroll
         for (int k = 0; k < 16; ++k) {
@@ -412,7 +425,7 @@ void plan_simt(srmra_ctx* c) {
   p.p1_groups = (int)ceil_div(n_tiles, p.p1_tiles_per_group);
 
   const int chunks = (int)ceil_div(g.l2, P2_BP);
-  p.p2_chunk_groups = (int)ceil_div(chunks, 8);
+  p.p2_chunk_groups = (int)ceil_div(chunks, P2_MAX_GC);
   p.p2_gc = (int)ceil_div(chunks, p.p2_chunk_groups);
   const int n_iblk2 = (int)(g.Npad / P2_BI);
   const int64_t per_split = (int64_t)p.p2_gc * (g.Spad / P2_BS) * p.p2_chunk_groups;
