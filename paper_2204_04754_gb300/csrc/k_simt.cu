@@ -182,11 +182,12 @@ __global__ void __launch_bounds__(256, 2)
 // round orders them: group A arrives after writing the weights of round p, group C
 // after it has finished reading round p - 1 (whose buffer round p + 1 reuses); group A
 // waits on it before writing a buffer, group C before reading one.  Each group stages
-// its operands through a 3-deep cp.async ring synchronised by its own named barrier.
+// its operands through a 2-deep cp.async ring synchronised by its own named barrier.
+constexpr int P2_ATHREADS = 256;
 constexpr int P2_THREADS = 512;
-constexpr int P2_NST = 3;     // cp.async stages per group
+constexpr int P2_NST = 2;     // cp.async stages per group
 constexpr int P2_MAX_GC = 4;  // cluster width (weight tiles held per round)
-constexpr int P2_KS = 32;     // group A: pixels (k) per stage
+constexpr int P2_KS = 64;     // group A: pixels (k) per stage
 constexpr int P2_SMEM_FLOATS = 2 * P2_MAX_GC * 64 * 64      // P[2][gc][64 obs][64 shifts]
                                + P2_NST * 2 * P2_KS * 64    // group A: As, Bs [stage][KS][64]
                                + P2_NST * 16 * 256;         // group C: Ys [stage][16][256]
@@ -200,7 +201,7 @@ __device__ __forceinline__ void cp16(float* dst, const float* src, bool valid) {
                : "memory");
 }
 __device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
-__device__ __forceinline__ void cp_wait1() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
+__device__ __forceinline__ void cp_wait0() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
 __device__ __forceinline__ void group_bar(int id) {
   asm volatile("bar.sync %0, 256;" ::"r"(id) : "memory");
 }
@@ -235,7 +236,7 @@ __global__ void __launch_bounds__(P2_THREADS, 1)
   const int rounds = (nb + gc - 1) / gc;
   const int nks = (ldy + P2_KS - 1) / P2_KS;  // rows past ldy are zero-filled
 
-  if (threadIdx.x < 256) {
+  if (threadIdx.x < P2_ATHREADS) {
     // ------------------------------------------------------------------ group A
     const int tid = threadIdx.x;
     const int ts = tid & 15, ti = tid >> 4;  // 4 shifts x 4 observations
@@ -271,11 +272,10 @@ __global__ void __launch_bounds__(P2_THREADS, 1)
         };
         group_bar(1);  // the stage buffers of the previous round are no longer read
         issue(0);
-        issue(1);
         for (int ks = 0; ks < nks; ++ks) {
-          cp_wait1();
+          cp_wait0();
           group_bar(1);
-          issue(ks + 2);
+          issue(ks + 1);  // into the buffer of stage ks - 1, free after the barrier
           const float* Ac = As + (ks % P2_NST) * P2_KS * 64;
           const float* Bc = Bs + (ks % P2_NST) * P2_KS * 64;
 #pragma unroll
@@ -343,7 +343,7 @@ __global__ void __launch_bounds__(P2_THREADS, 1)
     }
   } else {
     // ------------------------------------------------------------------ group C
-    const int tid = threadIdx.x - 256;
+    const int tid = threadIdx.x - P2_ATHREADS;
     const int sg = tid >> 5, pg = tid & 31;  // 8 shifts x 8 pixels
     f2 z2[8][4];  // z2[a][b/2] holds Z' entries (a, b) and (a, b + 1)
 #pragma unroll
@@ -374,11 +374,10 @@ __global__ void __launch_bounds__(P2_THREADS, 1)
       };
       group_bar(2);  // the stage buffers of the previous round are no longer read
       issue(0);
-      issue(1);
       for (int cidx = 0; cidx < nchunks; ++cidx) {
-        cp_wait1();
+        cp_wait0();
         group_bar(2);
-        issue(cidx + 2);
+        issue(cidx + 1);  // into the buffer of stage cidx - 1, free after the barrier
         const int q = cidx >> 2, ic = (cidx & 3) * 16;
         const float* Pq = P + q * 4096 + ic * 64 + sg * 8;
         const float* Yb = Ys + (cidx % P2_NST) * 4096;
