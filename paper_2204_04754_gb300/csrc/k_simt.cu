@@ -13,6 +13,10 @@
 // distributed shared memory, so no CTA recomputes another's logits.
 #include <cooperative_groups.h>
 
+#include <algorithm>
+#include <map>
+#include <mutex>
+
 #include "srmra_internal.cuh"
 
 namespace cg = cooperative_groups;
@@ -163,18 +167,25 @@ __global__ void __launch_bounds__(256, 2)
 }
 
 // ----------------------------------------------------------------------------- pass 2
-// Cluster of gc CTAs (blockIdx.x = rank), one 64-shift tile (blockIdx.y), one
-// observation range x chunk group (blockIdx.z).  Each round covers gc blocks of 64
-// observations: rank q computes the 64x64 weight tile of block q of the round, and
-// every rank accumulates Z' over its own 256-pixel chunk for all gc blocks of the
-// round.  Every rank holds the weight tiles of all gc blocks of a round: the rank that
-// computes a tile stores it into its own shared memory and into every other rank's
-// (remote stores through distributed shared memory, which do not wait for a reply),
-// so the M-step loop reads only local shared memory.
+// Work: for every 64-shift tile and group of gc 256-pixel chunks (a "unit"), the
+// observation blocks of 64 are taken gc at a time ("rounds", R per unit); in a round,
+// rank q of a cluster of gc CTAs computes the 64x64 weight tile of block q, and every
+// rank accumulates Z' over its own pixel chunk for all gc blocks.  The launch is
+// persistent: one cluster per co-resident slot, and cluster c walks the items
+// [c T / ncl, (c + 1) T / ncl) of the T = units x R rounds in order, so a unit is split
+// between at most a few consecutive clusters.  Each cluster writes the partial sums of
+// its part of a unit into its own segment (its index minus that of the unit's first
+// cluster); the cluster that finishes a unit zero-fills the segments after its own, so
+// the finalize sums nseg segments for every shift.
+//
+// Every rank holds the weight tiles of all gc blocks of a round: the rank that computes
+// a tile stores it into its own shared memory and into every other rank's (remote
+// stores through distributed shared memory, which do not wait for a reply), so the
+// M-step loop reads only local shared memory.
 //
 // The 512 threads of a CTA form two groups that work one round apart:
 //   group A (threads 0-255): logits S[s][i] = <T'_s, y'_i> of the next round's block
-//     (4x4 outputs per thread), then w = 2^(logit2 - lse2) into the weight buffer and
+//     (4x4 outputs per thread), then w = 2^(logit2 - lse2) into the weight buffers and
 //     the partial sums c[s], zb[s];
 //   group C (threads 256-511): Z'[s][p] += sum_i w[i][s] y'_i[p] for the current round
 //     (8 shifts x 8 pixels per thread).
@@ -217,8 +228,8 @@ __global__ void __launch_bounds__(P2_THREADS, 1)
              const float* __restrict__ AxT, int Spad, int ldy,
              const float* __restrict__ ybar, const float* __restrict__ colb,
              const float* __restrict__ colm, const float* __restrict__ lse2, float a2,
-             float c2, int64_t N, int S, int n_iblk, int iblk_per_split, int gc,
-             int n_cgroups, float* __restrict__ Zp, float* __restrict__ cp,
+             float c2, int64_t N, int S, int n_iblk, int gc, int n_cgroups, int R,
+             int64_t T, int ncl, int nseg, float* __restrict__ Zp, float* __restrict__ cp,
              float* __restrict__ zbp) {
   extern __shared__ __align__(16) float smem[];
   float* const Pbuf = smem;                              // [2][gc][64 obs][64 shifts]
@@ -227,30 +238,41 @@ __global__ void __launch_bounds__(P2_THREADS, 1)
   float* const Ys = Bs + P2_NST * P2_KS * 64;            // [P2_NST][16][256] pixels
   cg::cluster_group cluster = cg::this_cluster();
   const int rank = (int)cluster.block_rank();
-  const int s0 = blockIdx.y * 64;
-  const int split = blockIdx.z / n_cgroups, cgrp = blockIdx.z % n_cgroups;
-  const int p0 = (cgrp * gc + rank) * 256;
-  const int b_begin = split * iblk_per_split;
-  const int b_end = min(n_iblk, b_begin + iblk_per_split);
-  const int nb = max(0, b_end - b_begin);
-  const int rounds = (nb + gc - 1) / gc;
+  const int cid = (int)(blockIdx.x / gc);
+  const int64_t t_begin = (int64_t)cid * T / ncl, t_end = (int64_t)(cid + 1) * T / ncl;
   const int nks = (ldy + P2_KS - 1) / P2_KS;  // rows past ldy are zero-filled
+  // segment of unit u written by this cluster: its index minus that of the cluster
+  // holding the unit's first item
+  auto segment = [&](int64_t u) -> int {
+    const int64_t t0 = u * R;
+    int64_t c = t0 * ncl / T;
+    while (c + 1 < ncl && (c + 1) * T / ncl <= t0) ++c;
+    return cid - (int)c;
+  };
 
   if (threadIdx.x < P2_ATHREADS) {
     // ------------------------------------------------------------------ group A
     const int tid = threadIdx.x;
     const int ts = tid & 15, ti = tid >> 4;  // 4 shifts x 4 observations
     const int lk = tid >> 4, lc = (tid & 15) * 4;
-    float cacc[4] = {0.f, 0.f, 0.f, 0.f}, zacc[4] = {0.f, 0.f, 0.f, 0.f};
-    float cbA[4], cmA[4];
+    float cacc[4], zacc[4], cbA[4], cmA[4];
+    int64_t cur_u = -1;
+    for (int64_t t = t_begin; t < t_end; ++t) {
+      const int64_t u = t / R, tl = t - t_begin;
+      const int r = (int)(t % R);
+      const int cgrp = (int)(u % n_cgroups);
+      const int s0 = (int)(u / n_cgroups) * 64;
+      if (u != cur_u) {
+        cur_u = u;
 #pragma unroll
-    for (int a = 0; a < 4; ++a) {
-      cbA[a] = colb[s0 + ts * 4 + a];
-      cmA[a] = colm[s0 + ts * 4 + a];
-    }
-    for (int rd = 0; rd < rounds; ++rd) {
-      const int myb = b_begin + rd * gc + rank;
-      const bool mine = myb < b_end;
+        for (int a = 0; a < 4; ++a) {
+          cacc[a] = zacc[a] = 0.f;
+          cbA[a] = colb[s0 + ts * 4 + a];
+          cmA[a] = colm[s0 + ts * 4 + a];
+        }
+      }
+      const int myb = r * gc + rank;
+      const bool mine = myb < n_iblk;
       const int64_t ib = (int64_t)myb * 64;
       f2 acc2[4][2];  // acc2[a][b/2] holds S entries (a, b) and (a, b + 1)
 #pragma unroll
@@ -270,7 +292,7 @@ __global__ void __launch_bounds__(P2_THREADS, 1)
           }
           cp_commit();
         };
-        group_bar(1);  // the stage buffers of the previous round are no longer read
+        group_bar(1);  // the stage buffers (and the reduction area) are no longer read
         issue(0);
         for (int ks = 0; ks < nks; ++ks) {
           cp_wait0();
@@ -292,9 +314,9 @@ __global__ void __launch_bounds__(P2_THREADS, 1)
           }
         }
       }
-      if (rd >= 1) cluster_wait();  // every rank has finished reading round rd - 2
+      if (tl >= 1) cluster_wait();  // every rank has finished reading round tl - 2
       if (mine) {
-        float* const P = Pbuf + ((rd & 1) * P2_MAX_GC + rank) * 4096;  // this block's tile
+        float* const P = Pbuf + ((tl & 1) * P2_MAX_GC + rank) * 4096;  // this block's tile
 #pragma unroll
         for (int b = 0; b < 4; ++b) {
           const int64_t i = ib + ti * 4 + b;
@@ -316,31 +338,37 @@ __global__ void __launch_bounds__(P2_THREADS, 1)
             st4(cluster.map_shared_rank(P, q) + (ti * 4 + b) * 64 + ts * 4, w4);
         }
       }
-      cluster_arrive();  // the weights of round rd are in place
+      cluster_arrive();  // the weights of round tl are in place
+      if (cgrp == 0 && (r == R - 1 || t == t_end - 1)) {
+        // this cluster's part of the unit ends here: its partial c and zb
+        float* red = As;  // [16][64] c, then [16][64] zb
+        group_bar(1);
+#pragma unroll
+        for (int a = 0; a < 4; ++a) {
+          red[ti * 64 + ts * 4 + a] = cacc[a];
+          red[1024 + ti * 64 + ts * 4 + a] = zacc[a];
+        }
+        group_bar(1);
+        if (tid < 64) {
+          float c = 0.f, zb = 0.f;
+          for (int k = 0; k < 16; ++k) {
+            c += red[k * 64 + tid];
+            zb += red[1024 + k * 64 + tid];
+          }
+          const int seg = segment(u);
+          cp[((int64_t)seg * gc + rank) * Spad + s0 + tid] = c;
+          zbp[((int64_t)seg * gc + rank) * Spad + s0 + tid] = zb;
+          if (r == R - 1)  // the unit is complete: no later segment exists
+            for (int sg2 = seg + 1; sg2 < nseg; ++sg2) {
+              cp[((int64_t)sg2 * gc + rank) * Spad + s0 + tid] = 0.f;
+              zbp[((int64_t)sg2 * gc + rank) * Spad + s0 + tid] = 0.f;
+            }
+        }
+      }
     }
-    if (rounds >= 1) cluster_wait();
+    cluster_wait();
     cluster_arrive();
     cluster_wait();  // no rank leaves while another may still access its shared memory
-    if (cgrp == 0) {
-      float* red = As;  // [16][64] c, then [16][64] zb (group A's stages are idle now)
-      group_bar(1);
-#pragma unroll
-      for (int a = 0; a < 4; ++a) {
-        red[ti * 64 + ts * 4 + a] = cacc[a];
-        red[1024 + ti * 64 + ts * 4 + a] = zacc[a];
-      }
-      group_bar(1);
-      if (tid < 64) {
-        float c = 0.f, zb = 0.f;
-        for (int k = 0; k < 16; ++k) {
-          c += red[k * 64 + tid];
-          zb += red[1024 + k * 64 + tid];
-        }
-        const int64_t part = (int64_t)split * gc + rank;
-        cp[part * Spad + s0 + tid] = c;
-        zbp[part * Spad + s0 + tid] = zb;
-      }
-    }
   } else {
     // ------------------------------------------------------------------ group C
     const int tid = threadIdx.x - P2_ATHREADS;
@@ -350,18 +378,23 @@ __global__ void __launch_bounds__(P2_THREADS, 1)
     for (int a = 0; a < 8; ++a)
 #pragma unroll
       for (int b = 0; b < 4; ++b) z2[a][b] = 0ull;
-    for (int rd = 0; rd <= rounds; ++rd) {
-      cluster_arrive();  // finished reading round rd - 1
-      cluster_wait();    // the weights of round rd are in place
-      if (rd == rounds) break;
-      const float* const P = Pbuf + (rd & 1) * P2_MAX_GC * 4096;
-      const int nq = min(gc, b_end - (b_begin + rd * gc));
+    for (int64_t t = t_begin; t <= t_end; ++t) {
+      const int64_t tl = t - t_begin;
+      cluster_arrive();  // finished reading round tl - 1
+      cluster_wait();    // the weights of round tl are in place
+      if (t == t_end) break;
+      const int64_t u = t / R;
+      const int r = (int)(t % R);
+      const int s0 = (int)(u / n_cgroups) * 64;
+      const int p0 = ((int)(u % n_cgroups) * gc + rank) * 256;
+      const float* const P = Pbuf + (tl & 1) * P2_MAX_GC * 4096;
+      const int nq = min(gc, n_iblk - r * gc);
       const int nchunks = nq * 4;  // 16-observation chunks
       auto issue = [&](int cidx) {
         const int st = cidx % P2_NST;
         if (cidx < nchunks) {
           const int q = cidx >> 2, ic = (cidx & 3) * 16;
-          const int64_t ib = (int64_t)(b_begin + rd * gc + q) * 64 + ic;
+          const int64_t ib = (int64_t)(r * gc + q) * 64 + ic;
 #pragma unroll
           for (int j = 0; j < 4; ++j) {
             const int row = (tid >> 6) + 4 * j, col = (tid & 63) * 4;
@@ -397,20 +430,33 @@ __global__ void __launch_bounds__(P2_THREADS, 1)
           }
         }
       }
-    }
-    // partial M-step sums of this (observation range, shift tile, pixel chunk)
+      if (r == R - 1 || t == t_end - 1) {
+        // this cluster's part of the unit ends here: its partial Z' over the chunk
+        const int seg = segment(u);
+        const int pa = p0 + pg * 4, pb = p0 + 128 + pg * 4;
 #pragma unroll
-    for (int a = 0; a < 8; ++a) {
-      const int s = s0 + sg * 8 + a;
-      float* zr = Zp + ((int64_t)split * Spad + s) * ldy;
-      const int pa = p0 + pg * 4, pb = p0 + 128 + pg * 4;
-      if (pa < ldy) st4p(zr + pa, z2[a][0], z2[a][1]);
-      if (pb < ldy) st4p(zr + pb, z2[a][2], z2[a][3]);
+        for (int a = 0; a < 8; ++a) {
+          const int s = s0 + sg * 8 + a;
+          float* zr = Zp + ((int64_t)seg * Spad + s) * ldy;
+          if (pa < ldy) st4p(zr + pa, z2[a][0], z2[a][1]);
+          if (pb < ldy) st4p(zr + pb, z2[a][2], z2[a][3]);
+#pragma unroll
+          for (int b = 0; b < 4; ++b) z2[a][b] = 0ull;
+          if (r == R - 1)  // the unit is complete: no later segment exists
+            for (int sg2 = seg + 1; sg2 < nseg; ++sg2) {
+              float* zz = Zp + ((int64_t)sg2 * Spad + s) * ldy;
+              if (pa < ldy) st4(zz + pa, make_float4(0.f, 0.f, 0.f, 0.f));
+              if (pb < ldy) st4(zz + pb, make_float4(0.f, 0.f, 0.f, 0.f));
+            }
+        }
+      }
     }
   }
 }
 
 }  // namespace
+
+int p2_clusters(int gc, int num_sms);
 
 void plan_simt(srmra_ctx* c) {
   const Geom& g = c->g;
@@ -427,15 +473,26 @@ void plan_simt(srmra_ctx* c) {
   p.p2_chunk_groups = (int)ceil_div(chunks, P2_MAX_GC);
   p.p2_gc = (int)ceil_div(chunks, p.p2_chunk_groups);
   const int n_iblk2 = (int)(g.Npad / P2_BI);
-  const int64_t per_split = (int64_t)p.p2_gc * (g.Spad / P2_BS) * p.p2_chunk_groups;
-  int ns = (int)((4 * (int64_t)slots + per_split / 2) / per_split);
-  const int max_ns = (n_iblk2 + p.p2_gc - 1) / p.p2_gc;
-  ns = ns < 1 ? 1 : (ns > max_ns ? max_ns : ns);
-  if (ns > 32) ns = 32;
-  p.p2_iblk_per_split = (int)round_up(ceil_div(n_iblk2, ns), p.p2_gc);
-  p.p2_nsplit = (int)ceil_div(n_iblk2, p.p2_iblk_per_split);
-  p.nparts_z = p.p2_nsplit;
-  p.nparts_c = p.p2_nsplit * p.p2_gc;
+  const int R = (int)ceil_div(n_iblk2, p.p2_gc);
+  const int64_t U = (int64_t)(g.Spad / P2_BS) * p.p2_chunk_groups;
+  const int64_t T = U * R;
+  const int ncl = (int)std::min<int64_t>(p2_clusters(p.p2_gc, c->num_sms), T);
+  auto first_cluster = [&](int64_t t0) {
+    int64_t cl = t0 * ncl / T;
+    while (cl + 1 < ncl && (cl + 1) * T / ncl <= t0) ++cl;
+    return cl;
+  };
+  int nseg = 1;
+  for (int64_t u = 0; u < U; ++u)
+    nseg = std::max(nseg, (int)(first_cluster((u + 1) * R - 1) - first_cluster(u * R) + 1));
+  p.p2_rounds = R;
+  p.p2_items = T;
+  p.p2_ncl = ncl;
+  p.p2_nseg = nseg;
+  p.p2_iblk_per_split = R * p.p2_gc;
+  p.p2_nsplit = nseg;
+  p.nparts_z = nseg;
+  p.nparts_c = nseg * p.p2_gc;
   p.ll_blocks = (int)ceil_div(g.Npad, 256);
 }
 
@@ -455,6 +512,43 @@ cudaError_t simt_set_attributes() {
                               (int)P2_SMEM_BYTES);
 }
 
+// Clusters of gc pass-2 CTAs that are resident at once on the current device (one CTA
+// per SM; clusters must fit within a GPU processing cluster, so this can be below
+// num_sms / gc).  Without a device, num_sms / gc, which is an upper bound: more clusters
+// only ever split a unit into more segments.
+int p2_clusters(int gc, int num_sms) {
+  const int bound = std::max(1, num_sms / gc);
+  int dev = -1;
+  if (cudaGetDevice(&dev) != cudaSuccess) {
+    cudaGetLastError();
+    return bound;
+  }
+  static std::mutex mu;
+  static std::map<std::pair<int, int>, int> cache;
+  std::lock_guard<std::mutex> lock(mu);
+  auto it = cache.find({dev, gc});
+  if (it != cache.end()) return it->second;
+  int n = 0;
+  if (simt_set_attributes() == cudaSuccess) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)(gc * bound), 1, 1);
+    cfg.blockDim = dim3(P2_THREADS, 1, 1);
+    cfg.dynamicSmemBytes = P2_SMEM_BYTES;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = (unsigned)gc;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    if (cudaOccupancyMaxActiveClusters(&n, k_p2_f32, &cfg) != cudaSuccess) n = 0;
+  }
+  cudaGetLastError();
+  if (n < 1 || n > bound) n = bound;
+  cache[{dev, gc}] = n;
+  return n;
+}
+
 cudaError_t launch_pass2_f32(srmra_ctx* c) {
   static bool attr_done = false;
   if (!attr_done) {
@@ -466,8 +560,7 @@ cudaError_t launch_pass2_f32(srmra_ctx* c) {
   const Plan& p = c->plan;
   const LogitScalars ls = logit_scalars(g);
   cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = dim3((unsigned)p.p2_gc, (unsigned)(g.Spad / P2_BS),
-                     (unsigned)(p.p2_nsplit * p.p2_chunk_groups));
+  cfg.gridDim = dim3((unsigned)(p.p2_gc * p.p2_ncl), 1, 1);
   cfg.blockDim = dim3(P2_THREADS, 1, 1);
   cfg.dynamicSmemBytes = P2_SMEM_BYTES;
   cfg.stream = c->stream;
@@ -483,8 +576,8 @@ cudaError_t launch_pass2_f32(srmra_ctx* c) {
                                      g.Npad, (const float*)c->AxT, g.Spad, g.ldy,
                                      (const float*)c->ybar, (const float*)c->colb,
                                      (const float*)c->colm, (const float*)c->lse2, ls.a2, ls.c2,
-                                     g.N, g.S, n_iblk2, p.p2_iblk_per_split, p.p2_gc,
-                                     p.p2_chunk_groups, c->Zp, c->cp, c->zbp);
+                                     g.N, g.S, n_iblk2, p.p2_gc, p.p2_chunk_groups, p.p2_rounds,
+                                     p.p2_items, p.p2_ncl, p.p2_nseg, c->Zp, c->cp, c->zbp);
   c->launches++;
   return e;
 }
