@@ -171,10 +171,13 @@ __global__ void __launch_bounds__(256, 2)
 // observation blocks of 64 are taken gc at a time ("rounds", R per unit); in a round,
 // rank q of a cluster of gc CTAs computes the 64x64 weight tile of block q, and every
 // rank accumulates Z' over its own pixel chunk for all gc blocks.  The launch is
-// persistent: one cluster per co-resident slot, and cluster c walks the items
-// [c T / ncl, (c + 1) T / ncl) of the T = units x R rounds in order, so a unit is split
-// between at most a few consecutive clusters.  Each cluster writes the partial sums of
-// its part of a unit into its own segment (its index minus that of the unit's first
+// persistent, one cluster per co-resident slot.  The first U1 = ncl floor(U / ncl)
+// units are dealt out whole (cluster c takes units c, c + ncl, ...), so all clusters
+// sweep the observations in step and each block is read from DRAM about once.  The
+// items (unit, round) of the remaining units are split into ncl contiguous ranges, one
+// per cluster, so a remaining unit is shared by a few consecutive clusters.  Each
+// cluster writes the partial sums of its part of a unit into its own segment (whole
+// units: segment 0; shared units: the cluster's index minus that of the unit's first
 // cluster); the cluster that finishes a unit zero-fills the segments after its own, so
 // the finalize sums nseg segments for every shift.
 //
@@ -229,7 +232,8 @@ __global__ void __launch_bounds__(P2_THREADS, 1)
              const float* __restrict__ ybar, const float* __restrict__ colb,
              const float* __restrict__ colm, const float* __restrict__ lse2, float a2,
              float c2, int64_t N, int S, int n_iblk, int gc, int n_cgroups, int R,
-             int64_t T, int ncl, int nseg, float* __restrict__ Zp, float* __restrict__ cp,
+             int64_t U, int64_t U1, int ncl, int nseg, float* __restrict__ Zp,
+             float* __restrict__ cp,
              float* __restrict__ zbp) {
   extern __shared__ __align__(16) float smem[];
   float* const Pbuf = smem;                              // [2][gc][64 obs][64 shifts]
@@ -239,14 +243,24 @@ __global__ void __launch_bounds__(P2_THREADS, 1)
   cg::cluster_group cluster = cg::this_cluster();
   const int rank = (int)cluster.block_rank();
   const int cid = (int)(blockIdx.x / gc);
-  const int64_t t_begin = (int64_t)cid * T / ncl, t_end = (int64_t)(cid + 1) * T / ncl;
+  const int64_t kw = U1 / ncl;  // whole units of this cluster
+  const int64_t T2 = (U - U1) * R;  // items of the shared units
+  const int64_t ncl2 = T2 < ncl ? T2 : ncl;  // clusters sharing them (non-empty ranges)
+  const int64_t t2b = cid < ncl2 ? (int64_t)cid * T2 / ncl2 : 0;
+  const int64_t t2e = cid < ncl2 ? (int64_t)(cid + 1) * T2 / ncl2 : 0;
+  const int64_t n_loc = kw * R + (t2e - t2b);
+  // j-th item of this cluster, as (unit) * R + (round)
+  auto item = [&](int64_t j) -> int64_t {
+    if (j < kw * R) return (cid + (j / R) * ncl) * R + j % R;
+    return U1 * R + t2b + (j - kw * R);
+  };
   const int nks = (ldy + P2_KS - 1) / P2_KS;  // rows past ldy are zero-filled
-  // segment of unit u written by this cluster: its index minus that of the cluster
-  // holding the unit's first item
+  // segment of unit u written by this cluster
   auto segment = [&](int64_t u) -> int {
-    const int64_t t0 = u * R;
-    int64_t c = t0 * ncl / T;
-    while (c + 1 < ncl && (c + 1) * T / ncl <= t0) ++c;
+    if (u < U1) return 0;
+    const int64_t t0 = (u - U1) * R;
+    int64_t c = t0 * ncl2 / T2;
+    while (c + 1 < ncl2 && (c + 1) * T2 / ncl2 <= t0) ++c;
     return cid - (int)c;
   };
 
@@ -257,8 +271,8 @@ __global__ void __launch_bounds__(P2_THREADS, 1)
     const int lk = tid >> 4, lc = (tid & 15) * 4;
     float cacc[4], zacc[4], cbA[4], cmA[4];
     int64_t cur_u = -1;
-    for (int64_t t = t_begin; t < t_end; ++t) {
-      const int64_t u = t / R, tl = t - t_begin;
+    for (int64_t tl = 0; tl < n_loc; ++tl) {
+      const int64_t t = item(tl), u = t / R;
       const int r = (int)(t % R);
       const int cgrp = (int)(u % n_cgroups);
       const int s0 = (int)(u / n_cgroups) * 64;
@@ -339,7 +353,7 @@ __global__ void __launch_bounds__(P2_THREADS, 1)
         }
       }
       cluster_arrive();  // the weights of round tl are in place
-      if (cgrp == 0 && (r == R - 1 || t == t_end - 1)) {
+      if (cgrp == 0 && (r == R - 1 || tl == n_loc - 1)) {
         // this cluster's part of the unit ends here: its partial c and zb
         float* red = As;  // [16][64] c, then [16][64] zb
         group_bar(1);
@@ -378,12 +392,11 @@ __global__ void __launch_bounds__(P2_THREADS, 1)
     for (int a = 0; a < 8; ++a)
 #pragma unroll
       for (int b = 0; b < 4; ++b) z2[a][b] = 0ull;
-    for (int64_t t = t_begin; t <= t_end; ++t) {
-      const int64_t tl = t - t_begin;
+    for (int64_t tl = 0; tl <= n_loc; ++tl) {
       cluster_arrive();  // finished reading round tl - 1
       cluster_wait();    // the weights of round tl are in place
-      if (t == t_end) break;
-      const int64_t u = t / R;
+      if (tl == n_loc) break;
+      const int64_t t = item(tl), u = t / R;
       const int r = (int)(t % R);
       const int s0 = (int)(u / n_cgroups) * 64;
       const int p0 = ((int)(u % n_cgroups) * gc + rank) * 256;
@@ -430,7 +443,7 @@ __global__ void __launch_bounds__(P2_THREADS, 1)
           }
         }
       }
-      if (r == R - 1 || t == t_end - 1) {
+      if (r == R - 1 || tl == n_loc - 1) {
         // this cluster's part of the unit ends here: its partial Z' over the chunk
         const int seg = segment(u);
         const int pa = p0 + pg * 4, pb = p0 + 128 + pg * 4;
@@ -477,16 +490,21 @@ void plan_simt(srmra_ctx* c) {
   const int64_t U = (int64_t)(g.Spad / P2_BS) * p.p2_chunk_groups;
   const int64_t T = U * R;
   const int ncl = (int)std::min<int64_t>(p2_clusters(p.p2_gc, c->num_sms), T);
+  const int64_t U1 = (U / ncl) * ncl, T2 = (U - U1) * R;
+  const int64_t ncl2 = std::min<int64_t>(ncl, T2);
   auto first_cluster = [&](int64_t t0) {
-    int64_t cl = t0 * ncl / T;
-    while (cl + 1 < ncl && (cl + 1) * T / ncl <= t0) ++cl;
+    int64_t cl = t0 * ncl2 / T2;
+    while (cl + 1 < ncl2 && (cl + 1) * T2 / ncl2 <= t0) ++cl;
     return cl;
   };
   int nseg = 1;
-  for (int64_t u = 0; u < U; ++u)
-    nseg = std::max(nseg, (int)(first_cluster((u + 1) * R - 1) - first_cluster(u * R) + 1));
+  for (int64_t u = U1; u < U; ++u) {
+    const int64_t t0 = (u - U1) * R;
+    nseg = std::max(nseg, (int)(first_cluster(t0 + R - 1) - first_cluster(t0) + 1));
+  }
   p.p2_rounds = R;
-  p.p2_items = T;
+  p.p2_units = U;
+  p.p2_units_whole = U1;
   p.p2_ncl = ncl;
   p.p2_nseg = nseg;
   p.p2_iblk_per_split = R * p.p2_gc;
@@ -577,7 +595,8 @@ cudaError_t launch_pass2_f32(srmra_ctx* c) {
                                      (const float*)c->ybar, (const float*)c->colb,
                                      (const float*)c->colm, (const float*)c->lse2, ls.a2, ls.c2,
                                      g.N, g.S, n_iblk2, p.p2_gc, p.p2_chunk_groups, p.p2_rounds,
-                                     p.p2_items, p.p2_ncl, p.p2_nseg, c->Zp, c->cp, c->zbp);
+                                     p.p2_units, p.p2_units_whole, p.p2_ncl, p.p2_nseg, c->Zp,
+                                     c->cp, c->zbp);
   c->launches++;
   return e;
 }

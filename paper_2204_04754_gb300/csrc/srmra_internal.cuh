@@ -72,7 +72,8 @@ struct Plan {
   int p2_nsplit = 1;        // observation ranges with separate M-step partial sums
   int p2_iblk_per_split = 1;
   int p2_rounds = 1;        // float32 pass 2: rounds per (shift tile, chunk group) unit
-  int64_t p2_items = 1;     // float32 pass 2: units x rounds, walked by the clusters
+  int64_t p2_units = 1;     // float32 pass 2: (shift tile, chunk group) units
+  int64_t p2_units_whole = 0;  // float32 pass 2: units dealt out whole to the clusters
   int p2_ncl = 1;           // float32 pass 2: persistent clusters
   int p2_nseg = 1;          // float32 pass 2: partial-sum segments per unit
   int nparts_c = 1;         // number of partial c / zb slices

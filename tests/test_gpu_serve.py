@@ -39,7 +39,9 @@ def test_results_same_alone_and_in_the_mix(S, prec):
         s.solve(it, 1)
         alone.append(s.state())
         s.close()
-    budget = sum(S.srmra_estimate_device_bytes(p.L, p.K, p.N, p.sigma, prec) for p in probs[:3])
+    need = [S.srmra_estimate_device_bytes(p.L, p.K, p.N, p.sigma, prec) for p in probs]
+    # room for about three requests at once, and for every request on its own
+    budget = max(sum(need[:3]), max(need))
     srv = S.Server(budget, max_active=4, prec=prec)
     # staggered arrivals: two now, the rest while those are running
     ids = [srv.submit(p.L, p.K, p.sigma, p.y, it) for p, it in zip(probs[:2], iters[:2])]
