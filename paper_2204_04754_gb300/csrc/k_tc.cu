@@ -685,7 +685,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
   uint64_t* zempty = zfull + 1;
   uint64_t* mfull = zempty + 1;  // [MBOX_DEPTH]: one barrier per mailbox row
   uint64_t* drain = mfull + MBOX_DEPTH;
-  uint32_t* mbox = (uint32_t*)(drain + 1);  // [MBOX_DEPTH][4] reserved slot indices
+  uint64_t* wready = drain + 1;  // the 128 epilogue threads have written the weight tile
+  uint32_t* mbox = (uint32_t*)(wready + 1);  // [MBOX_DEPTH][4] reserved slot indices
   uint32_t* tptr = mbox + MBOX_DEPTH * 4;
   volatile int* abort = (volatile int*)(tptr + 1);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -705,6 +706,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     mbar_init(zempty, 128);
     for (int k = 0; k < MBOX_DEPTH; ++k) mbar_init(&mfull[k], G);
     mbar_init(drain, 1);
+    mbar_init(wready, 128);
     *abort = 0;
     fence_mbar_init();
   }
@@ -772,11 +774,16 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
               }
             }
           }
+          // the slots of round j - 1: the weight tile of block rp + kq (filled by CTA kq)
+          // is reserved one block ahead of the two Y'^T tiles it multiplies, i.e. in the
+          // order W0 W1 T0 T0 W2 T1 T1 W3 T2 T2 T3 T3.  Every Y'^T tile then lies within
+          // P2C_SLOTS - 1 places of its weight slot, so no fill waits for a slot that is
+          // only freed by the products that need that fill, while the tiles of the other
+          // CTAs can still be sent early.
           const int rp = (j - 1) * G, nqp = j >= 1 ? min(G, nb - rp) : 0;
-          for (int kq = 0; ok && kq < nqp; ++kq) {
-            // a slot for the weight tile of block rp + kq, filled by CTA kq
+          auto reserve_w = [&](int kq) {
             const int st = reserve(kq != (int)rank);
-            if (!ok) break;
+            if (!ok) return;
             // row sent % DEPTH of peer kq's mailbox, and that row's own barrier, so the
             // arrivals of different rounds can never complete each other's phases
             const uint32_t row = sent[kq] % MBOX_DEPTH;
@@ -784,15 +791,17 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             mbar_arrive_cluster(mapa(smem_u32(&mfull[row]), kq));
             ++sent[kq];
             ++it;
-            if (cvalid) {
-              const int ib = (jb0 + rp + kq) * 128;
-              for (int h = 0; ok && h < 2; ++h) {
-                const int s2 = reserve(false);
-                if (!ok) break;
-                mbar_expect_tx(&full[s2], 32768);
-                tma_load_2d(smem + s2 * SLOT, &I->tmYT, &full[s2], ib + h * 64, chunk * 256);
-                ++it;
-              }
+          };
+          if (nqp > 0) reserve_w(0);
+          for (int kq = 0; ok && kq < nqp; ++kq) {
+            if (kq + 1 < nqp) reserve_w(kq + 1);
+            const int ib = (jb0 + rp + kq) * 128;
+            for (int h = 0; ok && cvalid && h < 2; ++h) {
+              const int s2 = reserve(false);
+              if (!ok) break;
+              mbar_expect_tx(&full[s2], 32768);
+              tma_load_2d(smem + s2 * SLOT, &I->tmYT, &full[s2], ib + h * 64, chunk * 256);
+              ++it;
             }
           }
         }
@@ -877,10 +886,19 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             ++sc;
           }
           const int nqp = j >= 1 ? min(G, nb - (j - 1) * G) : 0;
-          for (int kq = 0; ok && kq < nqp; ++kq) {
-            const int stP = wait_slot();
-            if (!ok) break;
+          // same slot order as the producer: W0 W1 T0 T0 W2 T1 T1 W3 T2 T2 T3 T3
+          int stPs[4] = {0, 0, 0, 0};
+          if (nqp > 0) {
+            stPs[0] = wait_slot();
             ++it;
+          }
+          for (int kq = 0; ok && kq < nqp; ++kq) {
+            if (kq + 1 < nqp) {
+              stPs[kq + 1] = wait_slot();
+              ++it;
+              if (!ok) break;
+            }
+            const int stP = stPs[kq];
             if (cvalid) {
               if (first_z && !mbar_wait(zempty, (uc & 1) ^ 1, abort)) {
                 ok = false;
@@ -953,15 +971,13 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         float ny = a.ybar[ib + lane];
         float nl = (ib + lane < a.N) ? a.lse2[ib + lane] : INFINITY;
         ok = __all_sync(0xffffffffu, mbar_wait(&sfull[b], (sc >> 1) & 1, abort));
-        if (ok)
-          ok = __all_sync(0xffffffffu,
-                          mbar_wait_cluster(&mfull[mr % MBOX_DEPTH], (mr / MBOX_DEPTH) & 1, abort));
         if (!ok) break;
         tc_fence_after();
-        const uint32_t* mrow = mbox + (mr % MBOX_DEPTH) * 4;
-        const int own = (int)mrow[rank];
-        uint8_t* prow = smem + own * SLOT + row * 128;
-#pragma unroll 1
+        // the weights of this row, as fp16 pairs in the order of the tile's columns; they
+        // are computed as soon as the logits are in TMEM, before the slot they go to has
+        // been granted, so that the logit buffer is released early
+        uint32_t packed[64];
+#pragma unroll
         for (int c = 0; c < 4; ++c) {
           __syncwarp();  // the warp is done with the previous chunk's terms
           wobs[lane] = make_float2(ny, nl);
@@ -974,7 +990,6 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
           float v[32];
           tmem_ld32(lane_addr + (uint32_t)(b * 128 + c * 32), v);
           tmem_ld_wait();
-          uint32_t packed[16];
 #pragma unroll
           for (int e = 0; e < 32; e += 2) {
             float w2[2];
@@ -990,33 +1005,44 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
               zacc = fmaf(w2[h], ybi, zacc);
             }
             const __half2 pr = __floats2half2_rn(w2[0], w2[1]);
-            packed[e >> 1] = *reinterpret_cast<const uint32_t*>(&pr);
-          }
-#pragma unroll
-          for (int g4 = 0; g4 < 4; ++g4) {
-            const int col16 = c * 4 + g4;
-            const int kb2 = col16 >> 3, cc = col16 & 7;
-            *reinterpret_cast<uint4*>(prow + kb2 * 16384 + ((cc ^ (row & 7)) << 4)) =
-                make_uint4(packed[4 * g4], packed[4 * g4 + 1], packed[4 * g4 + 2],
-                           packed[4 * g4 + 3]);
+            packed[c * 16 + (e >> 1)] = *reinterpret_cast<const uint32_t*>(&pr);
           }
         }
         tc_fence_before();
-        mbar_arrive(&sempty[b]);
-        fence_proxy_async_smem();
-        named_bar(1, 128);
-        if (row == 0) {
-          const uint8_t* src = smem + own * SLOT;
-          for (int j = 0; j < G; ++j) {
-            if (j == (int)rank) continue;
-            const int dst = (int)mrow[j];
-            bulk_copy_to_peer(mapa(smem_u32(smem + dst * SLOT), j), src, 32768,
-                              mapa(smem_u32(&full[dst]), j));
-          }
-          bulk_commit();
-          bulk_wait_read0();
-          mbar_arrive(&full[own]);
+        mbar_arrive(&sempty[b]);  // the logits are no longer needed
+        ok = __all_sync(0xffffffffu,
+                        mbar_wait_cluster(&mfull[mr % MBOX_DEPTH], (mr / MBOX_DEPTH) & 1, abort));
+        if (!ok) break;
+        const uint32_t* mrow = mbox + (mr % MBOX_DEPTH) * 4;
+        const int own = (int)mrow[rank];
+        uint8_t* prow = smem + own * SLOT + row * 128;
+#pragma unroll
+        for (int col16 = 0; col16 < 16; ++col16) {  // 16-byte units along the observations
+          const int kb2 = col16 >> 3, cc = col16 & 7;
+          *reinterpret_cast<uint4*>(prow + kb2 * 16384 + ((cc ^ (row & 7)) << 4)) =
+              make_uint4(packed[4 * col16], packed[4 * col16 + 1], packed[4 * col16 + 2],
+                         packed[4 * col16 + 3]);
         }
+        fence_proxy_async_smem();
+        mbar_arrive(wready);
+        bool sent_ok = true;
+        if (row == 0) {  // all 128 rows written: send the tile to the other CTAs
+          sent_ok = mbar_wait(wready, mr & 1, abort);
+          if (sent_ok) {
+            const uint8_t* src = smem + own * SLOT;
+            for (int j = 0; j < G; ++j) {
+              if (j == (int)rank) continue;
+              const int dst = (int)mrow[j];
+              bulk_copy_to_peer(mapa(smem_u32(smem + dst * SLOT), j), src, 32768,
+                                mapa(smem_u32(&full[dst]), j));
+            }
+            bulk_commit();
+            bulk_wait_read0();
+            mbar_arrive(&full[own]);
+          }
+        }
+        ok = __all_sync(0xffffffffu, sent_ok);
+        if (!ok) break;
         ++sc;
         ++mr;
       }
