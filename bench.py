@@ -6,7 +6,7 @@ observations x L^2 shifts, M-step, block-DCT projection.  The metric is observat
 shift pairs per second, N * L^2 * steps / device time.  Prints one JSON line.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl srmra|reference]
-                    [--workload NAME] [--prec fp32|bf16|bf16x3]
+                    [--workload NAME] [--prec fp32|bf16|bf16x3|fft32]
 
 Under torchrun (N > 1) every rank runs an independent replica of the workload (its own
 seeded instance): the method has no data exchange between independent problems, so
@@ -38,7 +38,7 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="srmra", choices=["srmra", "reference"])
     ap.add_argument("--workload", default=DEFAULT_WORKLOAD)
-    ap.add_argument("--prec", default=None, help="fp32 | bf16 | bf16x3 (default: workload's)")
+    ap.add_argument("--prec", default=None, help="fp32 | bf16 | bf16x3 | fft32 (default: workload's)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
@@ -69,7 +69,7 @@ def fp32_peak_tflops(sm_mhz: float) -> float:
     return NUM_SMS * FP32_LANES_PER_SM * 2 * sm_mhz * 1e6 / 1e12
 
 
-KERNEL_SOURCE = {"fp32": "k_simt.cu", "bf16": "k_tc.cu", "bf16x3": "k_tc.cu"}
+KERNEL_SOURCE = {"fp32": "k_simt.cu", "bf16": "k_tc.cu", "bf16x3": "k_tc.cu", "fft32": "k_fft.cu"}
 
 
 def traffic_from_profiles(kernel: str, workload: str, prec: str):
@@ -244,12 +244,13 @@ def time_steps(run_step, steps, stream, torch, flush):
     return [a.elapsed_time(b) for a, b in evs]
 
 
-def mixed_block(p, w, steps, warmup, srmra, torch, stream, flush, fp32_value):
-    """The same workload in the split-bf16 tensor-core form: pairs/s and speedup over the
-    fp32 form; and the error at which that speedup holds: one EM iteration of each form
-    from the same state (the fp32 run's state after the warm-up), compared."""
+def mixed_block(p, w, steps, warmup, srmra, torch, stream, flush, fp32_value, form="bf16x3"):
+    """The same workload in another form (split-bf16 tensor cores, or the polyphase FFT):
+    pairs/s and speedup over the fp32 form; and the error at which that speedup holds:
+    one EM iteration of each form from the same state (the fp32 run's state after the
+    warm-up), compared."""
     import numpy as np
-    s3 = srmra.Solver(p.L, p.K, p.sigma, p.y, prec="bf16x3", x0=p.x0, rho1=p.rho1_0,
+    s3 = srmra.Solver(p.L, p.K, p.sigma, p.y, prec=form, x0=p.x0, rho1=p.rho1_0,
                       rho2=p.rho2_0, stream=stream.cuda_stream)
     s3.solve(warmup, w["F"], sigma_bm1=1.0, loglik=False)
     ms = time_steps(lambda: s3.solve(1, w["F"], sigma_bm1=0.0, loglik=False), steps,
@@ -266,12 +267,16 @@ def mixed_block(p, w, steps, warmup, srmra, torch, stream, flush, fp32_value):
     s3.close()
     value = p.N * p.L * p.L * steps / (sum(ms) / 1e3)
     rel = lambda a, b: float(np.linalg.norm(a.astype(np.float64) - b) / np.linalg.norm(b))
-    return {"precision": "bf16x3", "value": value, "unit": "pairs/s",
+    note = {"bf16x3": "per-iteration parity with the FP64 oracle (<= 1e-4) is tested in "
+                      "tests/test_gpu_tc.py",
+            "fft32": "exact reformulation (polyphase correlation by l x l FFTs) in float32; "
+                     "per-iteration parity with the FP64 oracle (<= 1e-5) is tested in "
+                     "tests/test_gpu_fft.py"}[form]
+    return {"precision": form, "value": value, "unit": "pairs/s",
             "ms_per_step": sum(ms) / steps, "speedup_vs_fp32": value / fp32_value,
             "one_step_rel_diff_vs_fp32": {"x": rel(x3, x1), "rho1": rel(r13, r11),
                                           "rho2": rel(r23, r21)},
-            "note": "per-iteration parity with the FP64 oracle (<= 1e-4) is tested in "
-                    "tests/test_gpu_tc.py"}
+            "note": note}
 
 
 def run_batched(args, rank, world, local):
@@ -492,10 +497,17 @@ def main():
     # roofline of the dominant kernel (phase), from the live CUDA events
     peaks, peak_src = load_peaks()
     dom = max(("pass1", "pass2"), key=lambda k: phase_ms[k])
-    per_pair_flops = {"pass1": 2 * p.l * p.l, "pass2": 4 * p.l * p.l}[dom]
+    if prec == "fft32":
+        # per (observation, phase): one inverse l x l FFT (pass 1), plus the forward FFT
+        # of the weight map and the products (pass 2), 5 n log2 n flops per complex
+        # n-point FFT; spread over the l^2 lags (pairs) of the phase
+        lg = math.log2(p.l * p.l)
+        per_pair_flops = {"pass1": 5 * lg + 6, "pass2": 10 * lg + 14}[dom]
+    else:
+        per_pair_flops = {"pass1": 2 * p.l * p.l, "pass2": 4 * p.l * p.l}[dom]
     avg_launch_s = phase_ms[dom] / max(1, phase_n[dom]) / 1e3
     achieved = per_pair_flops * pairs_per_step / avg_launch_s / 1e12
-    if prec == "fp32":
+    if prec in ("fp32", "fft32"):
         sm_max = float(peaks.get("sm_max_mhz", 2070.0))
         peak = fp32_peak_tflops(sm_max)
         bound = "alu"
@@ -515,7 +527,7 @@ def main():
     out = {"metric": METRIC, "value": value, "unit": "pairs/s", "n_gpus": world,
            "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-           "dtype": {"fp32": "f32", "bf16": "bf16", "bf16x3": "bf16x3"}[prec],
+           "dtype": {"fp32": "f32", "bf16": "bf16", "bf16x3": "bf16x3", "fft32": "f32"}[prec],
            "data": "synthetic (seeded blob image, mixture shift distributions, Gaussian noise)",
            "config": {"workload": args.workload, "L_high": p.L, "K": p.K, "L_low": p.l,
                       "N": p.N, "sigma": p.sigma, "F": F, "precision": prec,
@@ -531,6 +543,9 @@ def main():
     if rank == 0 and prec == "fp32" and not args.no_mixed:
         out["bf16x3"] = mixed_block(p, w, args.steps, args.warmup, srmra, torch, stream, flush,
                                     value)
+        if p.l in (8, 16, 32):
+            out["fft32"] = mixed_block(p, w, args.steps, args.warmup, srmra, torch, stream,
+                                       flush, value, form="fft32")
     if rank == 0 and world == 1 and not args.no_cpu:
         cb = cpu_oracle_rate(p, args.cpu_seconds)
         cb.pop("n_sub", None)

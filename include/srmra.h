@@ -63,10 +63,23 @@ typedef enum {
  *   SRMRA_FP32   : float32 CUDA-core FMA (the plain form).
  *   SRMRA_BF16   : bf16 tensor-core operands, float32 accumulation and softmax.
  *   SRMRA_BF16X3 : split-bf16 (hi + lo) for the cross term, hi*hi + hi*lo + lo*hi on
- *                  tensor cores with float32 accumulation; bf16 weights for the
- *                  M-step sum.  The global log-likelihood is reduced in float64 in
- *                  every form. */
-typedef enum { SRMRA_FP32 = 0, SRMRA_BF16 = 1, SRMRA_BF16X3 = 2 } srmra_precision;
+ *                  tensor cores with float32 accumulation; fp16 weights (scaled by
+ *                  2^12) and fp16 y' for the M-step sum.
+ *   SRMRA_FFT32  : float32 polyphase-FFT form.  Per sub-image x_r of the K^2
+ *                  polyphase components, <y_i, P R_s x> over all lags t of phase r
+ *                  is the circular cross-correlation of y_i with x_r (Sec. 2, the
+ *                  structure behind Theorem 1), computed with l x l FFTs; the M-step
+ *                  right-hand side of Eq. (x_EM) likewise.  Same results as the
+ *                  dense forms up to rounding, O(N K^2 l^2 log l) instead of
+ *                  O(N L^2 l^2) flops.  Needs l = L/K in {8, 16, 32}; srmra_create
+ *                  returns SRMRA_EINVAL otherwise.
+ * The global log-likelihood is reduced in float64 in every form. */
+typedef enum {
+  SRMRA_FP32 = 0,
+  SRMRA_BF16 = 1,
+  SRMRA_BF16X3 = 2,
+  SRMRA_FFT32 = 3
+} srmra_precision;
 
 /* flags */
 #define SRMRA_FLAG_CHECK_NUMERIC 1u /* scan x, rho, LL for NaN/Inf after each iteration */

@@ -134,17 +134,22 @@ struct PhaseTimer {
 srmra_status run_iteration(srmra_ctx* c, int ll_index) {
   cudaError_t e = cudaSuccess;
   { PhaseTimer t(c, SRMRA_PHASE_PREP); launch_prep_iter(c); }
-  const bool tc = c->prec != SRMRA_FP32;
+  const bool tc = is_tc_prec(c->prec), fft = c->prec == SRMRA_FFT32;
   {
     PhaseTimer t(c, SRMRA_PHASE_PASS1);
     if (tc)
       e = launch_pass1_tc(c);
+    else if (fft)
+      launch_pass1_fft(c);
     else
       launch_pass1_f32(c);
   }
   if (e != cudaSuccess) return cuda_fail(c, e, "pass 1 launch");
   { PhaseTimer t(c, SRMRA_PHASE_COMBINE); launch_lse_combine(c, c->plan.p1_groups); }
-  { PhaseTimer t(c, SRMRA_PHASE_PASS2); e = tc ? launch_pass2_tc(c) : launch_pass2_f32(c); }
+  {
+    PhaseTimer t(c, SRMRA_PHASE_PASS2);
+    e = tc ? launch_pass2_tc(c) : fft ? launch_pass2_fft(c) : launch_pass2_f32(c);
+  }
   if (e != cudaSuccess) return cuda_fail(c, e, "pass 2 launch");
   { PhaseTimer t(c, SRMRA_PHASE_FINAL); launch_finalize(c, ll_index); }
   e = cudaGetLastError();
@@ -186,7 +191,12 @@ void setup_ctx(srmra_ctx* c, const srmra_params* p, int num_sms, int caps[3]) {
   g.N = p->N;
   g.Npad = round_up(g.N, NPAD);
   g.sigma = p->sigma;
-  if (c->prec != SRMRA_FP32) {
+  if (c->prec == SRMRA_FFT32) {
+    plan_fft(c);
+    caps[0] = c->plan.p1_groups;
+    caps[1] = 0;
+    caps[2] = c->plan.nparts_c;
+  } else if (is_tc_prec(c->prec)) {
     // size the partial buffers for the finest decomposition the batch tuner may pick
     plan_tc(c, 2, 2);
     c->plan.cap_p1_groups = c->plan.p1_groups;
@@ -207,7 +217,7 @@ void setup_ctx(srmra_ctx* c, const srmra_params* p, int num_sms, int caps[3]) {
 cudaError_t allocate_buffers(srmra_ctx* c, Allocator& A, const int caps[3], const char** what) {
   const Geom& g = c->g;
   const Plan& pl = c->plan;
-  const bool tc = c->prec != SRMRA_FP32;
+  const bool tc = is_tc_prec(c->prec);
 #define AL(ptr, count)                                   \
   do {                                                   \
     cudaError_t e2 = A.get(&(ptr), (int64_t)(count));    \
@@ -231,6 +241,10 @@ cudaError_t allocate_buffers(srmra_ctx* c, Allocator& A, const int caps[3], cons
       AL(c->Yl, g.Npad * g.ldk);
       AL(c->Al, (int64_t)g.Spad * g.ldk);
     }
+  } else if (c->prec == SRMRA_FFT32) {
+    AL(c->Yf, g.Npad * g.l2);
+    AL(c->Xf, (int64_t)g.K * g.K * g.l2);
+    AL(c->Gp, (int64_t)pl.fft_blocks * g.K * g.K * g.l2);
   } else {
     AL(c->YcT, g.Npad * g.ldy);
     AL(c->AxT, (int64_t)g.ldy * g.Spad);
@@ -248,7 +262,7 @@ cudaError_t allocate_buffers(srmra_ctx* c, Allocator& A, const int caps[3], cons
   AL(c->lse2, g.Npad);
   AL(c->lse, g.Npad);
   AL(c->llpart, pl.ll_blocks);
-  AL(c->Zp, (int64_t)caps[1] * g.Spad * g.ldy);
+  if (caps[1] > 0) AL(c->Zp, (int64_t)caps[1] * g.Spad * g.ldy);
   AL(c->cp, (int64_t)caps[2] * g.Spad);
   AL(c->zbp, (int64_t)caps[2] * g.Spad);
   AL(c->cfin, 2 * (int64_t)g.Spad);
@@ -301,8 +315,11 @@ srmra_status srmra_create(const srmra_params* p, const float* y, int32_t y_is_de
   if (p->N < 1) return fail(nullptr, SRMRA_EINVAL, "need N >= 1");
   if (!(p->sigma > 0.0) || !std::isfinite(p->sigma))
     return fail(nullptr, SRMRA_EINVAL, "need sigma > 0");
-  if (p->prec != SRMRA_FP32 && p->prec != SRMRA_BF16 && p->prec != SRMRA_BF16X3)
+  if (p->prec != SRMRA_FP32 && p->prec != SRMRA_BF16 && p->prec != SRMRA_BF16X3 &&
+      p->prec != SRMRA_FFT32)
     return fail(nullptr, SRMRA_EINVAL, "unknown precision form");
+  if (p->prec == SRMRA_FFT32 && !fft_supported(p->L_high / p->K))
+    return fail(nullptr, SRMRA_EINVAL, "the FFT form needs l = L/K in {8, 16, 32}");
 
   std::vector<double> r1, r2;
   {
@@ -327,7 +344,7 @@ srmra_status srmra_create(const srmra_params* p, const float* y, int32_t y_is_de
   int caps[3];
   setup_ctx(c, p, prop.multiProcessorCount, caps);
   const Geom& g = c->g;
-  const bool tc = c->prec != SRMRA_FP32;
+  const bool tc = is_tc_prec(c->prec);
   Allocator A{c, 0, alloc_limit(), &c->owned};
   const char* what = nullptr;
   e = allocate_buffers(c, A, caps, &what);
@@ -354,11 +371,11 @@ srmra_status srmra_create(const srmra_params* p, const float* y, int32_t y_is_de
     }
   }
   launch_center_obs(c, y_is_device ? y : ytmp);
-  if (tc) {
-    e = prep_obs_tc(c);
+  if (tc || c->prec == SRMRA_FFT32) {
+    e = tc ? prep_obs_tc(c) : prep_obs_fft(c);
     if (e != cudaSuccess) {
       if (ytmp) cudaFree(ytmp);
-      return bail(e, "prepare tensor-core operands");
+      return bail(e, tc ? "prepare tensor-core operands" : "transform the observations");
     }
   }
   if (x0) {
@@ -499,7 +516,9 @@ srmra_status srmra_get_estep(srmra_ctx* c, double* lse, double* cs) {
 srmra_status srmra_estimate_device_bytes(const srmra_params* p, int64_t* bytes) {
   if (!p || !bytes) return fail(nullptr, SRMRA_EINVAL, "params or bytes is NULL");
   if (p->L_high < 2 || p->K < 1 || p->L_high % p->K != 0 || p->N < 1 ||
-      (p->prec != SRMRA_FP32 && p->prec != SRMRA_BF16 && p->prec != SRMRA_BF16X3))
+      (p->prec != SRMRA_FP32 && p->prec != SRMRA_BF16 && p->prec != SRMRA_BF16X3 &&
+       p->prec != SRMRA_FFT32) ||
+      (p->prec == SRMRA_FFT32 && !fft_supported(p->L_high / p->K)))
     return fail(nullptr, SRMRA_EINVAL, "invalid problem parameters");
   int dev = 0, sms = 152;
   if (cudaGetDevice(&dev) == cudaSuccess)

@@ -67,7 +67,7 @@ srmra_status bcuda(srmra_batch* b, cudaError_t e, const char* what) {
     if (e_ != cudaSuccess) return bcuda((b), e_, #call);   \
   } while (0)
 
-bool is_tc(int prec) { return prec != SRMRA_FP32; }
+bool is_tc(int prec) { return is_tc_prec(prec); }
 
 // Estimated cost of one pass-2 unit of a context (pixels x logit depth x observations).
 double unit_cost(const srmra_ctx* c) {
@@ -135,10 +135,14 @@ cudaError_t launch_pass(srmra_batch* b, int pass) {
     return cudaSuccess;
   }
   for (auto* c : b->ctxs) {
+    const bool fft = c->prec == SRMRA_FFT32;
     if (pass == 1) {
-      launch_pass1_f32(c);
+      if (fft)
+        launch_pass1_fft(c);
+      else
+        launch_pass1_f32(c);
     } else {
-      cudaError_t e = launch_pass2_f32(c);
+      cudaError_t e = fft ? launch_pass2_fft(c) : launch_pass2_f32(c);
       if (e != cudaSuccess) return e;
     }
   }
@@ -291,7 +295,9 @@ srmra_status srmra_batch_create(srmra_ctx** ctxs, int32_t count, uint32_t flags,
   b->stream = ctxs[0]->stream;
   b->num_sms = ctxs[0]->num_sms;
   b->flags = flags;
-  cudaError_t e = is_tc(b->prec) ? tc_set_attributes(b->prec) : simt_set_attributes();
+  cudaError_t e = is_tc(b->prec)                ? tc_set_attributes(b->prec)
+                  : b->prec == SRMRA_FFT32 ? fft_set_attributes()
+                                           : simt_set_attributes();
   for (int k = 0; k < 4 && e == cudaSuccess; ++k) e = cudaEventCreate(&b->ev[k]);
   if (e == cudaSuccess) e = cudaMalloc((void**)&b->d_status, sizeof(int));
   if (e == cudaSuccess) e = cudaMemsetAsync(b->d_status, 0, sizeof(int), b->stream);

@@ -476,6 +476,8 @@ void launch_prep_iter(srmra_ctx* c) {
     k_templates_T<<<grid, 256, 0, c->stream>>>(c->x, c->sub, g.L, g.K, g.l, g.S, g.Spad,
                                                 g.l2, c->AxT);
     c->launches++;
+  } else if (c->prec == SRMRA_FFT32) {
+    launch_templates_fft(c);
   } else {
     launch_templates_tc(c);
   }
@@ -497,10 +499,16 @@ void launch_finalize(srmra_ctx* c, int ll_index) {
   k_fin_counts<<<1, 1024, 0, c->stream>>>(c->cfin, g.Spad, g.S, g.L, g.K, g.l, c->llpart,
                                           c->plan.ll_blocks, c->rho1, c->rho2, c->Ar,
                                           c->ll_hist + ll_index, c->status);
-  const int n_ts = fin_t_splits(g, c->num_sms);
-  const int t_per = (int)ceil_div(g.l2, n_ts);
-  k_fin_b<<<dim3((unsigned)(g.K * g.K), (unsigned)n_ts), 256, 0, c->stream>>>(
-      c->Zp, c->plan.nparts_z, g.Spad, g.ldy, g.L, g.K, g.l, t_per, c->bpart);
+  int n_ts = 1;
+  if (c->prec == SRMRA_FFT32) {
+    launch_fin_b_fft(c);  // b' from the frequency-domain sums: one partial
+    c->launches--;        // counted below with the other three
+  } else {
+    n_ts = fin_t_splits(g, c->num_sms);
+    const int t_per = (int)ceil_div(g.l2, n_ts);
+    k_fin_b<<<dim3((unsigned)(g.K * g.K), (unsigned)n_ts), 256, 0, c->stream>>>(
+        c->Zp, c->plan.nparts_z, g.Spad, g.ldy, g.L, g.K, g.l, t_per, c->bpart);
+  }
   k_fin_x<<<(unsigned)ceil_div(g.S, 256), 256, 0, c->stream>>>(c->bpart, n_ts, g.L, g.K, g.l,
                                                                 c->Ar, c->x, c->status);
   c->launches += 4;

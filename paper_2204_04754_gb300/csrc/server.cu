@@ -113,7 +113,7 @@ srmra_status srmra_server_create(int64_t device_budget_bytes, int32_t max_active
   *out = nullptr;
   if (device_budget_bytes <= 0 || max_active < 1)
     return sfail(nullptr, SRMRA_EINVAL, "need a positive memory budget and slot count");
-  if (prec != SRMRA_FP32 && prec != SRMRA_BF16 && prec != SRMRA_BF16X3)
+  if (prec != SRMRA_FP32 && prec != SRMRA_BF16 && prec != SRMRA_BF16X3 && prec != SRMRA_FFT32)
     return sfail(nullptr, SRMRA_EINVAL, "unknown precision form");
   auto* s = new (std::nothrow) srmra_server();
   if (!s) return sfail(nullptr, SRMRA_ENOMEM, "host allocation failed");

@@ -79,6 +79,8 @@ struct Plan {
   int nparts_c = 1;         // number of partial c / zb slices
   int nparts_z = 1;         // number of partial Z slices
   int ll_blocks = 1;        // blocks of the lse-combine kernel
+  int fft_obs_per_block = 1;  // FFT form: observations per (block, phase) CTA
+  int fft_blocks = 1;         // FFT form: observation blocks
   int cap_p1_groups = 0;    // capacity of the pass-1 partial buffers (0 = unbounded)
   int cap_nsplit = 0;       // capacity of the pass-2 partial buffers (0 = unbounded)
 };
@@ -132,6 +134,9 @@ struct srmra_ctx {
   float* zbp = nullptr;    // [nparts_c][Spad] partial sum_i w ybar_i
   double* cfin = nullptr;  // [2*Spad] c_s and zb_s of the last E-step
   float* bpart = nullptr;  // [fin_t_splits][K*K][l2] partial b' per lag range
+  float2* Yf = nullptr;    // FFT form: [Npad][l2] FFT2(y'_i)
+  float2* Xf = nullptr;    // FFT form: [K*K][l2] FFT2(x'_r), per iteration
+  float2* Gp = nullptr;    // FFT form: [fft_blocks][K*K][l2] partial sum_i conj(W^) Y^'
   double* Ar = nullptr;    // [K*K] coverage per sub-image, then ZB per sub-image [K*K]
   double* ll_hist = nullptr;  // [ll_cap]
   int ll_cap = 0;
@@ -193,6 +198,17 @@ cudaError_t tc_launch_group_p2(int G, int prec, const void* d_insts, const int64
 // ---- k_simt.cu (float32 form)
 void plan_simt(srmra_ctx* c);
 cudaError_t simt_set_attributes();
+
+// polyphase-FFT form (k_fft.cu)
+bool fft_supported(int l);
+void plan_fft(srmra_ctx* c);
+cudaError_t fft_set_attributes();
+cudaError_t prep_obs_fft(srmra_ctx* c);
+void launch_templates_fft(srmra_ctx* c);
+void launch_pass1_fft(srmra_ctx* c);
+cudaError_t launch_pass2_fft(srmra_ctx* c);
+void launch_fin_b_fft(srmra_ctx* c);
+inline bool is_tc_prec(int prec) { return prec == SRMRA_BF16 || prec == SRMRA_BF16X3; }
 void launch_pass1_f32(srmra_ctx* c);
 cudaError_t launch_pass2_f32(srmra_ctx* c);
 

@@ -22,8 +22,9 @@ SRMRA_OK, SRMRA_EINVAL, SRMRA_ENOMEM, SRMRA_ECUDA, SRMRA_ETIMEOUT, SRMRA_ENUMERI
     SRMRA_EBUSY = range(7)
 STATUS_NAMES = {0: "OK", 1: "EINVAL", 2: "ENOMEM", 3: "ECUDA", 4: "ETIMEOUT",
                 5: "ENUMERIC", 6: "EBUSY"}
-SRMRA_FP32, SRMRA_BF16, SRMRA_BF16X3 = 0, 1, 2
-PRECISIONS = {"fp32": SRMRA_FP32, "bf16": SRMRA_BF16, "bf16x3": SRMRA_BF16X3}
+SRMRA_FP32, SRMRA_BF16, SRMRA_BF16X3, SRMRA_FFT32 = 0, 1, 2, 3
+PRECISIONS = {"fp32": SRMRA_FP32, "bf16": SRMRA_BF16, "bf16x3": SRMRA_BF16X3,
+              "fft32": SRMRA_FFT32}
 SRMRA_FLAG_CHECK_NUMERIC = 1
 
 
