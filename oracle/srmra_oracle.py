@@ -36,6 +36,14 @@ Readings where the paper is silent or ambiguous (each also listed in the design doc):
       |c| > 2.7 * sigma_BM (ties are zeroed), no clipping.
   R10 the projection runs after the M-step of every F-th iteration; F = 0 means none.
   R11 a fixed iteration count replaces "until a stopping criterion is met".
+  R13 online EM (the online strategy the paper suggests for large N, Sec. 7, without an
+      algorithm): mini-batch EM with stochastic-approximation sufficient statistics.
+      The statistics of Eqs. (x_EM) and (rho_EM) are the per-shift sums
+      Z[s] = sum_i w^{i,s} y_i and c[s] = sum_i w^{i,s}; step t takes a batch B_t,
+      averages them over it (Z_B / |B_t|, c_B / |B_t|), sets
+      S_t = (1 - gamma_t) S_{t-1} + gamma_t S_{B_t} (gamma_0 = 1), and runs the M-step
+      on S_t.  The M-step is scale-free in (Z, c), so a single batch of all N
+      observations with gamma = 1 is one EM iteration.
 """
 from __future__ import annotations
 
@@ -313,6 +321,50 @@ def projected_em(Y, x0, rho1, rho2, sigma, K, iters, F, sigma_bm1=1.0,
             hist["margin"] = min(hist["margin"], mg)
             sbm *= decay
     return x, r1, r2, hist
+
+
+# ---------------------------------------------------------------------------
+# Online EM (reading R13)
+# ---------------------------------------------------------------------------
+
+
+def batch_stats(Yb, x, rho1, rho2, sigma, K):
+    """E-step on a batch: the per-observation averages Z_B / n, c_B / n of the
+    sufficient statistics, and the batch log-likelihood terms lse_i."""
+    Yb = np.asarray(Yb, np.float64).reshape(Yb.shape[0], -1)
+    n = Yb.shape[0]
+    W, lse, _ = estep(Yb, x, rho1, rho2, sigma, K)
+    return (W.T @ Yb) / n, W.sum(axis=0) / n, lse
+
+
+def sa_update(S, Sb, gamma):
+    """Stochastic-approximation step S <- (1 - gamma) S + gamma S_B on (Z, c)."""
+    if S is None:
+        return Sb
+    return tuple((1.0 - gamma) * a + gamma * b for a, b in zip(S, Sb))
+
+
+def online_em(Y, batches, gammas, x0, rho1, rho2, sigma, K, F=0, sigma_bm1=1.0,
+              decay=2.0 ** -0.1):
+    """Online EM (R13): for each step t, an E-step on the observations Y[batches[t]]
+    (an index array or a slice), the update of the statistics with gammas[t]
+    (gamma_0 is taken as 1), the M-step of Eqs. (x_EM), (rho_EM) on them, and every
+    F-th step the projection of Algorithm 2.  Returns (x, rho1, rho2, batch LLs)."""
+    x = np.asarray(x0, np.float64)
+    r1 = np.asarray(rho1, np.float64)
+    r2 = np.asarray(rho2, np.float64)
+    S = None
+    lls = []
+    sbm = float(sigma_bm1)
+    for t, (bt, g) in enumerate(zip(batches, gammas)):
+        Zb, cb, lse = batch_stats(Y[bt], x, r1, r2, sigma, K)
+        S = sa_update(S, (Zb, cb), 1.0 if t == 0 else g)
+        x, r1, r2, _, _ = mstep_from_sums(S[0], S[1], x, K)
+        lls.append(float(lse.sum()))
+        if F > 0 and (t + 1) % F == 0:
+            x, _ = dct_denoise(x, sbm)
+            sbm *= decay
+    return x, r1, r2, lls
 
 
 # ---------------------------------------------------------------------------

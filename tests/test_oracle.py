@@ -399,3 +399,59 @@ def test_cycle_spinning_is_translation_equivariant():
     plain, _ = O.dct_denoise(x, 0.1)
     shifted, _ = O.dct_denoise(O.shift(x, 3, 5), 0.1)
     assert np.linalg.norm(shifted - O.shift(plain, 3, 5)) > 1e-3  # the plain one is not
+
+
+# ---------------------------------------------------------------------------
+# Online EM (reading R13)
+# ---------------------------------------------------------------------------
+
+
+def test_online_em_single_full_batch_is_one_em_iteration():
+    p = synth.make_problem(12, 2, 60, 0.5, seed=77, init="uniform")
+    xo, r1o, r2o, lls = O.online_em(p.y, [slice(0, p.N)], [0.3], p.x0, p.rho1_0, p.rho2_0,
+                                    p.sigma, p.K)
+    xe, r1e, r2e, lle, _ = O.em_iter(p.y, p.x0, p.rho1_0, p.rho2_0, p.sigma, p.K)
+    np.testing.assert_allclose(xo, xe, rtol=1e-13, atol=1e-13)
+    np.testing.assert_allclose(r1o, r1e, rtol=1e-13)
+    np.testing.assert_allclose(r2o, r2e, rtol=1e-13)
+    assert abs(lls[0] - lle) < 1e-10 * abs(lle)
+
+
+def test_online_statistics_average_to_the_full_data_ones():
+    """With theta frozen, the stochastic-approximation steps with
+    gamma_t = n_t / (n_0 + ... + n_t) over a partition of the observations give the
+    full-data averages Z / N, c / N (checked against sums computed without batches)."""
+    p = synth.make_problem(8, 2, 70, 0.4, seed=78, init="uniform")
+    cuts = [0, 13, 40, 41, 70]
+    S, seen = None, 0
+    for a, b in zip(cuts[:-1], cuts[1:]):
+        Zb, cb, _ = O.batch_stats(p.y[a:b], p.x0, p.rho1_0, p.rho2_0, p.sigma, p.K)
+        seen += b - a
+        S = O.sa_update(S, (Zb, cb), (b - a) / seen)
+    # the full-data sums, term by term from the brute-force weights of each observation
+    T = O.all_templates(p.x0, p.K)
+    lp = O.log_prior(p.rho1_0, p.rho2_0)
+    Y = p.y.reshape(p.N, -1).astype(np.float64)
+    Z = np.zeros_like(S[0])
+    c = np.zeros_like(S[1])
+    for i in range(p.N):
+        lg = -((Y[i][None, :] - T) ** 2).sum(axis=1) / (2 * p.sigma ** 2) + lp
+        w = np.exp(lg - lg.max())
+        w /= w.sum()
+        Z += np.outer(w, Y[i])
+        c += w
+    np.testing.assert_allclose(S[0], Z / p.N, rtol=1e-11, atol=1e-13)
+    np.testing.assert_allclose(S[1], c / p.N, rtol=1e-11, atol=1e-15)
+
+
+def test_online_em_gamma_one_forgets_the_past():
+    """gamma = 1 keeps only the current batch: the step equals an EM iteration on that
+    batch alone from the same theta."""
+    p = synth.make_problem(8, 2, 50, 0.4, seed=79, init="uniform")
+    b0, b1 = slice(0, 20), slice(20, 50)
+    x1, r11, r21, _ = O.online_em(p.y, [b0], [1.0], p.x0, p.rho1_0, p.rho2_0, p.sigma, p.K)
+    x2, r12, r22, _ = O.online_em(p.y, [b0, b1], [1.0, 1.0], p.x0, p.rho1_0, p.rho2_0,
+                                  p.sigma, p.K)
+    xe, r1e, r2e, _, _ = O.em_iter(p.y[b1], x1, r11, r21, p.sigma, p.K)
+    np.testing.assert_allclose(x2, xe, rtol=1e-12, atol=1e-13)
+    np.testing.assert_allclose(r12, r1e, rtol=1e-12)

@@ -113,3 +113,9 @@ def test_x_update_without_coverage_division_is_caught(monkeypatch):
 
     monkeypatch.setattr(O, "mstep_from_sums", bad)
     assert fails(pin_mstep) and fails(pin_worked)
+
+
+def test_unweighted_online_update_is_caught(monkeypatch):
+    monkeypatch.setattr(O, "sa_update",
+                        lambda S, Sb, g: Sb if S is None else tuple(a + g * b for a, b in zip(S, Sb)))
+    assert fails(T.test_online_statistics_average_to_the_full_data_ones)
