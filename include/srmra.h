@@ -313,6 +313,48 @@ srmra_status srmra_profile(srmra_ctx* ctx, int32_t enable);
  * SRMRA_NUM_PHASES, host, either may be NULL), and clear the records. */
 srmra_status srmra_profile_read(srmra_ctx* ctx, double* ms, int64_t* count);
 
+/* ---- Online (mini-batch) EM over shards of the observations. ----
+ *
+ * The paper points to online strategies to cut the cost of the likelihood term for
+ * large N (Sec. 7) without fixing an algorithm; this is mini-batch EM with
+ * stochastic-approximation sufficient statistics.  The observations are split into
+ * shard contexts (created with srmra_create, device resident; same L, K, sigma,
+ * precision and stream).  The online object holds the estimate theta = (x, rho1,
+ * rho2) and the running statistics S of Eqs. (x_EM), (rho_EM): per shift
+ * c_s = sum_i w^{i,s} and zb_s = sum_i w^{i,s} ybar_i, per low-resolution pixel of
+ * every sub-image the back-projection b' of the centred observations.  A step on
+ * shard k:
+ *   1. E-step of the current theta over shard k's n_k observations (both passes),
+ *   2. S <- (1 - gamma) S + gamma (shard statistics) / n_k   (the first step uses 1),
+ *   3. the M-step of Eqs. (x_EM), (rho_EM) on S.
+ * A single shard holding all observations with gamma = 1 is one EM iteration.
+ * The shards' own x / rho are overwritten by each step that uses them.            */
+typedef struct srmra_online srmra_online;
+
+/* srmra_online_create -- shards: n_shards distinct contexts (kept by the caller, not
+ * owned; they must outlive the online object).  x0, rho1_0, rho2_0: host, or NULL for
+ * shard 0's current state.  Errors: SRMRA_EINVAL (mismatched shards, bad rho). */
+srmra_status srmra_online_create(srmra_ctx* const* shards, int32_t n_shards, const float* x0,
+                                 const double* rho1_0, const double* rho2_0,
+                                 srmra_online** out);
+
+/* srmra_online_step -- one step on shard `shard` with step size gamma in (0, 1].
+ * loglik_out (host, may be NULL): the shard's log-likelihood sum_i lse_i at the theta
+ * the step started from (Eq. likelihood_EM over the batch).  Synchronous when
+ * loglik_out is given; otherwise only enqueued. */
+srmra_status srmra_online_step(srmra_online* on, int32_t shard, double gamma, double* loglik_out);
+
+/* srmra_online_project -- x <- D(x, sigma_bm) with the built-in block-DCT denoiser
+ * (the settings of srmra_set_denoiser on shard 0; needs L % 8 == 0). */
+srmra_status srmra_online_project(srmra_online* on, double sigma_bm);
+
+/* srmra_online_get_state -- current estimate to host buffers (any may be NULL). */
+srmra_status srmra_online_get_state(srmra_online* on, float* x, double* rho1, double* rho2,
+                                    int64_t* steps_done);
+
+void srmra_online_destroy(srmra_online* on);
+const char* srmra_online_last_error(const srmra_online* on);
+
 /* srmra_loglik_noalloc -- per-observation log-likelihood terms without any device
  * allocation.  The paper has no counterpart: this entry point exists for callers that
  * cannot call cudaMalloc -- services that size all device memory once at start-up so

@@ -130,8 +130,9 @@ struct PhaseTimer {
   }
 };
 
-// One EM iteration theta_t -> theta_{t+1}; LL(theta_t) goes to ll_hist[ll_index].
-srmra_status run_iteration(srmra_ctx* c, int ll_index) {
+// The E-step of theta_t over the context's observations, up to the sums the M-step
+// needs (launch_stats); shared by the EM iteration and the online step.
+srmra_status run_estep_passes(srmra_ctx* c) {
   cudaError_t e = cudaSuccess;
   { PhaseTimer t(c, SRMRA_PHASE_PREP); launch_prep_iter(c); }
   const bool tc = is_tc_prec(c->prec), fft = c->prec == SRMRA_FFT32;
@@ -151,8 +152,29 @@ srmra_status run_iteration(srmra_ctx* c, int ll_index) {
     e = tc ? launch_pass2_tc(c) : fft ? launch_pass2_fft(c) : launch_pass2_f32(c);
   }
   if (e != cudaSuccess) return cuda_fail(c, e, "pass 2 launch");
+  return SRMRA_OK;
+}
+
+}  // namespace
+
+srmra_status srmra::run_estep_stats(srmra_ctx* c) {
+  srmra_status st = run_estep_passes(c);
+  if (st != SRMRA_OK) return st;
+  { PhaseTimer t(c, SRMRA_PHASE_FINAL); launch_stats(c); }
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_fail(c, e, "E-step launch");
+  c->have_estep = true;
+  return SRMRA_OK;
+}
+
+namespace {
+
+// One EM iteration theta_t -> theta_{t+1}; LL(theta_t) goes to ll_hist[ll_index].
+srmra_status run_iteration(srmra_ctx* c, int ll_index) {
+  srmra_status st = run_estep_passes(c);
+  if (st != SRMRA_OK) return st;
   { PhaseTimer t(c, SRMRA_PHASE_FINAL); launch_finalize(c, ll_index); }
-  e = cudaGetLastError();
+  cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return cuda_fail(c, e, "EM iteration launch");
   c->t += 1;
   c->have_estep = true;

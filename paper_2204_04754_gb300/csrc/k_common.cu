@@ -491,27 +491,46 @@ void launch_lse_combine(srmra_ctx* c, int groups) {
   c->launches++;
 }
 
-void launch_finalize(srmra_ctx* c, int ll_index) {
+int stats_t_splits(const srmra_ctx* c) {
+  return c->prec == SRMRA_FFT32 ? 1 : fin_t_splits(c->g, c->num_sms);
+}
+
+// The E-step sums of the iteration: c_s, zb_s (float64, cfin) and the partials of b'
+// (bpart, stats_t_splits of them).
+void launch_stats(srmra_ctx* c) {
   const Geom& g = c->g;
   k_fin_sums<<<(unsigned)ceil_div(g.S, 256), 256, 0, c->stream>>>(c->cp, c->zbp,
                                                                   c->plan.nparts_c, g.Spad,
                                                                   g.S, c->cfin);
-  k_fin_counts<<<1, 1024, 0, c->stream>>>(c->cfin, g.Spad, g.S, g.L, g.K, g.l, c->llpart,
-                                          c->plan.ll_blocks, c->rho1, c->rho2, c->Ar,
-                                          c->ll_hist + ll_index, c->status);
-  int n_ts = 1;
+  c->launches++;
   if (c->prec == SRMRA_FFT32) {
     launch_fin_b_fft(c);  // b' from the frequency-domain sums: one partial
-    c->launches--;        // counted below with the other three
   } else {
-    n_ts = fin_t_splits(g, c->num_sms);
+    const int n_ts = fin_t_splits(g, c->num_sms);
     const int t_per = (int)ceil_div(g.l2, n_ts);
     k_fin_b<<<dim3((unsigned)(g.K * g.K), (unsigned)n_ts), 256, 0, c->stream>>>(
         c->Zp, c->plan.nparts_z, g.Spad, g.ldy, g.L, g.K, g.l, t_per, c->bpart);
+    c->launches++;
   }
-  k_fin_x<<<(unsigned)ceil_div(g.S, 256), 256, 0, c->stream>>>(c->bpart, n_ts, g.L, g.K, g.l,
-                                                                c->Ar, c->x, c->status);
-  c->launches += 4;
+}
+
+// M-step of Eqs. (x_EM), (rho_EM) from sums in the layout of launch_stats:
+// rho, coverage, LL (from the lse-combine partials) and x.
+void launch_mstep(srmra_ctx* c, const double* cfin, const float* bpart, int n_ts,
+                  const double* llpart, double* rho1, double* rho2, double* Ar,
+                  double* ll_out, float* x, int* status, cudaStream_t stream) {
+  const Geom& g = c->g;
+  k_fin_counts<<<1, 1024, 0, stream>>>(cfin, g.Spad, g.S, g.L, g.K, g.l, llpart,
+                                       c->plan.ll_blocks, rho1, rho2, Ar, ll_out, status);
+  k_fin_x<<<(unsigned)ceil_div(g.S, 256), 256, 0, stream>>>(bpart, n_ts, g.L, g.K, g.l, Ar,
+                                                            x, status);
+  c->launches += 2;
+}
+
+void launch_finalize(srmra_ctx* c, int ll_index) {
+  launch_stats(c);
+  launch_mstep(c, c->cfin, c->bpart, stats_t_splits(c), c->llpart, c->rho1, c->rho2, c->Ar,
+               c->ll_hist + ll_index, c->x, c->status, c->stream);
 }
 
 void launch_dct_sched(srmra_ctx* c, double thr) {

@@ -168,7 +168,13 @@ namespace srmra {
 void launch_center_obs(srmra_ctx* c, const float* y_dev);
 void launch_prep_iter(srmra_ctx* c);           // sub-image stats, column terms, templates
 void launch_lse_combine(srmra_ctx* c, int groups);
-void launch_finalize(srmra_ctx* c, int ll_index);
+void launch_finalize(srmra_ctx* c, int ll_index);  // launch_stats + launch_mstep
+int stats_t_splits(const srmra_ctx* c);
+void launch_stats(srmra_ctx* c);
+void launch_mstep(srmra_ctx* c, const double* cfin, const float* bpart, int n_ts,
+                  const double* llpart, double* rho1, double* rho2, double* Ar,
+                  double* ll_out, float* x, int* status, cudaStream_t stream);
+srmra_status run_estep_stats(srmra_ctx* c);  // prep, both passes, combine, launch_stats
 void launch_dct_denoise(srmra_ctx* c, double sigma_bm, double thr);
 void launch_dct_sched(srmra_ctx* c, double thr);  // projection from the device schedule
 LogitScalars logit_scalars(const Geom& g);

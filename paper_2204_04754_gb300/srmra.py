@@ -93,6 +93,14 @@ def lib() -> ctypes.CDLL:
         "srmra_server_memory": (c_int32, [c_void_p, P(c_int64), P(c_int64)]),
         "srmra_server_destroy": (None, [c_void_p]),
         "srmra_server_last_error": (c_char_p, [c_void_p]),
+        "srmra_online_create": (c_int32, [c_void_p, c_int32, c_void_p, c_void_p, c_void_p,
+                                          P(c_void_p)]),
+        "srmra_online_step": (c_int32, [c_void_p, c_int32, c_double, c_void_p]),
+        "srmra_online_project": (c_int32, [c_void_p, c_double]),
+        "srmra_online_get_state": (c_int32, [c_void_p, c_void_p, c_void_p, c_void_p,
+                                             P(c_int64)]),
+        "srmra_online_destroy": (None, [c_void_p]),
+        "srmra_online_last_error": (c_char_p, [c_void_p]),
         "srmra_last_error": (c_char_p, [c_void_p]),
         "srmra_version": (c_char_p, []),
     }
@@ -380,6 +388,58 @@ def srmra_estimate_device_bytes(L: int, K: int, N: int, sigma: float, prec: str 
     p = srmra_params(L, K, N, sigma, PRECISIONS[prec], 0)
     _check(lib().srmra_estimate_device_bytes(byref(p), byref(out)), None)
     return out.value
+
+
+class Online:
+    """Online (mini-batch) EM over shard :class:`Solver` objects (same L, K, sigma,
+    precision, stream): each step runs the E-step on one shard, folds its statistics
+    into the running ones with step size gamma, and runs the M-step on them."""
+
+    def __init__(self, shards, x0=None, rho1=None, rho2=None):
+        self.shards = list(shards)
+        arr = _ctx_array([s.ctx for s in self.shards])
+        x0 = None if x0 is None else np.ascontiguousarray(x0, dtype=np.float32)
+        r1 = None if rho1 is None else np.ascontiguousarray(rho1, dtype=np.float64)
+        r2 = None if rho2 is None else np.ascontiguousarray(rho2, dtype=np.float64)
+        out = c_void_p()
+        self._check(lib().srmra_online_create(arr, len(self.shards), _ptr(x0), _ptr(r1),
+                                              _ptr(r2), byref(out)), None)
+        self.handle = out.value
+        self.L = self.shards[0].L
+
+    @staticmethod
+    def _check(st, h):
+        if st != SRMRA_OK:
+            msg = lib().srmra_online_last_error(h)
+            raise SrmraError(st, msg.decode() if msg else "")
+
+    def step(self, shard: int, gamma: float, loglik: bool = True):
+        out = np.empty(1) if loglik else None
+        self._check(lib().srmra_online_step(self.handle, shard, gamma, _ptr(out)), self.handle)
+        return None if out is None else float(out[0])
+
+    def project(self, sigma_bm: float):
+        self._check(lib().srmra_online_project(self.handle, sigma_bm), self.handle)
+
+    def state(self):
+        x = np.empty((self.L, self.L), np.float32)
+        r1 = np.empty(self.L)
+        r2 = np.empty(self.L)
+        n = c_int64()
+        self._check(lib().srmra_online_get_state(self.handle, _ptr(x), _ptr(r1), _ptr(r2),
+                                                 byref(n)), self.handle)
+        return x, r1, r2, n.value
+
+    def close(self):
+        if getattr(self, "handle", None):
+            lib().srmra_online_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 class Server:
