@@ -279,6 +279,35 @@ def mixed_block(p, w, steps, warmup, srmra, torch, stream, flush, fp32_value, fo
             "note": note}
 
 
+def online_block(p, w, steps, warmup, srmra, torch, stream, flush, fp32_value, n_shards=10):
+    """Online (mini-batch) EM on the same workload: the observations split into n_shards
+    device-resident shards, one shard per step (cyclic), gamma_t = (t + 1)^-0.6; pairs/s
+    of the steps (shard observations x L^2 shifts per step)."""
+    cuts = [p.N * k // n_shards for k in range(n_shards + 1)]
+    shards = [srmra.Solver(p.L, p.K, p.sigma, p.y[a:b], prec="fp32", x0=p.x0, rho1=p.rho1_0,
+                           rho2=p.rho2_0, stream=stream.cuda_stream)
+              for a, b in zip(cuts[:-1], cuts[1:])]
+    on = srmra.Online(shards)
+    t = [0]
+
+    def one():
+        on.step(t[0] % n_shards, (t[0] + 1) ** -0.6, loglik=False)
+        t[0] += 1
+    for _ in range(warmup):
+        one()
+    ms = time_steps(one, steps, stream, torch, flush)
+    pairs = sum(b - a for a, b in zip(cuts[:-1], cuts[1:])) / n_shards * p.L * p.L
+    value = pairs * steps / (sum(ms) / 1e3)
+    on.close()
+    for s_ in shards:
+        s_.close()
+    return {"shards": n_shards, "obs_per_step": p.N // n_shards, "value": value,
+            "unit": "pairs/s", "ms_per_step": sum(ms) / steps,
+            "per_pair_vs_full_iteration": value / fp32_value,
+            "note": "mini-batch EM with stochastic-approximation statistics (fp32 form); "
+                    "steps checked against the oracle in tests/test_gpu_online.py"}
+
+
 def run_batched(args, rank, world, local):
     """64 uneven problems advanced together: grouped launches in a CUDA graph."""
     import numpy as np
@@ -546,6 +575,8 @@ def main():
         if p.l in (8, 16, 32):
             out["fft32"] = mixed_block(p, w, args.steps, args.warmup, srmra, torch, stream,
                                        flush, value, form="fft32")
+        out["online"] = online_block(p, w, args.steps, args.warmup, srmra, torch, stream,
+                                     flush, value)
     if rank == 0 and world == 1 and not args.no_cpu:
         cb = cpu_oracle_rate(p, args.cpu_seconds)
         cb.pop("n_sub", None)
