@@ -308,6 +308,40 @@ def online_block(p, w, steps, warmup, srmra, torch, stream, flush, fp32_value, n
                     "steps checked against the oracle in tests/test_gpu_online.py"}
 
 
+def mom_block(p, steps, warmup, srmra, torch, stream, flush, sm_max):
+    """Projected MoM (Algorithm 1) on the same observations: the one-pass empirical
+    moments (M1^, M2^ = Y^T Y / N: 2 N l^4 flops) and the projected gradient iterations
+    (the products T^T diag(rho) T and T R: 4 L^2 l^4 flops per step), against the FP32
+    FFMA peak."""
+    import numpy as np
+    s = srmra.Solver(p.L, p.K, p.sigma, p.y, prec="fp32", x0=p.x0, rho1=p.rho1_0,
+                     rho2=p.rho2_0, stream=stream.cuda_stream)
+    m = srmra.Mom(s)
+    for _ in range(warmup):
+        m.recompute_moments()
+    ms_mom = time_steps(m.recompute_moments, steps, stream, torch, flush)
+    _, gx, g1, g2 = m.eval()
+    mu_x = 0.003 / float(np.abs(gx).max())
+    mu_r = 0.003 / float(max(np.abs(g1).max(), np.abs(g2).max()))
+    m.run(warmup, 0, mu_x, mu_r, objective=False)
+    fs = []
+    ms_it = time_steps(lambda: fs.append(m.run(1, 0, mu_x, mu_r)), steps, stream, torch, flush)
+    l4 = float(p.l) ** 4
+    peak = fp32_peak_tflops(sm_max)
+    mom_tf = 2 * p.N * l4 / (float(np.mean(ms_mom)) / 1e3) / 1e12
+    it_tf = 4 * p.L * p.L * l4 / (float(np.mean(ms_it)) / 1e3) / 1e12
+    m.close()
+    s.close()
+    return {"moments_ms": float(np.mean(ms_mom)), "moments_tflops": mom_tf,
+            "moments_frac_fp32_peak": mom_tf / peak,
+            "iteration_ms": float(np.mean(ms_it)), "iteration_tflops": it_tf,
+            "iteration_frac_fp32_peak": it_tf / peak,
+            "objective_first_last": [float(fs[0][0]), float(fs[-1][0])],
+            "note": "float32 SIMT products (k_mom_gemm); each timed iteration includes its "
+                    "host synchronisation; checked against the oracle in "
+                    "tests/test_gpu_mom.py"}
+
+
 def run_batched(args, rank, world, local):
     """64 uneven problems advanced together: grouped launches in a CUDA graph."""
     import numpy as np
@@ -577,6 +611,8 @@ def main():
                                        flush, value, form="fft32")
         out["online"] = online_block(p, w, args.steps, args.warmup, srmra, torch, stream,
                                      flush, value)
+        out["mom"] = mom_block(p, args.steps, args.warmup, srmra, torch, stream, flush,
+                               float(load_peaks()[0].get("sm_max_mhz", 2070.0)))
     if rank == 0 and world == 1 and not args.no_cpu:
         cb = cpu_oracle_rate(p, args.cpu_seconds)
         cb.pop("n_sub", None)

@@ -355,6 +355,60 @@ srmra_status srmra_online_get_state(srmra_online* on, float* x, double* rho1, do
 void srmra_online_destroy(srmra_online* on);
 const char* srmra_online_last_error(const srmra_online* on);
 
+/* ---- Projected method of moments (Algorithm 1). ----
+ *
+ * Estimates theta = (x, rho1, rho2) from the first two moments of the observations,
+ * which a MoM object computes once from a context's device-resident observations
+ * (Eq. empiric_MOM with D = 2): M1^ = (1/N) sum_i y_i and M2^ = (1/N) sum_i y_i y_i^T,
+ * both over the flattened l x l images (float32 products, float64 partial sums).
+ * The model's moments at theta, with t_s = P R_s x and rho_s = rho1[s1] rho2[s2]
+ * (Sec. 2), are M1 = sum_s rho_s t_s and M2 = sum_s rho_s t_s t_s^T + sigma^2 I, and
+ * the objective is Eq. (LS_SR):
+ *   f = ||M2 - M2^||_F^2 + lambda ||M1 - M1^||^2,   lambda = 1 / (L^2 (1 + sigma^2)).
+ * Its gradient, with R = M2 - M2^ and r = M1 - M1^:
+ *   df/drho_s = 2 t_s^T R t_s + 2 lambda t_s^T r,
+ *   df/drho1  = G rho2, df/drho2 = G^T rho1   (G[s1][s2] = df/drho_s),
+ *   df/dx     = sum_s rho_s (P R_s)^T (4 R t_s + 2 lambda r).
+ * A step of srmra_mom_run is the fixed-step projected gradient iteration the paper
+ * analyses (Sec. 4, Eq. pgm) in place of the F BFGS steps of Algorithm 1:
+ *   x <- x - mu_x df/dx,  rho1, rho2 <- Euclidean projections onto the probability
+ *   simplex of rho - mu_rho df/drho (both gradients taken at the same theta),
+ * and after every F-th step x <- D(x, sigma_BM), sigma_BM <- decay sigma_BM
+ * (Eq. decaying_function).  The estimate lives in the context: srmra_mom_run starts
+ * from the context's x, rho1, rho2 and leaves its result there (srmra_get_state). */
+typedef struct srmra_mom srmra_mom;
+
+/* srmra_mom_create -- bind to ctx (not owned; it must outlive the MoM object), allocate
+ * the moment buffers (about 4 (3 + splits) l^4 + 12 L^2 l^2 bytes, l^2 rounded up to
+ * 128) and compute the empirical moments (synchronous).  Needs L <= 1024 and
+ * (L/K)^2 <= 8192.  Errors: SRMRA_EINVAL, SRMRA_ENOMEM, SRMRA_ECUDA. */
+srmra_status srmra_mom_create(srmra_ctx* ctx, srmra_mom** out);
+
+/* srmra_mom_moments -- copy M1^ (l^2 float64) and M2^ (l^2 x l^2 float64, row-major) to
+ * host buffers; either may be NULL.  Synchronous. */
+srmra_status srmra_mom_moments(srmra_mom* m, double* M1h, double* M2h);
+
+/* srmra_mom_eval -- f and its gradient at the context's current theta into host
+ * buffers (any may be NULL): f (1), gx (L x L, row-major), g1 = df/drho1 (L),
+ * g2 = df/drho2 (L).  Synchronous.  SRMRA_ENUMERIC if f is not finite. */
+srmra_status srmra_mom_eval(srmra_mom* m, double* f, double* gx, double* g1, double* g2);
+
+/* srmra_mom_run -- iters steps (above).  F = 0: no denoiser; fn == NULL selects the
+ * built-in denoiser of srmra_project (needs L % 8 == 0), else fn(user) is called as
+ * there.  f_out (host, iters float64, may be NULL): f at the theta each step started
+ * from.  Synchronous.  Errors: SRMRA_EINVAL (arguments, denoiser), SRMRA_ENUMERIC. */
+srmra_status srmra_mom_run(srmra_mom* m, int32_t iters, int32_t F, double mu_x, double mu_rho,
+                           double sigma_bm1, double decay, srmra_denoiser_fn fn, void* user,
+                           double* f_out);
+
+/* srmra_mom_recompute_moments -- enqueue the empirical-moment pass again (the
+ * observations are unchanged, so the result is the same; for timing the one-pass
+ * data-parallel part). */
+srmra_status srmra_mom_recompute_moments(srmra_mom* m);
+
+void srmra_mom_destroy(srmra_mom* m);
+const char* srmra_mom_last_error(const srmra_mom* m);
+
 /* srmra_loglik_noalloc -- per-observation log-likelihood terms without any device
  * allocation.  The paper has no counterpart: this entry point exists for callers that
  * cannot call cudaMalloc -- services that size all device memory once at start-up so

@@ -101,6 +101,14 @@ def lib() -> ctypes.CDLL:
                                              P(c_int64)]),
         "srmra_online_destroy": (None, [c_void_p]),
         "srmra_online_last_error": (c_char_p, [c_void_p]),
+        "srmra_mom_create": (c_int32, [c_void_p, P(c_void_p)]),
+        "srmra_mom_moments": (c_int32, [c_void_p, c_void_p, c_void_p]),
+        "srmra_mom_eval": (c_int32, [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]),
+        "srmra_mom_run": (c_int32, [c_void_p, c_int32, c_int32, c_double, c_double, c_double,
+                                    c_double, c_void_p, c_void_p, c_void_p]),
+        "srmra_mom_recompute_moments": (c_int32, [c_void_p]),
+        "srmra_mom_destroy": (None, [c_void_p]),
+        "srmra_mom_last_error": (c_char_p, [c_void_p]),
         "srmra_last_error": (c_char_p, [c_void_p]),
         "srmra_version": (c_char_p, []),
     }
@@ -433,6 +441,68 @@ class Online:
     def close(self):
         if getattr(self, "handle", None):
             lib().srmra_online_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Mom:
+    """Projected method of moments (Algorithm 1) on a :class:`Solver`'s observations:
+    the empirical moments are computed once at construction; :meth:`run` updates the
+    solver's estimate in place (read it with ``solver.state()``)."""
+
+    def __init__(self, solver):
+        self.solver = solver
+        out = c_void_p()
+        self._check(lib().srmra_mom_create(solver.ctx, byref(out)), None)
+        self.handle = out.value
+        self.L, self.l = solver.L, solver.l
+
+    @staticmethod
+    def _check(st, h):
+        if st != SRMRA_OK:
+            msg = lib().srmra_mom_last_error(h)
+            raise SrmraError(st, msg.decode() if msg else "")
+
+    def moments(self):
+        n = self.l * self.l
+        m1 = np.empty(n)
+        m2 = np.empty((n, n))
+        self._check(lib().srmra_mom_moments(self.handle, _ptr(m1), _ptr(m2)), self.handle)
+        return m1, m2
+
+    def eval(self):
+        """(f, df/dx (L x L), df/drho1, df/drho2) at the solver's current estimate."""
+        f = np.empty(1)
+        gx = np.empty((self.L, self.L))
+        g1 = np.empty(self.L)
+        g2 = np.empty(self.L)
+        self._check(lib().srmra_mom_eval(self.handle, _ptr(f), _ptr(gx), _ptr(g1), _ptr(g2)),
+                    self.handle)
+        return float(f[0]), gx, g1, g2
+
+    def run(self, iters: int, F: int, mu_x: float, mu_rho: float, sigma_bm1: float = 1.0,
+            decay: float = 2.0 ** -0.1, denoiser=None, objective: bool = True):
+        out = np.empty(max(iters, 1)) if objective else None
+        fn = None
+        if denoiser is not None:
+            fn = DENOISER_FN(denoiser)
+            self._fn = fn
+        self._check(lib().srmra_mom_run(self.handle, int(iters), int(F), float(mu_x),
+                                        float(mu_rho), float(sigma_bm1), float(decay), fn, None,
+                                        _ptr(out)), self.handle)
+        return None if out is None else out[:iters]
+
+    def recompute_moments(self):
+        self._check(lib().srmra_mom_recompute_moments(self.handle), self.handle)
+
+    def close(self):
+        if getattr(self, "handle", None):
+            lib().srmra_mom_destroy(self.handle)
             self.handle = None
 
     def __del__(self):

@@ -61,6 +61,11 @@ def test_invalid_arguments_are_rejected_without_a_gpu(lib):
     # NULL context is an error, not a crash
     assert lib.srmra_em_iter(None, 1, None) == S.SRMRA_EINVAL
     lib.srmra_destroy(None)
+    out = ctypes.c_void_p()
+    assert lib.srmra_mom_create(None, ctypes.byref(out)) == S.SRMRA_EINVAL and not out.value
+    assert lib.srmra_mom_run(None, 1, 0, 0.1, 0.1, 1.0, 0.9, None, None, None) == S.SRMRA_EINVAL
+    assert lib.srmra_mom_eval(None, None, None, None, None) == S.SRMRA_EINVAL
+    lib.srmra_mom_destroy(None)
 
 
 def test_no_cpu_fallback(lib):
