@@ -316,7 +316,7 @@ srmra_status srmra_profile_read(srmra_ctx* ctx, double* ms, int64_t* count);
 /* ---- Online (mini-batch) EM over shards of the observations. ----
  *
  * The paper points to online strategies to cut the cost of the likelihood term for
- * large N (Sec. 7) without fixing an algorithm; this is mini-batch EM with
+ * large N (Sec. 6) without fixing an algorithm; this is mini-batch EM with
  * stochastic-approximation sufficient statistics.  The observations are split into
  * shard contexts (created with srmra_create, device resident; same L, K, sigma,
  * precision and stream).  The online object holds the estimate theta = (x, rho1,

@@ -36,7 +36,7 @@ Readings where the paper is silent or ambiguous (each also listed in the design doc):
       |c| > 2.7 * sigma_BM (ties are zeroed), no clipping.
   R10 the projection runs after the M-step of every F-th iteration; F = 0 means none.
   R11 a fixed iteration count replaces "until a stopping criterion is met".
-  R13 online EM (the online strategy the paper suggests for large N, Sec. 7, without an
+  R13 online EM (the online strategy the paper suggests for large N, Sec. 6, without an
       algorithm): mini-batch EM with stochastic-approximation sufficient statistics.
       The statistics of Eqs. (x_EM) and (rho_EM) are the per-shift sums
       Z[s] = sum_i w^{i,s} y_i and c[s] = sum_i w^{i,s}; step t takes a batch B_t,
