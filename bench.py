@@ -310,9 +310,10 @@ def online_block(p, w, steps, warmup, srmra, torch, stream, flush, fp32_value, n
 
 def mom_block(p, steps, warmup, srmra, torch, stream, flush, sm_max):
     """Projected MoM (Algorithm 1) on the same observations: the one-pass empirical
-    moments (M1^, M2^ = Y^T Y / N: 2 N l^4 flops) and the projected gradient iterations
-    (the products T^T diag(rho) T and T R: 4 L^2 l^4 flops per step), against the FP32
-    FFMA peak."""
+    moments and the projected gradient iterations, against the FP32 FFMA peak.  Flops
+    counted are the algorithmic ones of the products: M2^ = Y^T Y / N is symmetric, so
+    N l^2 (l^2 + 1) (one multiply-add per unique entry and observation); per iteration
+    the symmetric T^T diag(rho) T, L^2 l^2 (l^2 + 1), plus T R, 2 L^2 l^4."""
     import numpy as np
     s = srmra.Solver(p.L, p.K, p.sigma, p.y, prec="fp32", x0=p.x0, rho1=p.rho1_0,
                      rho2=p.rho2_0, stream=stream.cuda_stream)
@@ -326,10 +327,10 @@ def mom_block(p, steps, warmup, srmra, torch, stream, flush, sm_max):
     m.run(warmup, 0, mu_x, mu_r, objective=False)
     fs = []
     ms_it = time_steps(lambda: fs.append(m.run(1, 0, mu_x, mu_r)), steps, stream, torch, flush)
-    l4 = float(p.l) ** 4
+    l2 = float(p.l) ** 2
     peak = fp32_peak_tflops(sm_max)
-    mom_tf = 2 * p.N * l4 / (float(np.mean(ms_mom)) / 1e3) / 1e12
-    it_tf = 4 * p.L * p.L * l4 / (float(np.mean(ms_it)) / 1e3) / 1e12
+    mom_tf = p.N * l2 * (l2 + 1) / (float(np.mean(ms_mom)) / 1e3) / 1e12
+    it_tf = p.L * p.L * l2 * (3 * l2 + 1) / (float(np.mean(ms_it)) / 1e3) / 1e12
     m.close()
     s.close()
     return {"moments_ms": float(np.mean(ms_mom)), "moments_tflops": mom_tf,

@@ -42,38 +42,69 @@ __device__ __forceinline__ float hi2(f2 v) { return __uint_as_float((unsigned)(v
 constexpr int GT = 128;  // product tile (rows and columns)
 
 struct GemmArgs {
-  const float* A;        // [K][lda], element (k, m)
+  const float* A;        // [K][lda], element (k, m); lda % 4 == 0, 16-byte aligned
   int lda, Mvalid;
-  const float* B;        // [K][ldb], element (k, n)
+  const float* B;        // [K][ldb], element (k, n); ldb % 4 == 0, 16-byte aligned
   int ldb, Nvalid;
-  const float* off;      // per-k offset added to row k of A and of B (nullable)
-  const float* scale;    // per-k scale of row k of A (nullable)
   int Kvalid, kchunk;    // split z covers k in [z kchunk, min(Kvalid, (z + 1) kchunk))
   float* C;              // [split][Mpad][ldc]
   int ldc;
   int64_t c_split;       // elements between splits
+  int sym;               // 1: C is symmetric; only the tiles (bi <= bj) of an nt x nt tile
+  int nt;                //    grid are computed, enumerated row by row by blockIdx.x
 };
 
-// C[m][n] = sum_k (A[k][m] + off[k]) scale[k] (B[k][n] + off[k]) over one 128 x 128 tile
-// and one k range; 256 threads with 8 x 8 outputs each, k staged 8 rows at a time in a
-// double-buffered shared tile.  Rows and columns past Mvalid / Nvalid and k past the range
-// read as zero; the whole tile is written.
+// 16-byte asynchronous copy global -> shared that reads `bytes` (0..16) and zero-fills the
+// rest; with bytes == 0 nothing is read.
+__device__ __forceinline__ void cp_async16(float* dst, const float* src, int bytes) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(d), "l"(src), "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() {
+  asm volatile("cp.async.commit_group;" ::: "memory");
+}
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
+
+constexpr int GK = 16;     // k rows per stage
+constexpr int GSTAGE = 3;  // stages in flight
+
+// C[m][n] = sum_k A[k][m] B[k][n] over one 128 x 128 tile and one k range: 256 threads
+// with 8 x 8 outputs each (packed FMA), operands staged GK rows at a time through a
+// GSTAGE-deep cp.async ring.  Rows and columns past Mvalid / Nvalid and k past the range
+// read as zero (zero-filled copies); the whole tile is written.
 __global__ void __launch_bounds__(256) k_mom_gemm(GemmArgs g) {
-  __shared__ __align__(16) float As[2][8][GT];
-  __shared__ __align__(16) float Bs[2][8][GT];
+  __shared__ __align__(16) float As[GSTAGE][GK][GT];
+  __shared__ __align__(16) float Bs[GSTAGE][GK][GT];
   const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
-  const int m0 = blockIdx.x * GT, n0 = blockIdx.y * GT;
+  int bi = blockIdx.x, bj = blockIdx.y;
+  if (g.sym) {
+    int t = blockIdx.x;
+    bi = 0;
+    while (t >= g.nt - bi) {
+      t -= g.nt - bi;
+      ++bi;
+    }
+    bj = bi + t;
+  }
+  const int m0 = bi * GT, n0 = bj * GT;
   const int k0 = blockIdx.z * g.kchunk, k1 = min(g.Kvalid, k0 + g.kchunk);
-  const int lk = tid >> 5, lc = (tid & 31) * 4;
-  auto load = [&](int k, float (&ra)[4], float (&rb)[4]) {
-    const bool kv = k < k1;
-    const float o = (kv && g.off) ? g.off[k] : 0.f;
-    const float sc = (kv && g.scale) ? g.scale[k] : 1.f;
+  const int nk = k1 > k0 ? (k1 - k0 + GK - 1) / GK : 0;
+  // each thread copies two 16-byte chunks of A and two of B per stage
+  auto issue = [&](int it) {
+    const int st = it % GSTAGE;
 #pragma unroll
-    for (int e = 0; e < 4; ++e) {
-      const int m = m0 + lc + e, n = n0 + lc + e;
-      ra[e] = (kv && m < g.Mvalid) ? (g.A[(int64_t)k * g.lda + m] + o) * sc : 0.f;
-      rb[e] = (kv && n < g.Nvalid) ? g.B[(int64_t)k * g.ldb + n] + o : 0.f;
+    for (int h = 0; h < 2; ++h) {
+      const int c = tid + h * 256, row = c >> 5, col = (c & 31) * 4;
+      const int k = k0 + it * GK + row;
+      const bool kv = k < k1;
+      const int va = kv ? max(0, min(4, g.Mvalid - (m0 + col))) : 0;
+      const int vb = kv ? max(0, min(4, g.Nvalid - (n0 + col))) : 0;
+      cp_async16(&As[st][row][col], va ? g.A + (int64_t)k * g.lda + m0 + col : g.A, va * 4);
+      cp_async16(&Bs[st][row][col], vb ? g.B + (int64_t)k * g.ldb + n0 + col : g.B, vb * 4);
     }
   };
   f2 acc[8][4];
@@ -81,24 +112,23 @@ __global__ void __launch_bounds__(256) k_mom_gemm(GemmArgs g) {
   for (int j = 0; j < 8; ++j)
 #pragma unroll
     for (int c = 0; c < 4; ++c) acc[j][c] = 0ull;
-  float ra[4], rb[4];
-  load(k0 + lk, ra, rb);
 #pragma unroll
-  for (int e = 0; e < 4; ++e) {
-    As[0][lk][lc + e] = ra[e];
-    Bs[0][lk][lc + e] = rb[e];
+  for (int it = 0; it < GSTAGE - 1; ++it) {
+    if (it < nk) issue(it);
+    cp_async_commit();
   }
-  __syncthreads();
-  int cur = 0;
-  for (int kc = k0; kc < k1; kc += 8) {
-    const bool more = kc + 8 < k1;
-    if (more) load(kc + 8 + lk, ra, rb);
+  for (int it = 0; it < nk; ++it) {
+    cp_async_wait<GSTAGE - 2>();
+    __syncthreads();
+    if (it + GSTAGE - 1 < nk) issue(it + GSTAGE - 1);
+    cp_async_commit();
+    const int st = it % GSTAGE;
 #pragma unroll
-    for (int kk = 0; kk < 8; ++kk) {
-      const float4 a0 = *reinterpret_cast<const float4*>(&As[cur][kk][ty * 4]);
-      const float4 a1 = *reinterpret_cast<const float4*>(&As[cur][kk][64 + ty * 4]);
-      const ulonglong2 b0 = *reinterpret_cast<const ulonglong2*>(&Bs[cur][kk][tx * 4]);
-      const ulonglong2 b1 = *reinterpret_cast<const ulonglong2*>(&Bs[cur][kk][64 + tx * 4]);
+    for (int kk = 0; kk < GK; ++kk) {
+      const float4 a0 = *reinterpret_cast<const float4*>(&As[st][kk][ty * 4]);
+      const float4 a1 = *reinterpret_cast<const float4*>(&As[st][kk][64 + ty * 4]);
+      const ulonglong2 b0 = *reinterpret_cast<const ulonglong2*>(&Bs[st][kk][tx * 4]);
+      const ulonglong2 b1 = *reinterpret_cast<const ulonglong2*>(&Bs[st][kk][64 + tx * 4]);
       const float a[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
       const f2 b[4] = {b0.x, b0.y, b1.x, b1.y};
 #pragma unroll
@@ -108,16 +138,8 @@ __global__ void __launch_bounds__(256) k_mom_gemm(GemmArgs g) {
         for (int c = 0; c < 4; ++c) ffma2(acc[j][c], aj, b[c]);
       }
     }
-    if (more) {
-#pragma unroll
-      for (int e = 0; e < 4; ++e) {
-        As[cur ^ 1][lk][lc + e] = ra[e];
-        Bs[cur ^ 1][lk][lc + e] = rb[e];
-      }
-    }
-    __syncthreads();
-    cur ^= 1;
   }
+  cp_async_wait<0>();
   float* C = g.C + (int64_t)blockIdx.z * g.c_split;
 #pragma unroll
   for (int j = 0; j < 8; ++j) {
@@ -131,86 +153,211 @@ __global__ void __launch_bounds__(256) k_mom_gemm(GemmArgs g) {
   }
 }
 
-// part[z][n] = sum over rows k of split z of (A[k][n] + off[k]) scale[k]  (float64).
-__global__ void k_mom_colsum(const float* __restrict__ A, int lda, int cols,
-                             const float* __restrict__ off, const float* __restrict__ scale,
-                             int64_t rows, int64_t chunk, double* __restrict__ part) {
+// Column sums of the centred observations for the moments, per row split z:
+//   part[z][n]       = sum_i y'_i[n],   part[z][l2 + n] = sum_i ybar_i y'_i[n],
+//   part[z][2 l2]    = sum_i ybar_i,    part[z][2 l2 + 1] = sum_i ybar_i^2
+// (float32 inside a split of at most 256 rows in four interleaved chains, float64 across
+// chains).
+__global__ void k_mom_colsum(const float* __restrict__ Y, int ldy, int l2,
+                             const float* __restrict__ ybar, int64_t rows, int64_t chunk,
+                             double* __restrict__ part) {
   const int n = blockIdx.x * blockDim.x + threadIdx.x;
-  if (n >= cols) return;
   const int64_t k0 = blockIdx.y * chunk, k1 = rows < k0 + chunk ? rows : k0 + chunk;
+  double* out = part + (int64_t)blockIdx.y * (2 * l2 + 2);
+  if (n < l2) {
+    float a[4] = {0.f, 0.f, 0.f, 0.f}, b[4] = {0.f, 0.f, 0.f, 0.f};
+    int64_t k = k0;
+    for (; k + 4 <= k1; k += 4) {
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const float v = Y[(k + j) * ldy + n];
+        a[j] += v;
+        b[j] = fmaf(ybar[k + j], v, b[j]);
+      }
+    }
+    for (int j = 0; k < k1; ++k, ++j) {
+      const float v = Y[k * ldy + n];
+      a[j] += v;
+      b[j] = fmaf(ybar[k], v, b[j]);
+    }
+    out[n] = ((double)a[0] + a[1]) + ((double)a[2] + a[3]);
+    out[l2 + n] = ((double)b[0] + b[1]) + ((double)b[2] + b[3]);
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    double s = 0.0, q = 0.0;
+    for (int64_t k = k0; k < k1; ++k) {
+      const double v = (double)ybar[k];
+      s += v;
+      q += v * v;
+    }
+    out[2 * l2] = s;
+    out[2 * l2 + 1] = q;
+  }
+}
+
+// The consumers of a symmetric product walk the 32 x 32 tiles (ti <= tj) of its upper
+// triangle (inside the computed 128 x 128 tiles), one block of 32 x 8 threads per tile,
+// and write the mirrored tile through shared memory.
+__device__ __forceinline__ void upper_tile(int nt32, int& ti, int& tj) {
+  int t = blockIdx.x;
+  ti = 0;
+  while (t >= nt32 - ti) {
+    t -= nt32 - ti;
+    ++ti;
+  }
+  tj = ti + t;
+}
+
+// The column sums of k_mom_colsum reduced over the splits in a fixed order:
+// cs[n] = sum_i y'_i[n], cs[l2 + n] = sum_i ybar_i y'_i[n], cs[2 l2] = sum_i ybar_i,
+// cs[2 l2 + 1] = sum_i ybar_i^2.
+__global__ void k_mom_colsum_fin(const double* __restrict__ part, int nsplit, int l2,
+                                 double* __restrict__ cs) {
+  const int n = blockIdx.x * blockDim.x + threadIdx.x;
+  const int w = 2 * l2 + 2;
+  if (n >= w) return;
   double s = 0.0;
-  for (int64_t k = k0; k < k1; ++k) {
-    const double v = (double)A[k * lda + n] + (off ? (double)off[k] : 0.0);
-    s += scale ? v * (double)scale[k] : v;
-  }
-  part[(int64_t)blockIdx.y * cols + n] = s;
+  for (int p = 0; p < nsplit; ++p) s += part[(int64_t)p * w + n];
+  cs[n] = s;
 }
 
-// Empirical moments from the split partials: M2^ [l2][l2] and M1^ [l2], float64.
-__global__ void k_mom_hat(const float* __restrict__ part, int nsplit, int64_t split_stride,
-                          int l2, int l2p, const double* __restrict__ part1, int nsplit1,
-                          double inv_n, double* __restrict__ M2h, double* __restrict__ M1h) {
-  const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (idx < (int64_t)l2 * l2) {
-    const int m = (int)(idx / l2), n = (int)(idx % l2);
+// Empirical second moment from the split partials of Y'^T Y' (y_i = y'_i + ybar_i 1):
+//   M2^[r][c] = (sum_i y'_i[r] y'_i[c] + v[r] + v[c] + q) / N,
+//   v = sum_i ybar_i y'_i,  q = sum_i ybar_i^2   (float64);
+// and M1^[n] = (sum_i y'_i[n] + sum_i ybar_i) / N.
+__global__ void __launch_bounds__(256) k_mom_hat(const float* __restrict__ part, int nsplit,
+                                                 int64_t split_stride, int l2, int l2p,
+                                                 const double* __restrict__ cs, double inv_n,
+                                                 double* __restrict__ M2h,
+                                                 double* __restrict__ M1h) {
+  __shared__ double tile[32][33];
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+  int ti, tj;
+  upper_tile(l2p / 32, ti, tj);
+  const double q = cs[2 * l2 + 1];
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    const int r = ti * 32 + ty + 8 * j, c = tj * 32 + tx;
     double s = 0.0;
-    for (int p = 0; p < nsplit; ++p) s += (double)part[p * split_stride + (int64_t)m * l2p + n];
-    M2h[idx] = s * inv_n;
+    if (r < l2 && c < l2) {
+      for (int p = 0; p < nsplit; ++p) s += (double)part[p * split_stride + (int64_t)r * l2p + c];
+      s = (s + (cs[l2 + r] + cs[l2 + c]) + q) * inv_n;  // symmetric in (r, c) bit for bit
+      M2h[(int64_t)r * l2 + c] = s;
+    }
+    tile[ty + 8 * j][tx] = s;
   }
-  if (idx < l2) {
-    double s = 0.0;
-    for (int p = 0; p < nsplit1; ++p) s += part1[(int64_t)p * l2 + idx];
-    M1h[idx] = s * inv_n;
+  if (ti != tj) {
+    __syncthreads();
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int r = tj * 32 + ty + 8 * j, c = ti * 32 + tx;
+      if (r < l2 && c < l2) M2h[(int64_t)r * l2 + c] = tile[tx][ty + 8 * j];
+    }
+  }
+  const int n = blockIdx.x * 256 + threadIdx.x;  // the first blocks also write M1^
+  if (n < l2) M1h[n] = (cs[n] + cs[2 * l2]) * inv_n;
+}
+
+// Templates t_s = P R_s x, t_s[n1 l + n2] = x[(n1 K - s1) mod L][(n2 K - s2) mod L], in the
+// layouts T[s][n], TS[s][n] = rho_s t_s[n] and TT[n][s] (zero padding), one block of
+// 32 x 8 threads per 32 x 32 (shift, pixel) tile, the transposed copy through shared
+// memory; and the joint prior rho_s = rho1[s1] rho2[s2] (float, zero padding).
+__global__ void __launch_bounds__(256) k_mom_templates(
+    const float* __restrict__ x, const double* __restrict__ rho1, const double* __restrict__ rho2,
+    int L, int K, int l, int S, int Spad, int l2p, float* __restrict__ T, float* __restrict__ TS,
+    float* __restrict__ TT, float* __restrict__ rho) {
+  __shared__ float tile[32][33];
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+  const int s0 = blockIdx.x * 32, n0 = blockIdx.y * 32;
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    const int s = s0 + ty + 8 * j, n = n0 + tx;
+    float v = 0.f, r = 0.f;
+    if (s < S && n < l * l) {
+      const int s1 = s / L, s2 = s % L, n1 = n / l, n2 = n % l;
+      v = x[((n1 * K - s1) % L + L) % L * L + ((n2 * K - s2) % L + L) % L];
+      r = (float)(rho1[s1] * rho2[s2]);
+    }
+    T[(int64_t)s * l2p + n] = v;
+    TS[(int64_t)s * l2p + n] = r * v;
+    tile[ty + 8 * j][tx] = v;
+  }
+  __syncthreads();
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    const int n = n0 + ty + 8 * j, s = s0 + tx;
+    TT[(int64_t)n * Spad + s] = tile[tx][ty + 8 * j];
+  }
+  if (blockIdx.y == 0 && ty == 0) {
+    const int s = s0 + tx;
+    rho[s] = s < S ? (float)(rho1[s / L] * rho2[s % L]) : 0.f;
   }
 }
 
-// Templates t_s = P R_s x in both layouts, T[s][n] and TT[n][s] (zero padding), and the
-// joint prior rho_s = rho1[s1] rho2[s2] (block row 0).
-__global__ void k_mom_templates(const float* __restrict__ x, const double* __restrict__ rho1,
-                                const double* __restrict__ rho2, int L, int K, int l, int S,
-                                int Spad, int l2p, float* __restrict__ T, float* __restrict__ TT,
-                                float* __restrict__ rho) {
-  const int s = blockIdx.x * blockDim.x + threadIdx.x;
-  const int n = blockIdx.y;
-  if (s >= Spad) return;
-  float v = 0.f;
-  if (s < S && n < l * l) {
-    const int s1 = s / L, s2 = s % L, n1 = n / l, n2 = n % l;
-    v = x[((n1 * K - s1) % L + L) % L * L + ((n2 * K - s2) % L + L) % L];
-  }
-  T[(int64_t)s * l2p + n] = v;
-  TT[(int64_t)n * Spad + s] = v;
-  if (n == 0) rho[s] = s < S ? (float)(rho1[s / L] * rho2[s % L]) : 0.f;
+// M1 = sum_s rho_s t_s in separable form (float64):
+//   Y1[q1][n2] = sum_{s2} rho2[s2] x[q1][(n2 K - s2) mod L]                (k_mom_m1_rows)
+//   M1[n1][n2] = sum_{s1} rho1[s1] Y1[(n1 K - s1) mod L][n2],  r = M1 - M1^   (k_mom_m1)
+__global__ void k_mom_m1_rows(const float* __restrict__ x, const double* __restrict__ rho2,
+                              int L, int K, int l, double* __restrict__ Y1) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= L * l) return;
+  const int q1 = j / l, n2 = j % l;
+  double a = 0.0;
+#pragma unroll 8
+  for (int s2 = 0; s2 < L; ++s2) a += rho2[s2] * (double)x[q1 * L + ((n2 * K - s2) % L + L) % L];
+  Y1[j] = a;
 }
 
-// R = M2 - M2^ (float32 copy for the next product, zero padding), r = M1 - M1^, and the
-// block partials of f = ||R||^2 + lambda ||r||^2.
-__global__ void __launch_bounds__(256) k_mom_residual(
-    const float* __restrict__ part, int nsplit, int64_t split_stride, int l2, int l2p,
-    double sigma2, const double* __restrict__ M2h, const double* __restrict__ part1,
-    int nsplit1, const double* __restrict__ M1h, double lambda, float* __restrict__ R,
-    double* __restrict__ r1, double* __restrict__ fpart) {
+__global__ void k_mom_m1(const double* __restrict__ Y1, const double* __restrict__ rho1, int L,
+                         int K, int l, const double* __restrict__ M1h, double* __restrict__ r1) {
+  const int n = blockIdx.x * blockDim.x + threadIdx.x;
+  if (n >= l * l) return;
+  const int n1 = n / l, n2 = n % l;
+  double a = 0.0;
+#pragma unroll 8
+  for (int s1 = 0; s1 < L; ++s1) a += rho1[s1] * Y1[((n1 * K - s1) % L + L) % L * l + n2];
+  r1[n] = a - M1h[n];
+}
+
+// R = M2 - M2^ (float32, zero padding; both triangles) and the block partials of
+// ||R||_F^2 (an off-diagonal tile counts twice).
+__global__ void __launch_bounds__(256) k_mom_residual(const float* __restrict__ part, int nsplit,
+                                                      int64_t split_stride, int l2, int l2p,
+                                                      double sigma2, const double* __restrict__ M2h,
+                                                      float* __restrict__ R,
+                                                      double* __restrict__ fpart) {
+  __shared__ float tile[32][33];
   __shared__ double red[256];
-  const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+  int ti, tj;
+  upper_tile(l2p / 32, ti, tj);
   double f = 0.0;
-  if (idx < (int64_t)l2p * l2p) {
-    const int m = (int)(idx / l2p), n = (int)(idx % l2p);
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    const int r = ti * 32 + ty + 8 * j, c = tj * 32 + tx;
     float rv = 0.f;
-    if (m < l2 && n < l2) {
+    if (r < l2 && c < l2) {
+      // the split partials in float32 pairs (each already float32-rounded), then float64
+      const float* pp = part + (int64_t)r * l2p + c;
       double s = 0.0;
-      for (int p = 0; p < nsplit; ++p) s += (double)part[p * split_stride + idx];
-      const double d = s + (m == n ? sigma2 : 0.0) - M2h[(int64_t)m * l2 + n];
-      f = d * d;
+      int p = 0;
+      for (; p + 2 <= nsplit; p += 2) s += (double)(pp[p * split_stride] + pp[(p + 1) * split_stride]);
+      if (p < nsplit) s += (double)pp[p * split_stride];
+      const double d = s + (r == c ? sigma2 : 0.0) - M2h[(int64_t)r * l2 + c];
+      f += d * d;
       rv = (float)d;
     }
-    R[idx] = rv;
+    R[(int64_t)r * l2p + c] = rv;
+    tile[ty + 8 * j][tx] = rv;
   }
-  if (idx < l2) {
-    double s = 0.0;
-    for (int p = 0; p < nsplit1; ++p) s += part1[(int64_t)p * l2 + idx];
-    const double d = s - M1h[idx];
-    r1[idx] = d;
-    f += lambda * d * d;
+  if (ti != tj) {
+    f *= 2.0;
+    __syncthreads();
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int r = tj * 32 + ty + 8 * j, c = ti * 32 + tx;
+      R[(int64_t)r * l2p + c] = tile[tx][ty + 8 * j];
+    }
   }
   red[threadIdx.x] = f;
   __syncthreads();
@@ -231,16 +378,19 @@ __global__ void k_mom_gshift(const float* __restrict__ Upart, int nsplit, int64_
   const int s = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
   const int lane = threadIdx.x & 31;
   if (s >= S) return;
-  const double rs = (double)rho[s];
-  double a = 0.0, b = 0.0;
+  const float rs = rho[s], lam2 = (float)(2.0 * lambda);
+  float af = 0.f, bf = 0.f;  // per-lane partial dot products (float32), float64 across lanes
+#pragma unroll 4
   for (int n = lane; n < l2; n += 32) {
-    double u = 0.0;
-    for (int p = 0; p < nsplit; ++p) u += (double)Upart[p * split_stride + (int64_t)s * l2p + n];
-    const double t = (double)T[(int64_t)s * l2p + n];
-    a += u * t;
-    b += t * r1[n];
-    W[(int64_t)s * l2p + n] = (float)(rs * (4.0 * u + 2.0 * lambda * r1[n]));
+    float u = 0.f;
+    for (int p = 0; p < nsplit; ++p) u += Upart[p * split_stride + (int64_t)s * l2p + n];
+    const float t = T[(int64_t)s * l2p + n];
+    const float rn = (float)r1[n];
+    af = fmaf(u, t, af);
+    bf = fmaf(t, rn, bf);
+    W[(int64_t)s * l2p + n] = rs * fmaf(4.f, u, lam2 * rn);
   }
+  double a = af, b = bf;
   for (int o = 16; o > 0; o >>= 1) {
     a += __shfl_xor_sync(0xffffffffu, a, o);
     b += __shfl_xor_sync(0xffffffffu, b, o);
@@ -248,20 +398,23 @@ __global__ void k_mom_gshift(const float* __restrict__ Upart, int nsplit, int64_
   if (lane == 0) gs[s] = 2.0 * a + 2.0 * lambda * b;
 }
 
-// df/dx[q1][q2] = sum_{n1, n2} W[s(n1, q1) L + s(n2, q2)][n1 l + n2] with
-// s(n, q) = (n K - q) mod L per axis (the adjoint of t_s = P R_s x).  One block per row
-// q1; for each n1 and each 32-column chunk of n2 the slab of all L shifts s2 is staged in
-// shared memory (pitch 33) so that the global reads are row-contiguous.
+// Partial df/dx over a range of n1: gxp[z][q1 L + q2] = sum_{n1 in range z, n2}
+// W[s(n1, q1) L + s(n2, q2)][n1 l + n2] with s(n, q) = (n K - q) mod L per axis (the
+// adjoint of t_s = P R_s x).  One block per (row q1, range z); for each n1 and each
+// 32-column chunk of n2 the slab of all L shifts s2 is staged in shared memory (pitch 33)
+// so that the global reads are row-contiguous.
 constexpr int GX_THREADS = 256;
 constexpr int GX_MAXQ = 4;  // L <= GX_THREADS * GX_MAXQ
 __global__ void __launch_bounds__(GX_THREADS) k_mom_gx(const float* __restrict__ W, int L, int K,
-                                                       int l, int l2p, double* __restrict__ gx) {
+                                                       int l, int l2p, int nz,
+                                                       double* __restrict__ gxp) {
   extern __shared__ float slab[];  // [L][33]
-  const int q1 = blockIdx.x, tid = threadIdx.x;
+  const int q1 = blockIdx.x, z = blockIdx.y, tid = threadIdx.x;
+  const int na = z * l / nz, nb = (z + 1) * l / nz;
   double acc[GX_MAXQ];
 #pragma unroll
   for (int j = 0; j < GX_MAXQ; ++j) acc[j] = 0.0;
-  for (int n1 = 0; n1 < l; ++n1) {
+  for (int n1 = na; n1 < nb; ++n1) {
     const int s1 = ((n1 * K - q1) % L + L) % L;
     for (int c0 = 0; c0 < l; c0 += 32) {
       const int cw = min(32, l - c0);
@@ -275,12 +428,14 @@ __global__ void __launch_bounds__(GX_THREADS) k_mom_gx(const float* __restrict__
       for (int jq = 0; jq < GX_MAXQ; ++jq) {
         const int q2 = tid + jq * GX_THREADS;
         if (q2 < L) {
-          double a = 0.0;
+          float a = 0.f;  // at most 32 terms in float32, then float64
+          int s2 = ((c0 * K - q2) % L + L) % L;  // (n2 K - q2) mod L, stepped by K
           for (int j = 0; j < cw; ++j) {
-            const int s2 = (((c0 + j) * K - q2) % L + L) % L;
-            a += (double)slab[s2 * 33 + j];
+            a += slab[s2 * 33 + j];
+            s2 += K;
+            if (s2 >= L) s2 -= L;
           }
-          acc[jq] += a;
+          acc[jq] += (double)a;
         }
       }
     }
@@ -288,7 +443,7 @@ __global__ void __launch_bounds__(GX_THREADS) k_mom_gx(const float* __restrict__
 #pragma unroll
   for (int jq = 0; jq < GX_MAXQ; ++jq) {
     const int q2 = tid + jq * GX_THREADS;
-    if (q2 < L) gx[(int64_t)q1 * L + q2] = acc[jq];
+    if (q2 < L) gxp[(int64_t)z * L * L + (int64_t)q1 * L + q2] = acc[jq];
   }
 }
 
@@ -326,20 +481,33 @@ __device__ void simplex_project(double* v, int n, double* css, int* kk, double* 
   __syncthreads();
 }
 
-// f (from the block partials) into f_out; df/drho1 = G rho2 and df/drho2 = G^T rho1 into
-// g12 (both at the current rho); with apply: x <- x - mu_x gx and rho1, rho2 <- their
+// df/dx = the sum of the nz partials (fixed order) into gx; with apply,
+// x <- x - mu_x df/dx.  One thread per pixel.
+__global__ void k_mom_xstep(const double* __restrict__ gxp, int nz, int S, int apply,
+                            double mu_x, float* __restrict__ x, double* __restrict__ gx) {
+  const int q = blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= S) return;
+  double g = 0.0;
+  for (int z = 0; z < nz; ++z) g += gxp[(int64_t)z * S + q];
+  gx[q] = g;
+  if (apply) x[q] = (float)((double)x[q] - mu_x * g);
+}
+
+// f = ||R||^2 (block partials) + lambda ||r||^2 into f_out; df/drho1 = G rho2 and
+// df/drho2 = G^T rho1 into g12 (both at the current rho); with apply, rho1, rho2 <- their
 // simplex projections after a step mu_rho.  One block of 1024 threads (L <= 1024).
 __global__ void __launch_bounds__(1024) k_mom_step(
-    const double* __restrict__ fpart, int nfp, const double* __restrict__ gs,
-    const double* __restrict__ gx, int L, int apply, double mu_x, double mu_rho,
-    float* __restrict__ x, double* __restrict__ rho1, double* __restrict__ rho2,
-    double* __restrict__ g12, double* __restrict__ f_out, int* __restrict__ status) {
+    const double* __restrict__ fpart, int nfp, const double* __restrict__ r1, int l2,
+    double lambda, const double* __restrict__ gs, int L, int apply, double mu_rho,
+    double* __restrict__ rho1, double* __restrict__ rho2, double* __restrict__ g12,
+    double* __restrict__ f_out, int* __restrict__ status) {
   __shared__ double red[1024], v1[1024], v2[1024], css[1024];
   __shared__ int kk[1024];
   __shared__ double tau;
-  const int t = threadIdx.x;
+  const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
   double f = 0.0;
   for (int k = t; k < nfp; k += 1024) f += fpart[k];
+  for (int n = t; n < l2; n += 1024) f += lambda * r1[n] * r1[n];
   red[t] = f;
   __syncthreads();
   for (int s = 512; s > 0; s >>= 1) {
@@ -350,20 +518,27 @@ __global__ void __launch_bounds__(1024) k_mom_step(
     *f_out = red[0];
     if (!isfinite(red[0])) atomicOr(status, STATUS_NUMERIC);
   }
-  if (t < L) {
-    double a = 0.0, b = 0.0;
-    for (int k = 0; k < L; ++k) {
-      a += gs[(int64_t)t * L + k] * rho2[k];
-      b += gs[(int64_t)k * L + t] * rho1[k];
+  // df/drho1[a] = sum_b G[a][b] rho2[b]: one warp per row a (row-contiguous reads)
+  for (int a = warp; a < L; a += 32) {
+    double g = 0.0;
+#pragma unroll 4
+    for (int b = lane; b < L; b += 32) g += gs[(int64_t)a * L + b] * rho2[b];
+    for (int o = 16; o > 0; o >>= 1) g += __shfl_xor_sync(0xffffffffu, g, o);
+    if (lane == 0) {
+      g12[a] = g;
+      v1[a] = rho1[a] - mu_rho * g;
     }
-    g12[t] = a;
-    g12[L + t] = b;
-    v1[t] = rho1[t] - mu_rho * a;
-    v2[t] = rho2[t] - mu_rho * b;
+  }
+  // df/drho2[b] = sum_a G[a][b] rho1[a]: one thread per column b
+  if (t < L) {
+    double g = 0.0;
+#pragma unroll 8
+    for (int a = 0; a < L; ++a) g += gs[(int64_t)a * L + t] * rho1[a];
+    g12[L + t] = g;
+    v2[t] = rho2[t] - mu_rho * g;
   }
   __syncthreads();
   if (!apply) return;
-  for (int q = t; q < L * L; q += 1024) x[q] = (float)((double)x[q] - mu_x * gx[q]);
   simplex_project(v1, L, css, kk, &tau);
   simplex_project(v2, L, css, kk, &tau);
   if (t < L) {
@@ -378,15 +553,19 @@ struct srmra_mom {
   srmra_ctx* ctx = nullptr;
   int l2p = 0, Mpad_u = 0;
   int ns_y = 1, ns_t = 1, ns_u = 1;  // k splits of the three products
-  int ns_c1 = 1, ns_ct = 1;          // row splits of the two column sums
+  int ns_c1 = 1;                     // row splits of the observation column sum
+  int nz = 1;                        // n1 ranges of the df/dx gather
   double lambda = 0.0;
   double* M2h = nullptr;    // [l2][l2]
   double* M1h = nullptr;    // [l2]
   float* T = nullptr;       // [Spad][l2p]
+  float* TS = nullptr;      // [Spad][l2p] rho_s t_s
   float* TT = nullptr;      // [l2p][Spad]
   float* rho = nullptr;     // [Spad]
   float* part = nullptr;    // split partials of the products
-  double* part1 = nullptr;  // split partials of the column sums [ns][l2]
+  double* part1 = nullptr;  // split partials of the observation column sums [ns_c1][2 l2 + 2]
+  double* cs = nullptr;     // [2 l2 + 2] their totals
+  double* Y1 = nullptr;     // [L][l] first stage of M1
   float* R = nullptr;       // [l2p][l2p]
   float* W = nullptr;       // [Spad][l2p] back-projection operand
   double* r1 = nullptr;     // [l2]
@@ -394,6 +573,7 @@ struct srmra_mom {
   int nfp = 0;
   double* gs = nullptr;     // [S]
   double* gx = nullptr;     // [L*L]
+  double* gxp = nullptr;    // [nz][L*L] partials of df/dx
   double* g12 = nullptr;    // [2L]
   double* fhist = nullptr;  // [fcap]
   int fcap = 0;
@@ -430,12 +610,24 @@ cudaError_t mget(srmra_mom* m, T** p, int64_t count) {
   return cudaMemsetAsync(*p, 0, sizeof(T) * (size_t)count, m->ctx->stream);
 }
 
-// k splits of a product with `tiles` output tiles: about two blocks per SM, at least
-// 256 k per split.
-int product_splits(int64_t tiles, int64_t kdim, int sms) {
-  int64_t s = (2 * (int64_t)sms + tiles - 1) / tiles;
-  const int64_t kmax = (kdim + 255) / 256;
-  s = std::min(s, kmax);
+// Co-resident blocks of the product kernel on the device (SMs x blocks per SM).
+int gemm_slots(int sms) {
+  static int per_sm = 0;
+  if (per_sm == 0) {
+    int b = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_mom_gemm, 256, 0) != cudaSuccess ||
+        b < 1)
+      b = 1;
+    per_sm = b;
+  }
+  return per_sm * sms;
+}
+
+// k splits of a product with `tiles` output tiles: as many as keep all blocks in one
+// wave of co-resident blocks (no partly filled second wave), at least 256 k per split.
+int product_splits(int64_t tiles, int64_t kdim, int slots) {
+  int64_t s = slots / tiles;
+  s = std::min(s, (kdim + 255) / 256);
   return (int)std::max<int64_t>(1, s);
 }
 
@@ -448,19 +640,16 @@ int colsum_splits(int cols, int64_t rows, int sms) {
   return (int)std::max<int64_t>(1, s);
 }
 
+int tri(int n) { return n * (n + 1) / 2; }
+
 void gemm(srmra_mom* m, const GemmArgs& a, int Mpad, int Npad, int nsplit, cudaStream_t st) {
-  dim3 grid((unsigned)(Mpad / GT), (unsigned)(Npad / GT), (unsigned)nsplit);
+  const dim3 grid = a.sym ? dim3((unsigned)tri(a.nt), 1u, (unsigned)nsplit)
+                          : dim3((unsigned)(Mpad / GT), (unsigned)(Npad / GT), (unsigned)nsplit);
   k_mom_gemm<<<grid, 256, 0, st>>>(a);
   m->ctx->launches++;
 }
 
-void colsum(srmra_mom* m, const float* A, int lda, int cols, const float* off,
-            const float* scale, int64_t rows, int nsplit, cudaStream_t st) {
-  const int64_t chunk = ceil_div(rows, nsplit);
-  k_mom_colsum<<<dim3((unsigned)ceil_div(cols, 256), (unsigned)nsplit), 256, 0, st>>>(
-      A, lda, cols, off, scale, rows, chunk, m->part1);
-  m->ctx->launches++;
-}
+
 
 // The empirical moments of the context's observations.
 void launch_moments(srmra_mom* m) {
@@ -468,15 +657,18 @@ void launch_moments(srmra_mom* m) {
   const Geom& g = c->g;
   const cudaStream_t st = c->stream;
   const int l2p = m->l2p;
-  GemmArgs a{c->Yc, g.ldy, g.l2, c->Yc, g.ldy, g.l2, c->ybar, nullptr, (int)g.N,
-             (int)ceil_div(g.N, m->ns_y), m->part, l2p, (int64_t)l2p * l2p};
+  // Y'^T Y' (upper-triangle tiles), the column sums for the ybar terms, then M2^ and M1^
+  GemmArgs a{c->Yc, g.ldy, g.l2, c->Yc, g.ldy, g.l2, (int)g.N, (int)ceil_div(g.N, m->ns_y),
+             m->part, l2p, (int64_t)l2p * l2p, 1, l2p / GT};
   gemm(m, a, l2p, l2p, m->ns_y, st);
-  colsum(m, c->Yc, g.ldy, g.l2, c->ybar, nullptr, g.N, m->ns_c1, st);
-  const int64_t n = (int64_t)g.l2 * g.l2;
-  k_mom_hat<<<(unsigned)ceil_div(n, 256), 256, 0, st>>>(
-      m->part, m->ns_y, (int64_t)l2p * l2p, g.l2, l2p, m->part1, m->ns_c1, 1.0 / (double)g.N,
-      m->M2h, m->M1h);
-  c->launches++;
+  k_mom_colsum<<<dim3((unsigned)ceil_div(g.l2, 256), (unsigned)m->ns_c1), 256, 0, st>>>(
+      c->Yc, g.ldy, g.l2, c->ybar, g.N, ceil_div(g.N, m->ns_c1), m->part1);
+  k_mom_colsum_fin<<<(unsigned)ceil_div(2 * g.l2 + 2, 256), 256, 0, st>>>(m->part1, m->ns_c1,
+                                                                          g.l2, m->cs);
+  k_mom_hat<<<(unsigned)tri(l2p / 32), 256, 0, st>>>(m->part, m->ns_y, (int64_t)l2p * l2p, g.l2,
+                                                     l2p, m->cs, 1.0 / (double)g.N, m->M2h,
+                                                     m->M1h);
+  c->launches += 3;
 }
 
 // f and the gradient at the context's theta; with apply, the projected gradient step.
@@ -485,28 +677,36 @@ void launch_step(srmra_mom* m, int apply, double mu_x, double mu_rho, double* f_
   const Geom& g = c->g;
   const cudaStream_t st = c->stream;
   const int l2p = m->l2p;
-  k_mom_templates<<<dim3((unsigned)ceil_div(g.Spad, 256), (unsigned)l2p), 256, 0, st>>>(
-      c->x, c->rho1, c->rho2, g.L, g.K, g.l, g.S, g.Spad, l2p, m->T, m->TT, m->rho);
-  c->launches++;
-  // M2 - sigma^2 I = T^T diag(rho) T and M1 = T^T rho
-  GemmArgs a2{m->T, l2p, g.l2, m->T, l2p, g.l2, nullptr, m->rho, g.S,
-              (int)ceil_div(g.S, m->ns_t), m->part, l2p, (int64_t)l2p * l2p};
+  k_mom_templates<<<dim3((unsigned)(g.Spad / 32), (unsigned)(l2p / 32)), 256, 0, st>>>(
+      c->x, c->rho1, c->rho2, g.L, g.K, g.l, g.S, g.Spad, l2p, m->T, m->TS, m->TT, m->rho);
+  // M1 = T^T rho (separable form) and r = M1 - M1^
+  k_mom_m1_rows<<<(unsigned)ceil_div((int64_t)g.L * g.l, 128), 128, 0, st>>>(c->x, c->rho2, g.L,
+                                                                            g.K, g.l, m->Y1);
+  k_mom_m1<<<(unsigned)ceil_div(g.l2, 128), 128, 0, st>>>(m->Y1, c->rho1, g.L, g.K, g.l, m->M1h,
+                                                          m->r1);
+  c->launches += 3;
+  // M2 - sigma^2 I = T^T diag(rho) T, then R = M2 - M2^ and ||R||^2
+  GemmArgs a2{m->TS, l2p, g.l2, m->T, l2p, g.l2, g.S, (int)ceil_div(g.S, m->ns_t), m->part,
+              l2p, (int64_t)l2p * l2p, 1, l2p / GT};
   gemm(m, a2, l2p, l2p, m->ns_t, st);
-  colsum(m, m->T, l2p, g.l2, nullptr, m->rho, g.S, m->ns_ct, st);
-  k_mom_residual<<<(unsigned)m->nfp, 256, 0, st>>>(
-      m->part, m->ns_t, (int64_t)l2p * l2p, g.l2, l2p, g.sigma * g.sigma, m->M2h, m->part1,
-      m->ns_ct, m->M1h, m->lambda, m->R, m->r1, m->fpart);
+  k_mom_residual<<<(unsigned)m->nfp, 256, 0, st>>>(m->part, m->ns_t, (int64_t)l2p * l2p, g.l2,
+                                                   l2p, g.sigma * g.sigma, m->M2h, m->R,
+                                                   m->fpart);
   // U = T R (rows R t_s), then the shift gradient and the back-projection operand
-  GemmArgs au{m->TT, g.Spad, g.S, m->R, l2p, g.l2, nullptr, nullptr, g.l2,
-              (int)ceil_div(g.l2, m->ns_u), m->part, l2p, (int64_t)m->Mpad_u * l2p};
+  GemmArgs au{m->TT, g.Spad, g.S, m->R, l2p, g.l2, g.l2, (int)ceil_div(g.l2, m->ns_u), m->part,
+              l2p, (int64_t)m->Mpad_u * l2p, 0, 0};
   gemm(m, au, m->Mpad_u, l2p, m->ns_u, st);
   k_mom_gshift<<<(unsigned)ceil_div(g.S, 8), 256, 0, st>>>(
       m->part, m->ns_u, (int64_t)m->Mpad_u * l2p, m->T, m->rho, g.l2, l2p, g.S, m->r1,
       m->lambda, m->gs, m->W);
-  k_mom_gx<<<(unsigned)g.L, GX_THREADS, m->gx_smem, st>>>(m->W, g.L, g.K, g.l, l2p, m->gx);
-  k_mom_step<<<1, 1024, 0, st>>>(m->fpart, m->nfp, m->gs, m->gx, g.L, apply, mu_x, mu_rho, c->x,
-                                 c->rho1, c->rho2, m->g12, f_out, m->status);
-  c->launches += 4;
+  k_mom_gx<<<dim3((unsigned)g.L, (unsigned)m->nz), GX_THREADS, m->gx_smem, st>>>(
+      m->W, g.L, g.K, g.l, l2p, m->nz, m->gxp);
+  // rho first: its gradient reads nothing the x step writes
+  k_mom_step<<<1, 1024, 0, st>>>(m->fpart, m->nfp, m->r1, g.l2, m->lambda, m->gs, g.L, apply,
+                                 mu_rho, c->rho1, c->rho2, m->g12, f_out, m->status);
+  k_mom_xstep<<<(unsigned)ceil_div(g.S, 256), 256, 0, st>>>(m->gxp, m->nz, g.S, apply, mu_x, c->x,
+                                                           m->gx);
+  c->launches += 5;
 }
 
 srmra_status check_status(srmra_mom* m) {
@@ -537,15 +737,16 @@ srmra_status srmra_mom_create(srmra_ctx* ctx, srmra_mom** out) {
   m->lambda = 1.0 / ((double)g.L * g.L * (1.0 + g.sigma * g.sigma));
   const int l2p = m->l2p;
   const int sms = ctx->num_sms;
-  const int64_t tiles2 = (int64_t)(l2p / GT) * (l2p / GT);
-  m->ns_y = product_splits(tiles2, g.N, sms);
-  m->ns_t = product_splits(tiles2, g.S, sms);
-  m->ns_u = product_splits((int64_t)(m->Mpad_u / GT) * (l2p / GT), g.l2, sms);
-  m->ns_c1 = colsum_splits(g.l2, g.N, sms);
-  m->ns_ct = colsum_splits(g.l2, g.S, sms);
+  const int slots = gemm_slots(sms);
+  const int64_t tiles2 = tri(l2p / GT);  // symmetric products: upper-triangle tiles
+  m->ns_y = product_splits(tiles2, g.N, slots);
+  m->ns_t = product_splits(tiles2, g.S, slots);
+  m->ns_u = product_splits((int64_t)(m->Mpad_u / GT) * (l2p / GT), g.l2, slots);
+  m->ns_c1 = (int)std::max<int64_t>(colsum_splits(g.l2, g.N, sms), ceil_div(g.N, 256));
+  m->nz = (int)std::min<int64_t>(g.l, ceil_div(4 * (int64_t)sms, g.L));
   const int64_t part = std::max({(int64_t)m->ns_y * l2p * l2p, (int64_t)m->ns_t * l2p * l2p,
                                  (int64_t)m->ns_u * m->Mpad_u * l2p});
-  m->nfp = (int)ceil_div((int64_t)l2p * l2p, 256);
+  m->nfp = tri(l2p / 32);  // one f partial per upper-triangle 32 x 32 tile
   m->gx_smem = sizeof(float) * (size_t)g.L * 33;
   cudaError_t e = mget(m, &m->M2h, (int64_t)g.l2 * g.l2);
   if (e == cudaSuccess) e = mget(m, &m->M1h, g.l2);
@@ -553,7 +754,11 @@ srmra_status srmra_mom_create(srmra_ctx* ctx, srmra_mom** out) {
   if (e == cudaSuccess) e = mget(m, &m->TT, (int64_t)l2p * g.Spad);
   if (e == cudaSuccess) e = mget(m, &m->rho, g.Spad);
   if (e == cudaSuccess) e = mget(m, &m->part, part);
-  if (e == cudaSuccess) e = mget(m, &m->part1, (int64_t)std::max(m->ns_c1, m->ns_ct) * g.l2);
+  if (e == cudaSuccess) e = mget(m, &m->part1, (int64_t)m->ns_c1 * (2 * g.l2 + 2));
+  if (e == cudaSuccess) e = mget(m, &m->cs, 2 * (int64_t)g.l2 + 2);
+  if (e == cudaSuccess) e = mget(m, &m->TS, (int64_t)g.Spad * l2p);
+  if (e == cudaSuccess) e = mget(m, &m->Y1, (int64_t)g.L * g.l);
+  if (e == cudaSuccess) e = mget(m, &m->gxp, (int64_t)m->nz * g.S);
   if (e == cudaSuccess) e = mget(m, &m->R, (int64_t)l2p * l2p);
   if (e == cudaSuccess) e = mget(m, &m->W, (int64_t)g.Spad * l2p);
   if (e == cudaSuccess) e = mget(m, &m->r1, g.l2);
