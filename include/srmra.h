@@ -181,6 +181,37 @@ srmra_status srmra_set_state(srmra_ctx* ctx, const float* x, const double* rho1,
  * pointer may be NULL.  EINVAL before the first iteration.  Synchronises. */
 srmra_status srmra_get_estep(srmra_ctx* ctx, double* lse, double* c);
 
+/* ---- Data-parallel decomposition over the observations (one all-reduce per iteration).
+ * The M-step of Eqs. (x_EM), (rho_EM) reads only sums over observations: per shift s
+ * c_s = sum_i w[i,s] and zb_s = sum_i w[i,s] ybar_i, per sub-image r and low-resolution
+ * pixel m the back-projection b'_r[m] of the centred observations, and LL = sum_i lse_i.
+ * Shards of the observations (contexts holding disjoint subsets, all at the same theta)
+ * therefore produce statistics that add, and the M-step of their sum is the EM iteration
+ * of the union.  The vector layout (float64, srmra_stats_length() entries):
+ *   [c_s (L^2, s = s1 L + s2) | zb_s (L^2) | b'_r[m] (K^2 l^2 = L^2, index r l^2 + m,
+ *    r = r1 K + r2) | LL (1)].
+ * Sums are in the centred form of the context: y'_i = y_i - ybar_i, so shards must come
+ * from the same problem (same L, K, sigma); ybar_i is per observation, so any split of
+ * the observations is valid. */
+
+/* srmra_stats_length -- entries of the statistics vector, 3 L^2 + 1. */
+srmra_status srmra_stats_length(const srmra_ctx* ctx, int64_t* len);
+
+/* srmra_estep_stats -- the E-step (both passes) at the context's theta over its
+ * observations, reduced to the statistics vector.  stats: host memory (the call
+ * synchronises and checks the device status word) or, with stats_is_device != 0, device
+ * memory on the context's device, written in stream order without synchronising. */
+srmra_status srmra_estep_stats(srmra_ctx* ctx, double* stats, int32_t stats_is_device);
+
+/* srmra_mstep_stats -- the M-step (Eqs. x_EM, rho_EM) from a statistics vector (for
+ * example the sum over shards): theta_t -> theta_{t+1} in this context, t += 1.  No
+ * projection (call srmra_project).  stats: host, or device memory read in the context's
+ * stream order (the caller orders any producer, e.g. a collective on another stream,
+ * before this call).  loglik_out (host, may be NULL): the LL entry of the vector;
+ * given, the call synchronises and checks the status word (ENUMERIC). */
+srmra_status srmra_mstep_stats(srmra_ctx* ctx, const double* stats, int32_t stats_is_device,
+                               double* loglik_out);
+
 /* srmra_launch_count -- number of CUDA kernels this context has launched so far. */
 srmra_status srmra_launch_count(const srmra_ctx* ctx, int64_t* count);
 

@@ -290,6 +290,7 @@ cudaError_t allocate_buffers(srmra_ctx* c, Allocator& A, const int caps[3], cons
   AL(c->cfin, 2 * (int64_t)g.Spad);
   AL(c->bpart, (int64_t)fin_t_splits(g, c->num_sms) * g.S);
   AL(c->Ar, 2 * g.K * g.K);
+  AL(c->dstats, 3 * (int64_t)g.S + 1);
   AL(c->status, 1);
   AL(c->d_sched, 1);
 #undef AL
@@ -440,6 +441,48 @@ srmra_status srmra_em_iter(srmra_ctx* c, int32_t n_iters, double* loglik_out) {
   if (loglik_out && n_iters > 0) {
     CK(c, cudaMemcpyAsync(loglik_out, c->ll_hist, sizeof(double) * n_iters,
                           cudaMemcpyDeviceToHost, c->stream));
+    return read_status(c);
+  }
+  if (c->flags & SRMRA_FLAG_CHECK_NUMERIC) return read_status(c);
+  return SRMRA_OK;
+}
+
+srmra_status srmra_stats_length(const srmra_ctx* c, int64_t* len) {
+  if (!c || !len) return fail(nullptr, SRMRA_EINVAL, "ctx or len is NULL");
+  *len = 3 * (int64_t)c->g.S + 1;
+  return SRMRA_OK;
+}
+
+srmra_status srmra_estep_stats(srmra_ctx* c, double* stats, int32_t stats_is_device) {
+  if (!c) return fail(nullptr, SRMRA_EINVAL, "ctx is NULL");
+  if (!stats) return fail(c, SRMRA_EINVAL, "stats is NULL");
+  srmra_status st = run_estep_stats(c);
+  if (st != SRMRA_OK) return st;
+  launch_pack_stats(c, stats_is_device ? stats : c->dstats);
+  CK(c, cudaGetLastError());
+  if (stats_is_device) return SRMRA_OK;
+  CK(c, cudaMemcpyAsync(stats, c->dstats, sizeof(double) * (3 * (size_t)c->g.S + 1),
+                        cudaMemcpyDeviceToHost, c->stream));
+  return read_status(c);
+}
+
+srmra_status srmra_mstep_stats(srmra_ctx* c, const double* stats, int32_t stats_is_device,
+                               double* loglik_out) {
+  if (!c) return fail(nullptr, SRMRA_EINVAL, "ctx is NULL");
+  if (!stats) return fail(c, SRMRA_EINVAL, "stats is NULL");
+  srmra_status st = ensure_ll(c, 1);
+  if (st != SRMRA_OK) return st;
+  if (!stats_is_device)
+    CK(c, cudaMemcpyAsync(c->dstats, stats, sizeof(double) * (3 * (size_t)c->g.S + 1),
+                          cudaMemcpyHostToDevice, c->stream));
+  launch_unpack_stats(c, stats_is_device ? stats : c->dstats);
+  launch_mstep(c, c->cfin, c->bpart, 1, c->llpart, 1, c->rho1, c->rho2, c->Ar, c->ll_hist, c->x,
+               c->status, c->stream);
+  CK(c, cudaGetLastError());
+  c->t += 1;
+  if (loglik_out) {
+    CK(c, cudaMemcpyAsync(loglik_out, c->ll_hist, sizeof(double), cudaMemcpyDeviceToHost,
+                          c->stream));
     return read_status(c);
   }
   if (c->flags & SRMRA_FLAG_CHECK_NUMERIC) return read_status(c);

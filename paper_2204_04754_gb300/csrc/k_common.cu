@@ -517,11 +517,11 @@ void launch_stats(srmra_ctx* c) {
 // M-step of Eqs. (x_EM), (rho_EM) from sums in the layout of launch_stats:
 // rho, coverage, LL (from the lse-combine partials) and x.
 void launch_mstep(srmra_ctx* c, const double* cfin, const float* bpart, int n_ts,
-                  const double* llpart, double* rho1, double* rho2, double* Ar,
+                  const double* llpart, int ll_blocks, double* rho1, double* rho2, double* Ar,
                   double* ll_out, float* x, int* status, cudaStream_t stream) {
   const Geom& g = c->g;
-  k_fin_counts<<<1, 1024, 0, stream>>>(cfin, g.Spad, g.S, g.L, g.K, g.l, llpart,
-                                       c->plan.ll_blocks, rho1, rho2, Ar, ll_out, status);
+  k_fin_counts<<<1, 1024, 0, stream>>>(cfin, g.Spad, g.S, g.L, g.K, g.l, llpart, ll_blocks,
+                                       rho1, rho2, Ar, ll_out, status);
   k_fin_x<<<(unsigned)ceil_div(g.S, 256), 256, 0, stream>>>(bpart, n_ts, g.L, g.K, g.l, Ar,
                                                             x, status);
   c->launches += 2;
@@ -529,8 +529,58 @@ void launch_mstep(srmra_ctx* c, const double* cfin, const float* bpart, int n_ts
 
 void launch_finalize(srmra_ctx* c, int ll_index) {
   launch_stats(c);
-  launch_mstep(c, c->cfin, c->bpart, stats_t_splits(c), c->llpart, c->rho1, c->rho2, c->Ar,
-               c->ll_hist + ll_index, c->x, c->status, c->stream);
+  launch_mstep(c, c->cfin, c->bpart, stats_t_splits(c), c->llpart, c->plan.ll_blocks, c->rho1,
+               c->rho2, c->Ar, c->ll_hist + ll_index, c->x, c->status, c->stream);
+}
+
+// The E-step statistics of launch_stats as one float64 vector (sums over the context's
+// observations, so the vectors of disjoint shards of the data add):
+//   [c_s (S) | zb_s (S) | b'_r[m] (K^2 l^2 = S, the partials summed in a fixed order) |
+//    LL (1, the lse-combine partials summed in a fixed order)].
+__global__ void k_pack_stats(const double* __restrict__ cfin, const float* __restrict__ bpart,
+                             int n_ts, const double* __restrict__ llpart, int ll_blocks, int S,
+                             int Spad, double* __restrict__ out) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j < S) {
+    out[j] = cfin[j];
+    out[S + j] = cfin[Spad + j];
+    double b = 0.0;
+    for (int t = 0; t < n_ts; ++t) b += (double)bpart[(int64_t)t * S + j];
+    out[2 * S + j] = b;
+  }
+  if (j == 0) {
+    double ll = 0.0;
+    for (int k = 0; k < ll_blocks; ++k) ll += llpart[k];
+    out[3 * S] = ll;
+  }
+}
+
+// The inverse layout for the M-step: c_s, zb_s into cfin; b' into partial 0 of bpart;
+// LL into llpart[0].
+__global__ void k_unpack_stats(const double* __restrict__ in, int S, int Spad,
+                               double* __restrict__ cfin, float* __restrict__ bpart,
+                               double* __restrict__ llpart) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j < S) {
+    cfin[j] = in[j];
+    cfin[Spad + j] = in[S + j];
+    bpart[j] = (float)in[2 * S + j];
+  }
+  if (j == 0) llpart[0] = in[3 * S];
+}
+
+void launch_pack_stats(srmra_ctx* c, double* out) {
+  const Geom& g = c->g;
+  k_pack_stats<<<(unsigned)ceil_div(g.S, 256), 256, 0, c->stream>>>(
+      c->cfin, c->bpart, stats_t_splits(c), c->llpart, c->plan.ll_blocks, g.S, g.Spad, out);
+  c->launches++;
+}
+
+void launch_unpack_stats(srmra_ctx* c, const double* in) {
+  const Geom& g = c->g;
+  k_unpack_stats<<<(unsigned)ceil_div(g.S, 256), 256, 0, c->stream>>>(in, g.S, g.Spad, c->cfin,
+                                                                       c->bpart, c->llpart);
+  c->launches++;
 }
 
 void launch_dct_sched(srmra_ctx* c, double thr) {

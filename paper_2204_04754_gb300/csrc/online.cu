@@ -176,8 +176,8 @@ srmra_status srmra_online_step(srmra_online* on, int32_t shard, double gamma,
       c->cfin, c->bpart, stats_t_splits(c), g.S, g.Spad, KKl2, gm, 1.0 / (double)c->g.N,
       on->sfin, on->sb, on->b1);
   c->launches++;
-  launch_mstep(c, on->sfin, on->b1, 1, c->llpart, on->rho1, on->rho2, on->Ar, on->ll, on->x,
-               on->status, st);
+  launch_mstep(c, on->sfin, on->b1, 1, c->llpart, c->plan.ll_blocks, on->rho1, on->rho2, on->Ar,
+               on->ll, on->x, on->status, st);
   OCK(on, cudaGetLastError());
   on->steps += 1;
   if (loglik_out) {

@@ -138,6 +138,7 @@ struct srmra_ctx {
   float2* Xf = nullptr;    // FFT form: [K*K][l2] FFT2(x'_r), per iteration
   float2* Gp = nullptr;    // FFT form: [fft_blocks][K*K][l2] partial sum_i conj(W^) Y^'
   double* Ar = nullptr;    // [K*K] coverage per sub-image, then ZB per sub-image [K*K]
+  double* dstats = nullptr;  // [3 L^2 + 1] packed E-step statistics (host transfers)
   double* ll_hist = nullptr;  // [ll_cap]
   int ll_cap = 0;
   int* status = nullptr;   // device status word
@@ -172,8 +173,10 @@ void launch_finalize(srmra_ctx* c, int ll_index);  // launch_stats + launch_mste
 int stats_t_splits(const srmra_ctx* c);
 void launch_stats(srmra_ctx* c);
 void launch_mstep(srmra_ctx* c, const double* cfin, const float* bpart, int n_ts,
-                  const double* llpart, double* rho1, double* rho2, double* Ar,
+                  const double* llpart, int ll_blocks, double* rho1, double* rho2, double* Ar,
                   double* ll_out, float* x, int* status, cudaStream_t stream);
+void launch_pack_stats(srmra_ctx* c, double* out);       // [c | zb | b' | LL], 3 L^2 + 1
+void launch_unpack_stats(srmra_ctx* c, const double* in);
 srmra_status run_estep_stats(srmra_ctx* c);  // prep, both passes, combine, launch_stats
 void launch_dct_denoise(srmra_ctx* c, double sigma_bm, double thr);
 void launch_dct_sched(srmra_ctx* c, double thr);  // projection from the device schedule

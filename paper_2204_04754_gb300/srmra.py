@@ -101,6 +101,9 @@ def lib() -> ctypes.CDLL:
                                              P(c_int64)]),
         "srmra_online_destroy": (None, [c_void_p]),
         "srmra_online_last_error": (c_char_p, [c_void_p]),
+        "srmra_stats_length": (c_int32, [c_void_p, P(c_int64)]),
+        "srmra_estep_stats": (c_int32, [c_void_p, c_void_p, c_int32]),
+        "srmra_mstep_stats": (c_int32, [c_void_p, c_void_p, c_int32, c_void_p]),
         "srmra_mom_create": (c_int32, [c_void_p, P(c_void_p)]),
         "srmra_mom_moments": (c_int32, [c_void_p, c_void_p, c_void_p]),
         "srmra_mom_eval": (c_int32, [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]),
@@ -323,6 +326,33 @@ class Solver:
         c = np.empty(self.L * self.L)
         srmra_get_estep(self.ctx, lse, c)
         return lse, c
+
+    def stats_length(self) -> int:
+        n = c_int64()
+        _check(lib().srmra_stats_length(self.ctx, byref(n)), self.ctx)
+        return n.value
+
+    def estep_stats(self, out=None):
+        """E-step statistics at the current estimate (see include/srmra.h): a float64
+        numpy vector (host), or written into `out`, a float64 CUDA tensor (device, in
+        stream order)."""
+        if out is not None and getattr(out, "is_cuda", False):
+            _check(lib().srmra_estep_stats(self.ctx, c_void_p(out.data_ptr()), 1), self.ctx)
+            return out
+        v = np.empty(self.stats_length())
+        _check(lib().srmra_estep_stats(self.ctx, _ptr(v), 0), self.ctx)
+        return v
+
+    def mstep_stats(self, stats, loglik: bool = True):
+        """M-step from a statistics vector (numpy float64, or a float64 CUDA tensor)."""
+        out = np.empty(1) if loglik else None
+        if getattr(stats, "is_cuda", False):
+            _check(lib().srmra_mstep_stats(self.ctx, c_void_p(stats.data_ptr()), 1, _ptr(out)),
+                   self.ctx)
+        else:
+            v = np.ascontiguousarray(stats, dtype=np.float64)
+            _check(lib().srmra_mstep_stats(self.ctx, _ptr(v), 0, _ptr(out)), self.ctx)
+        return None if out is None else float(out[0])
 
     @property
     def launches(self) -> int:

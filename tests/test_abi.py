@@ -66,6 +66,10 @@ def test_invalid_arguments_are_rejected_without_a_gpu(lib):
     assert lib.srmra_mom_run(None, 1, 0, 0.1, 0.1, 1.0, 0.9, None, None, None) == S.SRMRA_EINVAL
     assert lib.srmra_mom_eval(None, None, None, None, None) == S.SRMRA_EINVAL
     lib.srmra_mom_destroy(None)
+    n = ctypes.c_int64()
+    assert lib.srmra_stats_length(None, ctypes.byref(n)) == S.SRMRA_EINVAL
+    assert lib.srmra_estep_stats(None, None, 0) == S.SRMRA_EINVAL
+    assert lib.srmra_mstep_stats(None, None, 0, None) == S.SRMRA_EINVAL
 
 
 def test_no_cpu_fallback(lib):
