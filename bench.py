@@ -45,6 +45,10 @@ def parse():
     ap.add_argument("--requests", type=int, default=12, help="serve: trace length")
     ap.add_argument("--serve-slots", type=int, default=16)
     ap.add_argument("--serve-budget-gb", type=float, default=120.0)
+    ap.add_argument("--serve-pool", type=int, default=16,
+                    help="serve: distinct seeded problems the requests draw from")
+    ap.add_argument("--rates", default=None,
+                    help="serve: comma-separated arrival rates per second (a sweep)")
     ap.add_argument("--no-mixed", action="store_true",
                     help="skip the bf16x3-vs-fp32 comparison block")
     return ap.parse_args()
@@ -408,55 +412,23 @@ def run_batched(args, rank, world, local):
     _ = np
 
 
-def run_serve(args, rank, local):
-    """Poisson arrivals of projected-EM solve requests (L in {64,96,128}, K in {2,4},
-    N in {1e4, 5e4, 1e5}, sigma ~ U[0.2, 1], 30 projected iterations) served with
-    continuous batching.  Latency = completion - planned arrival (queueing included)."""
+def serve_trace(srmra, srv, probs, arrivals, iters, F):
+    """Submit probs[k] at arrivals[k] (seconds from the start) and step the server until
+    every request has finished.  Returns (latencies in ms, makespan s, server steps);
+    latency = completion - planned arrival (queueing included)."""
     import numpy as np
-    import torch
-    from paper_2204_04754_gb300 import srmra, synth
-    if rank != 0:
-        return
-    torch.cuda.set_device(local)
-    w = synth.WORKLOADS[args.workload]
-    prec = args.prec or w["prec"]
-    rng = np.random.Generator(np.random.PCG64(synth.seed_for(5)))
-    n = args.requests
-    arrivals = np.cumsum(rng.exponential(1.0 / w["rate"], size=n))
-    specs = []
-    for k in range(n):
-        L = int(rng.choice([64, 96, 128]))
-        K = int(rng.choice([2, 4]))
-        N = int(rng.choice([10_000, 50_000, 100_000]))
-        sigma = float(rng.uniform(0.2, 1.0))
-        specs.append((L, K, N, sigma))
-    t0 = time.perf_counter()
-    probs = [synth.make_problem(L, K, N, sg, seed=synth.seed_for(5, k))
-             for k, (L, K, N, sg) in enumerate(specs)]
-    gen_s = time.perf_counter() - t0
-    stream = torch.cuda.current_stream()
-    free, total = torch.cuda.mem_get_info()
-    budget = int(min(free * 0.8, args.serve_budget_gb * 2 ** 30))
-    srv = srmra.Server(budget, max_active=args.serve_slots, prec=prec, stream=stream.cuda_stream)
-    # warm the kernels and graph machinery on a tiny request (not part of the trace)
-    wp = synth.make_problem(64, 4, 2000, 0.5, seed=synth.seed_for(5, 999))
-    wid = srv.submit(wp.L, wp.K, wp.sigma, wp.y, 2, F=w["F"])
-    while srv.step()[0] > 0:
-        pass
-    srv.result(wid, wp.L)
+    n = len(probs)
     ids = {}
     done = {}
     pending = list(range(n))
     steps = 0
-    clocks = ClockSampler(local)
-    clocks.start()
     start = time.perf_counter()
     while len(done) < n:
         now = time.perf_counter() - start
         while pending and arrivals[pending[0]] <= now:
             k = pending.pop(0)
             p = probs[k]
-            ids[k] = srv.submit(p.L, p.K, p.sigma, p.y, w["iters"], F=w["F"])
+            ids[k] = srv.submit(p.L, p.K, p.sigma, p.y, iters, F=F)
         running, queued, finished = srv.step()
         steps += 1
         if finished:
@@ -469,22 +441,81 @@ def run_serve(args, rank, local):
             if wait > 0:
                 time.sleep(min(wait, 0.05))
     makespan = time.perf_counter() - start
-    clk = clocks.stop()
     lat = np.array([1e3 * (done[k] - arrivals[k]) for k in range(n)])
+    return lat, makespan, steps
+
+
+def run_serve(args, rank, local):
+    """Poisson arrivals of projected-EM solve requests (L in {64,96,128}, K in {2,4},
+    N in {1e4, 5e4, 1e5}, sigma ~ U[0.2, 1], 30 projected iterations) served with
+    continuous batching.  Latency = completion - planned arrival (queueing included).
+    The requests draw their data from a pool of --serve-pool distinct seeded problems
+    (request k uses pool entry k mod pool size), so that long traces fit in host memory;
+    --rates runs the same trace at several arrival rates (a sweep that shows where the
+    offered load exceeds capacity)."""
+    import numpy as np
+    import torch
+    from paper_2204_04754_gb300 import srmra, synth
+    if rank != 0:
+        return
+    torch.cuda.set_device(local)
+    w = synth.WORKLOADS[args.workload]
+    prec = args.prec or w["prec"]
+    rng = np.random.Generator(np.random.PCG64(synth.seed_for(5)))
+    n = args.requests
+    rates = [float(r) for r in args.rates.split(",")] if args.rates else [w["rate"]]
+    unit_gaps = rng.exponential(1.0, size=n)  # arrivals at rate r: cumsum(unit_gaps) / r
+    pool = min(n, args.serve_pool)
+    specs = []
+    for k in range(pool):
+        L = int(rng.choice([64, 96, 128]))
+        K = int(rng.choice([2, 4]))
+        N = int(rng.choice([10_000, 50_000, 100_000]))
+        sigma = float(rng.uniform(0.2, 1.0))
+        specs.append((L, K, N, sigma))
+    t0 = time.perf_counter()
+    pool_probs = [synth.make_problem(L, K, N, sg, seed=synth.seed_for(5, k))
+                  for k, (L, K, N, sg) in enumerate(specs)]
+    probs = [pool_probs[k % pool] for k in range(n)]
+    gen_s = time.perf_counter() - t0
+    stream = torch.cuda.current_stream()
+    free, total = torch.cuda.mem_get_info()
+    budget = int(min(free * 0.8, args.serve_budget_gb * 2 ** 30))
+    srv = srmra.Server(budget, max_active=args.serve_slots, prec=prec, stream=stream.cuda_stream)
+    # warm the kernels and graph machinery on a tiny request (not part of the trace)
+    wp = synth.make_problem(64, 4, 2000, 0.5, seed=synth.seed_for(5, 999))
+    wid = srv.submit(wp.L, wp.K, wp.sigma, wp.y, 2, F=w["F"])
+    while srv.step()[0] > 0:
+        pass
+    srv.result(wid, wp.L)
     pairs = sum(p.N * p.L * p.L * w["iters"] for p in probs)
+    sweep = []
+    clocks = ClockSampler(local)
+    clocks.start()
+    for rate in rates:
+        arrivals = np.cumsum(unit_gaps) / rate
+        lat, makespan, steps = serve_trace(srmra, srv, probs, arrivals, w["iters"], w["F"])
+        sweep.append({"rate_per_s": rate, "p50_ms": float(np.percentile(lat, 50)),
+                      "p99_ms": float(np.percentile(lat, 99)), "max_ms": float(lat.max()),
+                      "solves_per_s": n / makespan, "pairs_per_s": pairs / makespan,
+                      "makespan_s": makespan, "server_steps": steps})
+    clk = clocks.stop()
     srv.close()
-    out = {"metric": "serve p99 latency", "value": float(np.percentile(lat, 99)), "unit": "ms",
-           "n_gpus": 1, "steps": steps, "warmup": 1, "higher_is_better": False,
+    head = sweep[0]
+    out = {"metric": "serve p99 latency", "value": head["p99_ms"], "unit": "ms",
+           "n_gpus": 1, "steps": head["server_steps"], "warmup": 1, "higher_is_better": False,
            "scaling": "weak", "vs_baseline": None, "dtype": prec,
            "data": "synthetic (seeded requests)",
-           "config": {"workload": args.workload, "requests": n, "rate_per_s": w["rate"],
+           "config": {"workload": args.workload, "requests": n, "rate_per_s": head["rate_per_s"],
                       "iters_per_request": w["iters"], "F": w["F"],
                       "mix": "L {64,96,128} x K {2,4} x N {1e4,5e4,1e5}, sigma U[0.2,1]",
-                      "slots": args.serve_slots, "budget_bytes": budget,
-                      "data_generation_s": gen_s},
-           "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
-           "max_ms": float(lat.max()), "solves_per_s": n / makespan,
-           "pairs_per_s": pairs / makespan, "makespan_s": makespan, "clocks": clk}
+                      "distinct_problems": pool, "slots": args.serve_slots,
+                      "budget_bytes": budget, "data_generation_s": gen_s},
+           "p50_ms": head["p50_ms"], "p99_ms": head["p99_ms"], "max_ms": head["max_ms"],
+           "solves_per_s": head["solves_per_s"], "pairs_per_s": head["pairs_per_s"],
+           "makespan_s": head["makespan_s"], "clocks": clk}
+    if len(sweep) > 1:
+        out["sweep"] = sweep
     print(json.dumps(out), flush=True)
 
 

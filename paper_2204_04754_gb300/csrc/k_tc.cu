@@ -658,7 +658,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
 }
 
 // ------------------------------------------------------------------------------ pass 2,
-// cluster form.  A cluster of G CTAs (G = 2..4) shares one 128-shift tile and one range
+// cluster form.  A cluster of G CTAs (G = 2..8) shares one 128-shift tile and one range
 // of observation blocks; CTA `rank` owns pixel chunk cg*G + rank of Z'.  In each round
 // every CTA computes the logits of ITS OWN 128-observation block (no CTA recomputes
 // another's), turns them into the fp16 weight tile, and the tile reaches the other CTAs
@@ -669,7 +669,19 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
 // of the round.  The weights of one (shift tile, observation block) are thus computed
 // once instead of once per pixel chunk.
 constexpr int P2C_SLOTS = 7;
-constexpr int MBOX_DEPTH = 4;
+constexpr int P2C_MAX_G = 8;  // largest cluster (the portable limit); mailbox row width
+// Mailbox rows, one per use: a producer leads a peer's epilogue by at most one row per ring
+// slot it holds for that peer (the slot is freed only after the peer has read the row and
+// sent its tile), so more rows than ring slots keep a row from being reused before it is
+// read, whatever the cluster's chunk ownership (CTAs without a pixel chunk hold one slot
+// per single-block unit and can run up to P2C_SLOTS units ahead).
+constexpr int MBOX_DEPTH = 8;
+static_assert(MBOX_DEPTH > P2C_SLOTS, "a mailbox row could be reused before it is read");
+// barriers: full, empty (ring), sfull, sempty, zfull, zempty, mfull (rows), drain, wready;
+// then the mailbox, the TMEM address and the abort flag, in 512 bytes after the ring
+static_assert((2 * P2C_SLOTS + 2 + 2 + 1 + 1 + MBOX_DEPTH + 1 + 1) * 8 +
+                      MBOX_DEPTH * P2C_MAX_G * 4 + 4 + 4 <= 512,
+              "cluster pass-2 bookkeeping exceeds its 512 bytes");
 
 template <int NPROD>
 __global__ void __launch_bounds__(TC_THREADS, 1)
@@ -686,8 +698,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
   uint64_t* mfull = zempty + 1;  // [MBOX_DEPTH]: one barrier per mailbox row
   uint64_t* drain = mfull + MBOX_DEPTH;
   uint64_t* wready = drain + 1;  // the 128 epilogue threads have written the weight tile
-  uint32_t* mbox = (uint32_t*)(wready + 1);  // [MBOX_DEPTH][4] reserved slot indices
-  uint32_t* tptr = mbox + MBOX_DEPTH * 4;
+  uint32_t* mbox = (uint32_t*)(wready + 1);  // [MBOX_DEPTH][P2C_MAX_G] reserved slots
+  uint32_t* tptr = mbox + MBOX_DEPTH * P2C_MAX_G;
   volatile int* abort = (volatile int*)(tptr + 1);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const uint32_t rank = cluster_rank();
@@ -723,7 +735,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
 
   if (warp == 0) {
     if (lane == 0) {
-      uint32_t it = 0, sent[4] = {0, 0, 0, 0};
+      uint32_t it = 0, sent[P2C_MAX_G] = {};
       bool ok = true;
       auto reserve = [&](bool expect_copy) -> int {
         const int st = it % P2C_SLOTS;
@@ -787,7 +799,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             // row sent % DEPTH of peer kq's mailbox, and that row's own barrier, so the
             // arrivals of different rounds can never complete each other's phases
             const uint32_t row = sent[kq] % MBOX_DEPTH;
-            st_cluster_u32(mapa(smem_u32(mbox + row * 4 + rank), kq), (uint32_t)st);
+            st_cluster_u32(mapa(smem_u32(mbox + row * P2C_MAX_G + rank), kq), (uint32_t)st);
             mbar_arrive_cluster(mapa(smem_u32(&mfull[row]), kq));
             ++sent[kq];
             ++it;
@@ -887,7 +899,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
           }
           const int nqp = j >= 1 ? min(G, nb - (j - 1) * G) : 0;
           // same slot order as the producer: W0 W1 T0 T0 W2 T1 T1 W3 T2 T2 T3 T3
-          int stPs[4] = {0, 0, 0, 0};
+          int stPs[P2C_MAX_G] = {};
           if (nqp > 0) {
             stPs[0] = wait_slot();
             ++it;
@@ -1013,7 +1025,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         ok = __all_sync(0xffffffffu,
                         mbar_wait_cluster(&mfull[mr % MBOX_DEPTH], (mr / MBOX_DEPTH) & 1, abort));
         if (!ok) break;
-        const uint32_t* mrow = mbox + (mr % MBOX_DEPTH) * 4;
+        const uint32_t* mrow = mbox + (mr % MBOX_DEPTH) * P2C_MAX_G;
         const int own = (int)mrow[rank];
         uint8_t* prow = smem + own * SLOT + row * 128;
 #pragma unroll
@@ -1087,7 +1099,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
   cluster_sync_all();  // no CTA leaves while a peer may still copy into it
 }
 
-// ring + bookkeeping (25 mbarriers, mailbox, TMEM address, abort flag: < 512 bytes) +
+// ring + bookkeeping (30 mbarriers, 8 x 8 mailbox, TMEM address, abort flag: 504 of the
+// 512 bytes) +
 // per-warp staging of one 32-observation chunk's (ybar, lse2) (4 x 256 bytes)
 constexpr size_t P2C_SMEM = 1024 + P2C_SLOTS * SLOT + 512 + 1024;
 static_assert(P2C_SMEM <= 232448, "exceeds the shared memory of one CTA");
@@ -1193,6 +1206,8 @@ cudaError_t set_smem(K kernel, size_t bytes) {
 
 }  // namespace
 
+int choose_p2_cluster(int chunks, int prec, int num_sms);
+
 // Work decomposition of the tensor-core passes.  s1 multiplies the number of shift
 // groups of pass 1 and s2 the number of observation ranges of pass 2: finer units
 // balance a grouped launch better at the price of more partial sums.  The result is
@@ -1220,17 +1235,7 @@ void plan_tc(srmra_ctx* c, int s1, int s2) {
   p.p2_iblk_per_split = (int)ceil_div(n_iblk, ns);
   p.p2_nsplit = (int)ceil_div(n_iblk, p.p2_iblk_per_split);
   // cluster size of pass 2: CTAs that share each weight tile, one pixel chunk each
-  int G = 1;
-  if (chunks > 1 && !c->no_cluster) {
-    if (chunks % 4 == 0)
-      G = 4;
-    else if (chunks % 3 == 0)
-      G = 3;
-    else if (chunks % 2 == 0)
-      G = 2;
-    else
-      G = chunks < 4 ? chunks : 4;
-  }
+  const int G = c->no_cluster ? 1 : choose_p2_cluster(chunks, c->prec, sms);
   p.p2_gc = G;
   p.p2_chunk_groups = (int)ceil_div(chunks, G);
   p.nparts_z = p.p2_nsplit;
@@ -1348,8 +1353,10 @@ void fill_inst(const srmra_ctx* c, TcInst* I) {
 // Co-resident clusters of G CTAs of the clustered pass-2 kernel (queried once per G).
 template <int NPROD>
 int max_clusters(int G, int num_sms) {
-  static int cache[5] = {0, 0, 0, 0, 0};
+  static int cache[P2C_MAX_G + 1] = {};
   if (cache[G] > 0) return cache[G];
+  cudaGetLastError();
+  set_smem(k_p2c_tc<NPROD>, P2C_SMEM);
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3((unsigned)(G * (num_sms / G)), 1, 1);
   cfg.blockDim = dim3(TC_THREADS, 1, 1);
@@ -1423,6 +1430,30 @@ cudaError_t launch_group(int pass, const TcInst* d_insts, const int64_t* d_ustar
 }
 
 }  // namespace
+
+// Cluster size of pass 2 for `chunks` 256-pixel chunks of Z'.  Up to 4 chunks one cluster
+// covers them all (G = chunks).  Beyond, the weights of a (shift tile, observation block)
+// are computed once per group of G chunks, so G trades recompute against how many
+// clusters of G co-reside (GPC packing): the G in 2..8 (and <= chunks) that minimises the
+// executed work per co-resident CTA, (NPROD groups + 1) / (G clusters(G)) with
+// groups = ceil(chunks / G) (NPROD logit products, one Z' product per pair and pixel).
+int choose_p2_cluster(int chunks, int prec, int num_sms) {
+  if (chunks <= 1) return 1;
+  if (chunks <= 4) return chunks;
+  const int nprod = prec == SRMRA_BF16X3 ? 3 : 1;
+  int best = 4;
+  double best_cost = 0.0;
+  for (int G = 2; G <= P2C_MAX_G && G <= chunks; ++G) {
+    const int groups = (chunks + G - 1) / G;
+    const int ncl = nprod == 3 ? max_clusters<3>(G, num_sms) : max_clusters<1>(G, num_sms);
+    const double cost = (double)(nprod * groups + 1) / ((double)G * (double)ncl);
+    if (best_cost == 0.0 || cost < best_cost) {
+      best = G;
+      best_cost = cost;
+    }
+  }
+  return best;
+}
 
 size_t tc_inst_bytes() { return sizeof(TcInst); }
 

@@ -164,6 +164,9 @@ WORKLOADS = {
 }
 
 
+# the largest request of the serving mix, as a single problem
+WORKLOADS["largest_request_L128_K2_N1e5"] = dict(L=128, K=2, N=100_000, sigma=0.5,
+                                                 n_blobs=6, iters=30, F=1, config=5)
 WORKLOADS["batched_64"] = dict(count=64, iters=30, F=1, config=4, prec="bf16x3")
 WORKLOADS["serve"] = dict(rate=50.0, iters=30, F=1, config=5, prec="bf16x3")
 

@@ -13,16 +13,21 @@ import random
 
 import pytest
 
-SLOTS, MBOX = 7, 4
+SLOTS, MBOX = 7, 8
 
 
-def run(G, units, order, seed=0, nk=16, cvalid=None):
+class MailboxRace(Exception):
+    """An epilogue read a mailbox row whose entries belong to different rounds."""
+
+
+def run(G, units, order, seed=0, nk=16, cvalid=None, mbox=MBOX):
     """units: observation blocks per work unit (every CTA of the cluster walks the same
     units).  order: 'lookahead' (the kernel's) or 'weights_first'.  Returns True when
     every role finishes, False on a deadlock."""
     rnd = random.Random(seed)
     st = [dict(free=[0] * SLOTS, full=[0] * SLOTS, sfull=[0, 0], sempty=[0, 0], zfull=0,
-               zempty=0, mfull=[0] * MBOX, mbox=[[None] * G for _ in range(MBOX)])
+               zempty=0, mfull=[0] * mbox, mbox=[[None] * G for _ in range(mbox)],
+               rounds=[[None] * G for _ in range(mbox)])
           for _ in range(G)]
     valid = cvalid or [True] * G
 
@@ -39,8 +44,9 @@ def run(G, units, order, seed=0, nk=16, cvalid=None):
 
         def reserve_w(kq):  # a slot for CTA kq's weight tile, announced in its mailbox
             s = yield from reserve()
-            row = sent[kq] % MBOX
+            row = sent[kq] % mbox
             st[kq]["mbox"][row][r] = s
+            st[kq]["rounds"][row][r] = sent[kq]  # which use of the row this entry is for
             st[kq]["mfull"][row] += 1
             sent[kq] += 1
 
@@ -134,8 +140,10 @@ def run(G, units, order, seed=0, nk=16, cvalid=None):
                 b, need = sc & 1, (sc >> 1) + 1
                 yield lambda b=b, need=need: st[r]["sfull"][b] >= need
                 st[r]["sempty"][b] += 1  # weights computed; logits released
-                row, mneed = mr % MBOX, G * (mr // MBOX + 1)
+                row, mneed = mr % mbox, G * (mr // mbox + 1)
                 yield lambda row=row, mneed=mneed: st[r]["mfull"][row] >= mneed
+                if st[r]["rounds"][row] != [mr] * G:
+                    raise MailboxRace((r, mr, st[r]["rounds"][row]))
                 slots = list(st[r]["mbox"][row])
                 for j in range(G):  # own slot written, copies land in the others'
                     st[j]["full"][slots[j]] += 1
@@ -162,15 +170,33 @@ def run(G, units, order, seed=0, nk=16, cvalid=None):
         ro[1] = next(ro[0], None)
 
 
-UNITS = [[24] * 4, [23] * 4, [24, 23, 24, 23], [6], [2], [5, 3], [1], [7, 1, 9], [13] * 3]
+UNITS = [[24] * 4, [23] * 4, [24, 23, 24, 23], [6], [2], [5, 3], [1], [7, 1, 9], [13] * 3,
+         [16] * 2, [40], [9, 7], [1] * 10, [2, 1, 1, 1, 1, 1, 1, 3]]
 
 
-@pytest.mark.parametrize("G", [2, 3, 4])
+def cvalid_patterns(G):
+    """Which CTAs of the cluster own a pixel chunk: all, all but one, one (a last chunk
+    group with a single chunk), and about half."""
+    return [None, [True] * (G - 1) + [False], [True] + [False] * (G - 1),
+            [k < (G + 1) // 2 for k in range(G)]]
+
+
+@pytest.mark.parametrize("G", [2, 3, 4, 5, 6, 7, 8])
 def test_kernel_slot_order_never_deadlocks(G):
     for units in UNITS:
-        for cvalid in (None, [True] * (G - 1) + [False]):
+        for cvalid in cvalid_patterns(G):
             for seed in range(3):
-                assert run(G, units, "lookahead", seed=seed, cvalid=cvalid), (units, cvalid)
+                assert run(G, units, "lookahead", seed=seed, cvalid=cvalid, nk=8), (units, cvalid)
+
+
+def test_model_catches_a_mailbox_shallower_than_the_ring():
+    """A producer may lead a peer's epilogue by one mailbox row per ring slot it holds
+    for that peer (at most 7); with rows for only 4 uses, CTAs that own no pixel chunk
+    in a run of one-block units (one ring slot per unit) overwrite rows not yet read."""
+    with pytest.raises(MailboxRace):
+        for seed in range(6):
+            run(4, [1] * 10, "lookahead", seed=seed, cvalid=[True, False, False, False], nk=8,
+                mbox=4)
 
 
 def test_model_catches_the_weights_first_order():

@@ -64,6 +64,12 @@ CASES = [
     (64, 2, 700, 0.3),     # l = 32: four pixel chunks
     (48, 1, 300, 0.8),     # l^2 = 2304
     (32, 2, 1000, 1.0),    # low SNR
+    # l^2 = 4096 (sixteen pixel chunks, clusters of up to 8) and l^2 = 2304 (nine chunks,
+    # two chunk groups).  The fp16 M-step rounding of the mixed form averages over the
+    # observations (measured at L = 128: 1.5e-4 with N = 300, 2.6e-5 with N = 1200, the
+    # same in the cluster and per-chunk forms), so these shapes use N >= 900.
+    (128, 2, 1200, 0.5),
+    (96, 2, 900, 0.6),
 ]
 
 
@@ -117,7 +123,8 @@ def test_precision_workload_full_size_sampled(S, name):
     assert np.all(np.isfinite(x))
 
 
-@pytest.mark.parametrize("L,K,N,sigma", [(64, 2, 900, 0.3), (48, 1, 400, 0.8), (96, 4, 600, 0.5)])
+@pytest.mark.parametrize("L,K,N,sigma", [(64, 2, 900, 0.3), (48, 1, 400, 0.8), (96, 4, 600, 0.5),
+                                         (128, 2, 500, 0.5), (112, 2, 300, 0.7)])
 def test_cluster_and_per_chunk_pass2_agree(S, L, K, N, sigma):
     """The cluster form of pass 2 (weights computed once per observation block and
     shared through distributed shared memory) and the per-chunk form (weights
