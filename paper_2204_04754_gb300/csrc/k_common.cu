@@ -180,6 +180,7 @@ __global__ void k_fin_sums(const float* __restrict__ cp, const float* __restrict
   const int s = blockIdx.x * blockDim.x + threadIdx.x;
   if (s >= S) return;
   double c = 0.0, z = 0.0;
+#pragma unroll 8  // loads issued ahead; the additions keep their order
   for (int p = 0; p < nparts; ++p) {
     c += (double)cp[(int64_t)p * Spad + s];
     z += (double)zbp[(int64_t)p * Spad + s];
@@ -194,10 +195,12 @@ __device__ __forceinline__ double warp_sum_f64(double v) {
   return v;
 }
 
-// M-step totals (one block, warp-level float64 reductions in a fixed order):
-//   rho (Eq. rho_EM): joint c_s / sum c, marginals rho1 (rows), rho2 (columns);
-//   coverage A_r = sum_t c_{(r,t)} and ZB_r = sum_t zb_{(r,t)} per sub-image r;
-//   LL(theta_t) = sum of the lse-combine block partials.
+// M-step totals in a fixed order, over K^2 + 1 blocks of 1024 threads:
+//   blocks r < K^2: coverage A_r = sum_t c_{(r,t)} and ZB_r = sum_t zb_{(r,t)} of
+//     sub-image r (each thread a few lags, then a block reduction);
+//   block K^2: rho (Eq. rho_EM) = joint c_s / sum c with its marginals rho1 (rows) and
+//     rho2 (columns), one warp per row / column, and LL(theta_t) = the sum of the
+//     lse-combine block partials.
 __global__ void __launch_bounds__(1024) k_fin_counts(
     const double* __restrict__ cfin, int Spad, int S, int L, int K, int l,
     const double* __restrict__ llpart, int ll_blocks, double* __restrict__ rho1,
@@ -205,6 +208,23 @@ __global__ void __launch_bounds__(1024) k_fin_counts(
     int* __restrict__ status) {
   __shared__ double red[1024];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int KK = K * K;
+  if ((int)blockIdx.x < KK) {
+    const int r = blockIdx.x, r1 = r / K, r2 = r % K, l2 = l * l;
+    double a = 0.0, z = 0.0;
+    for (int t = threadIdx.x; t < l2; t += 1024) {
+      const int s1 = mod_pos((t / l) * K - r1, L), s2 = mod_pos((t % l) * K - r2, L);
+      a += cfin[s1 * L + s2];
+      z += cfin[Spad + s1 * L + s2];
+    }
+    a = block_sum_f64<1024>(a, red);
+    z = block_sum_f64<1024>(z, red);
+    if (threadIdx.x == 0) {
+      Ar[r] = a;
+      Ar[KK + r] = z;
+    }
+    return;
+  }
   double loc = 0.0;
   for (int s = threadIdx.x; s < S; s += 1024) loc += cfin[s];
   const double ctot = block_sum_f64<1024>(loc, red);
@@ -220,22 +240,6 @@ __global__ void __launch_bounds__(1024) k_fin_counts(
         rho1[j] = acc / ctot;
       else
         rho2[j - L] = acc / ctot;
-    }
-  }
-  const int l2 = l * l;
-  for (int r = warp; r < K * K; r += 32) {  // one warp per sub-image
-    const int r1 = r / K, r2 = r % K;
-    double a = 0.0, z = 0.0;
-    for (int t = lane; t < l2; t += 32) {
-      const int s1 = mod_pos((t / l) * K - r1, L), s2 = mod_pos((t % l) * K - r2, L);
-      a += cfin[s1 * L + s2];
-      z += cfin[Spad + s1 * L + s2];
-    }
-    a = warp_sum_f64(a);
-    z = warp_sum_f64(z);
-    if (lane == 0) {
-      Ar[r] = a;
-      Ar[K * K + r] = z;
     }
   }
   if (warp == 0) {
@@ -520,8 +524,8 @@ void launch_mstep(srmra_ctx* c, const double* cfin, const float* bpart, int n_ts
                   const double* llpart, int ll_blocks, double* rho1, double* rho2, double* Ar,
                   double* ll_out, float* x, int* status, cudaStream_t stream) {
   const Geom& g = c->g;
-  k_fin_counts<<<1, 1024, 0, stream>>>(cfin, g.Spad, g.S, g.L, g.K, g.l, llpart, ll_blocks,
-                                       rho1, rho2, Ar, ll_out, status);
+  k_fin_counts<<<(unsigned)(g.K * g.K + 1), 1024, 0, stream>>>(
+      cfin, g.Spad, g.S, g.L, g.K, g.l, llpart, ll_blocks, rho1, rho2, Ar, ll_out, status);
   k_fin_x<<<(unsigned)ceil_div(g.S, 256), 256, 0, stream>>>(bpart, n_ts, g.L, g.K, g.l, Ar,
                                                             x, status);
   c->launches += 2;

@@ -351,6 +351,7 @@ __global__ void __launch_bounds__(256) k_fft_fin_b(const float2* __restrict__ Gp
   const int r = blockIdx.x;
   for (int idx = threadIdx.x; idx < N * N; idx += 256) {
     float2 acc = make_float2(0.f, 0.f);
+#pragma unroll 8  // loads issued ahead; the additions keep their order
     for (int b = 0; b < nb; ++b) {
       const float2 q = Gp[((int64_t)b * KK + r) * (N * N) + idx];
       acc.x += q.x;
@@ -447,6 +448,11 @@ void plan_fft(srmra_ctx* c) {
   B = round_up(B, FFT_WARPS);
   p.fft_obs_per_block = (int)B;
   p.fft_blocks = (int)ceil_div(g.N, B);
+  // pass 1 writes only per-observation results and fits two CTAs per SM: twice the CTAs
+  // (pass 2 keeps one per SM, bounded by its shared memory, and one partial per block)
+  const int64_t B1 = round_up(ceil_div(g.N, 2 * (int64_t)nb), FFT_WARPS);
+  p.fft_p1_obs_per_block = (int)B1;
+  p.fft_p1_blocks = (int)ceil_div(g.N, B1);
   p.p1_groups = KK;
   p.p1_tiles_per_group = 1;
   p.nparts_c = p.fft_blocks;
@@ -489,8 +495,9 @@ void launch_templates_fft(srmra_ctx* c) {
 
 void launch_pass1_fft(srmra_ctx* c) {
   const Geom& g = c->g;
-  const FftPassArgs a = pass_args(c);
-  const dim3 grid((unsigned)c->plan.fft_blocks, (unsigned)(g.K * g.K));
+  FftPassArgs a = pass_args(c);
+  a.B = c->plan.fft_p1_obs_per_block;
+  const dim3 grid((unsigned)c->plan.fft_p1_blocks, (unsigned)(g.K * g.K));
   switch (g.l) {
     case 8: k_fft_p1<8><<<grid, 32 * FFT_WARPS, p1_smem_bytes<8>(), c->stream>>>(a, c->pm, c->ps); break;
     case 16: k_fft_p1<16><<<grid, 32 * FFT_WARPS, p1_smem_bytes<16>(), c->stream>>>(a, c->pm, c->ps); break;

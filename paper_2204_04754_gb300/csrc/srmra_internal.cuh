@@ -80,7 +80,9 @@ struct Plan {
   int nparts_z = 1;         // number of partial Z slices
   int ll_blocks = 1;        // blocks of the lse-combine kernel
   int fft_obs_per_block = 1;  // FFT form: observations per (block, phase) CTA
-  int fft_blocks = 1;         // FFT form: observation blocks
+  int fft_blocks = 1;         // FFT form: observation blocks (pass 2: one partial each)
+  int fft_p1_obs_per_block = 1;  // FFT form, pass 1 (per-observation outputs only)
+  int fft_p1_blocks = 1;
   int cap_p1_groups = 0;    // capacity of the pass-1 partial buffers (0 = unbounded)
   int cap_nsplit = 0;       // capacity of the pass-2 partial buffers (0 = unbounded)
 };
