@@ -1218,7 +1218,23 @@ void plan_tc(srmra_ctx* c, int s1, int s2) {
   const int sms = c->num_sms;
   const int n_st1 = g.Spad / 256;
   const int iblk1 = (int)(g.Npad / 128);
-  int groups = (int)ceil_div(4 * (int64_t)sms, iblk1) * s1;
+  // pass 1 is a persistent kernel that deals its (observation block, shift group) units
+  // round-robin to one CTA per SM: pick the shift-group size that minimises the rounds
+  // times the tiles per unit (plus a quarter tile of per-unit overhead), i.e. the time
+  // of the busiest CTA, so that the last round is not left mostly empty
+  int groups = 1;
+  double best = 0.0;
+  for (int tpg = n_st1; tpg >= 1; --tpg) {
+    const int gr = (int)ceil_div(n_st1, tpg);
+    if (ceil_div(n_st1, gr) != tpg) continue;
+    const int64_t rounds = ceil_div((int64_t)gr * iblk1, sms);
+    const double cost = (double)rounds * (tpg + 0.25);
+    if (best == 0.0 || cost < best) {
+      best = cost;
+      groups = gr;
+    }
+  }
+  groups *= s1;
   groups = groups < 1 ? 1 : (groups > n_st1 ? n_st1 : groups);
   if (p.cap_p1_groups > 0 && groups > p.cap_p1_groups) groups = p.cap_p1_groups;
   p.p1_tiles_per_group = (int)ceil_div(n_st1, groups);
