@@ -474,12 +474,25 @@ int p2_clusters(int gc, int num_sms);
 void plan_simt(srmra_ctx* c) {
   const Geom& g = c->g;
   Plan& p = c->plan;
-  const int slots = c->num_sms * 2;
+  const int slots = c->num_sms * 2;  // pass 1: two 256-thread CTAs per SM (128 registers)
   const int n_tiles = g.Spad / P1_BN;
   const int iblk1 = (int)(g.Npad / P1_BM);
-  int G = (int)ceil_div(4 * (int64_t)slots, iblk1);
-  G = G < 1 ? 1 : (G > n_tiles ? n_tiles : G);
-  p.p1_tiles_per_group = (int)ceil_div(n_tiles, G);
+  // CTAs of equal work run in waves of `slots`: pick the shift tiles per CTA that
+  // minimise waves x (tiles + a quarter tile of per-CTA overhead), so that the last wave
+  // is not mostly empty
+  int tpg_best = 1;
+  double best = 0.0;
+  for (int tpg = n_tiles; tpg >= 1; --tpg) {
+    const int G = (int)ceil_div(n_tiles, tpg);
+    if (ceil_div(n_tiles, G) != tpg) continue;
+    const int64_t waves = ceil_div((int64_t)G * iblk1, slots);
+    const double cost = (double)waves * (tpg + 0.25);
+    if (best == 0.0 || cost < best) {
+      best = cost;
+      tpg_best = tpg;
+    }
+  }
+  p.p1_tiles_per_group = tpg_best;
   p.p1_groups = (int)ceil_div(n_tiles, p.p1_tiles_per_group);
 
   const int chunks = (int)ceil_div(g.l2, P2_BP);
