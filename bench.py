@@ -613,11 +613,17 @@ def main():
         bound = "tensor"
         peak_note = f"dense bf16, sustained, of {peak_src}"
     kern = {"pass1": f"k_p1_{prec}", "pass2": f"k_p2_{prec}"}[dom]
+    traffic = traffic_from_profiles(kern, args.workload, prec)
     roof = {"bound": bound, "kernel": kern, "achieved": achieved, "peak": peak,
-            "unit": "TFLOP/s", "frac": achieved / peak,
-            "traffic": traffic_from_profiles(kern, args.workload, prec),
+            "unit": "TFLOP/s", "frac": achieved / peak, "traffic": traffic,
             "algorithmic_flops_per_launch": per_pair_flops * pairs_per_step,
             "avg_launch_ms": avg_launch_s * 1e3, "peak_source": peak_note}
+    if traffic:
+        # the same kernel's DRAM bandwidth: recorded bytes per launch over the live launch
+        # time, against the measured HBM copy bandwidth
+        hbm = float(peaks["hbm_gbs"])
+        roof["dram_gbs"] = traffic / avg_launch_s / 1e9
+        roof["dram_frac_of_hbm_peak"] = roof["dram_gbs"] / hbm
 
     out = {"metric": METRIC, "value": value, "unit": "pairs/s", "n_gpus": world,
            "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
