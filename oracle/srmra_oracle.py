@@ -19,7 +19,7 @@ It computes, in float64, what the paper defines:
   * Eq. (decaying_function): sigma_BM_t = 2^(-1/10) sigma_BM_{t-1}, sigma_BM_1 = 1.
   * Algorithm 2 (projected EM): F EM steps, then x <- D(x, sigma_BM), then decay.
 
-Readings where the paper is silent or ambiguous (each also listed in the design doc):
+Readings where the paper is silent or ambiguous:
   R1  "P^{-1}" in Eq. (x_EM) is read as P^T (zero-filling adjoint); P has no inverse.
   R2  rho is the product rho1 (x) rho2 (Sec. 2 parameter set, and the diagonal of D_rho
       in the moment formulas); Eq. (rho_EM) is evaluated for the joint, and rho1, rho2
