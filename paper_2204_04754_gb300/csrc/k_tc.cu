@@ -24,6 +24,8 @@
 #include <cuda_bf16.h>
 #include <cudaTypedefs.h>
 
+#include <algorithm>
+
 #include "ptx_sm103.cuh"
 #include "srmra_internal.cuh"
 
@@ -1207,6 +1209,8 @@ cudaError_t set_smem(K kernel, size_t bytes) {
 }  // namespace
 
 int choose_p2_cluster(int chunks, int prec, int num_sms);
+template <int NPROD>
+int max_clusters_p2(int G, int num_sms);
 
 // Work decomposition of the tensor-core passes.  s1 multiplies the number of shift
 // groups of pass 1 and s2 the number of observation ranges of pass 2: finer units
@@ -1243,15 +1247,39 @@ void plan_tc(srmra_ctx* c, int s1, int s2) {
   const int n_st2 = g.Spad / 128;
   const int chunks = (int)ceil_div(g.l2, 256);
   const int n_iblk = (int)(g.Npad / 128);
-  const int64_t per_split = (int64_t)n_st2 * chunks;
-  int ns = (int)((4 * (int64_t)sms + per_split / 2) / per_split) * s2;
+  // cluster size of pass 2: CTAs that share each weight tile, one pixel chunk each
+  const int G = c->no_cluster ? 1 : choose_p2_cluster(chunks, c->prec, sms);
+  // observation splits of pass 2: each split adds a partial Z' (Spad x l2 float32) that
+  // pass 2 writes and the finalize reads, so take the split count that minimises the
+  // busiest cluster's block-rounds plus the partials' cost in the same units (a partial
+  // of 4096 x 1024 floats measured about 1.4 block-rounds)
+  const int ncg = (int)ceil_div(chunks, G);
+  const int64_t slots2 = G > 1 ? (int64_t)(c->prec == SRMRA_BF16X3 ? max_clusters_p2<3>(G, sms)
+                                                                   : max_clusters_p2<1>(G, sms))
+                               : (int64_t)sms;
+  const double part_cost = 1.4 * (double)g.Spad * (double)g.ldy / (4096.0 * 1024.0);
+  // no more splits than about four units per SM would give (bounds the partial buffers)
+  const int64_t per_split_old = (int64_t)n_st2 * chunks;
+  const int ns_max = (int)std::max<int64_t>(1, (4 * (int64_t)sms + per_split_old / 2) /
+                                                   per_split_old);
+  int ns = 1;
+  double best_ns = 0.0;
+  for (int cand = 1; cand <= ns_max && cand <= 64 && cand <= n_iblk; ++cand) {
+    const int64_t per = ceil_div(n_iblk, cand);
+    if (cand > 1 && ceil_div(n_iblk, per) != cand) continue;
+    const int64_t units = (int64_t)n_st2 * ncg * cand;
+    const double cost = (double)ceil_div(units, slots2) * (double)per + part_cost * cand;
+    if (best_ns == 0.0 || cost < best_ns) {
+      best_ns = cost;
+      ns = cand;
+    }
+  }
+  ns *= s2;
   ns = ns < 1 ? 1 : (ns > n_iblk ? n_iblk : ns);
   if (ns > 64) ns = 64;
   if (p.cap_nsplit > 0 && ns > p.cap_nsplit) ns = p.cap_nsplit;
   p.p2_iblk_per_split = (int)ceil_div(n_iblk, ns);
   p.p2_nsplit = (int)ceil_div(n_iblk, p.p2_iblk_per_split);
-  // cluster size of pass 2: CTAs that share each weight tile, one pixel chunk each
-  const int G = c->no_cluster ? 1 : choose_p2_cluster(chunks, c->prec, sms);
   p.p2_gc = G;
   p.p2_chunk_groups = (int)ceil_div(chunks, G);
   p.nparts_z = p.p2_nsplit;
@@ -1446,6 +1474,13 @@ cudaError_t launch_group(int pass, const TcInst* d_insts, const int64_t* d_ustar
 }
 
 }  // namespace
+
+template <int NPROD>
+int max_clusters_p2(int G, int num_sms) {
+  return max_clusters<NPROD>(G, num_sms);
+}
+template int max_clusters_p2<1>(int, int);
+template int max_clusters_p2<3>(int, int);
 
 // Cluster size of pass 2 for `chunks` 256-pixel chunks of Z'.  Up to 4 chunks one cluster
 // covers them all (G = chunks).  Beyond, the weights of a (shift tile, observation block)
