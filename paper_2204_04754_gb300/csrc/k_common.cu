@@ -261,38 +261,47 @@ __global__ void __launch_bounds__(1024) k_fin_counts(
 __global__ void __launch_bounds__(256) k_fin_b(const float* __restrict__ Zp, int nparts, int Spad,
                                                int ldy, int L, int K, int l, int t_per,
                                                float* __restrict__ bpart) {
+  constexpr int MPT = 4;  // pixels per thread per pass; the (lag, slice) arithmetic is shared
   const int r = blockIdx.x, ts = blockIdx.y;
   const int r1 = r / K, r2 = r % K, l2 = l * l;
   const int t0 = ts * t_per, t1 = min(l2, t0 + t_per);
   const int total = (t1 - t0) * nparts;  // (lag, slice) pairs of this range
-  for (int m = threadIdx.x; m < l2; m += 256) {
-    const int m1 = m / l, m2 = m % l;
-    float acc = 0.f, comp = 0.f;
-    for (int j0 = 0; j0 < total; j0 += 8) {
-      float v[8];
+  for (int mb = threadIdx.x; mb < l2; mb += 256 * MPT) {
+    int m1[MPT], m2[MPT];
+    float acc[MPT], comp[MPT];
 #pragma unroll
-      for (int q = 0; q < 8; ++q) {  // eight independent loads, then the sums in order
-        const int j = j0 + q;
-        v[q] = 0.f;
-        if (j < total) {
-          const int t = t0 + j / nparts, p = j % nparts;
-          const int tt1 = t / l, tt2 = t % l;
-          int a1 = m1 + tt1, a2 = m2 + tt2;
-          a1 -= (a1 >= l) ? l : 0;
-          a2 -= (a2 >= l) ? l : 0;
-          const int s = mod_pos(tt1 * K - r1, L) * L + mod_pos(tt2 * K - r2, L);
-          v[q] = Zp[((int64_t)p * Spad + s) * ldy + a1 * l + a2];
-        }
+    for (int k = 0; k < MPT; ++k) {
+      const int m = mb + 256 * k;
+      m1[k] = m < l2 ? m / l : 0;
+      m2[k] = m < l2 ? m % l : 0;
+      acc[k] = comp[k] = 0.f;
+    }
+    for (int j = 0; j < total; ++j) {
+      const int t = t0 + j / nparts, p = j % nparts;
+      const int tt1 = t / l, tt2 = t % l;
+      const int s = mod_pos(tt1 * K - r1, L) * L + mod_pos(tt2 * K - r2, L);
+      const float* row = Zp + ((int64_t)p * Spad + s) * ldy;
+      float v[MPT];
+#pragma unroll
+      for (int k = 0; k < MPT; ++k) {  // independent loads, then the sums in order
+        int a1 = m1[k] + tt1, a2 = m2[k] + tt2;
+        a1 -= (a1 >= l) ? l : 0;
+        a2 -= (a2 >= l) ? l : 0;
+        v[k] = (mb + 256 * k < l2) ? row[a1 * l + a2] : 0.f;
       }
 #pragma unroll
-      for (int q = 0; q < 8; ++q) {
-        const float y = v[q] - comp;
-        const float tsum = acc + y;
-        comp = (tsum - acc) - y;
-        acc = tsum;
+      for (int k = 0; k < MPT; ++k) {
+        const float y = v[k] - comp[k];
+        const float tsum = acc[k] + y;
+        comp[k] = (tsum - acc[k]) - y;
+        acc[k] = tsum;
       }
     }
-    bpart[((int64_t)ts * K * K + r) * l2 + m] = acc;
+#pragma unroll
+    for (int k = 0; k < MPT; ++k) {
+      const int m = mb + 256 * k;
+      if (m < l2) bpart[((int64_t)ts * K * K + r) * l2 + m] = acc[k];
+    }
   }
 }
 
