@@ -125,21 +125,38 @@ __global__ void k_columns(const double* __restrict__ sub, const double* __restri
 }
 
 // Centred templates, pixel-major: AxT[n][s] = x'_r(s)[n - t(s)] (zero for padding).
+// Shift s = (s1, s2) has phase r = (-s1 mod K, -s2 mod K) and low-resolution lag
+// t = ((s1 + r1) / K mod l, (s2 + r2) / K mod l); each thread holds one shift and walks
+// the pixels n2 of row n1 = blockIdx.y (blockIdx.y = l writes the padding rows), so the
+// index arithmetic is per shift, and the subtraction of the sub-image mean is float32
+// (a rounding of the mean common to all pixels of a sub-image cancels in <y', T'>,
+// since every y' sums to zero).
 __global__ void k_templates_T(const float* __restrict__ x, const double* __restrict__ sub,
-                              int L, int K, int l, int S, int Spad, int l2,
+                              int L, int K, int l, int S, int Spad, int l2, int ldy,
                               float* __restrict__ AxT) {
   const int s = blockIdx.x * blockDim.x + threadIdx.x;
-  const int n = blockIdx.y;
+  const int n1 = blockIdx.y;
   if (s >= Spad) return;
-  float v = 0.f;
-  if (s < S && n < l2) {
-    const int s1 = s / L, s2 = s % L;
-    const int r1 = mod_pos(-s1, K), r2 = mod_pos(-s2, K);
-    const int t1 = ((s1 + r1) / K) % l, t2 = ((s2 + r2) / K) % l;
-    const int m1 = mod_pos(n / l - t1, l), m2 = mod_pos(n % l - t2, l);
-    v = (float)((double)x[(r1 + m1 * K) * L + r2 + m2 * K] - sub[r1 * K + r2]);
+  if (n1 == l) {  // padding rows
+    for (int n = l2; n < ldy; ++n) AxT[(int64_t)n * Spad + s] = 0.f;
+    return;
   }
-  AxT[(int64_t)n * Spad + s] = v;
+  float* out = AxT + (int64_t)n1 * l * Spad + s;
+  if (s >= S) {
+    for (int n2 = 0; n2 < l; ++n2) out[(int64_t)n2 * Spad] = 0.f;
+    return;
+  }
+  const int s1 = s / L, s2 = s % L;
+  const int r1 = mod_pos(-s1, K), r2 = mod_pos(-s2, K);
+  const int t1 = ((s1 + r1) / K) % l, t2 = ((s2 + r2) / K) % l;
+  const int m1 = mod_pos(n1 - t1, l);
+  const float mr = (float)sub[r1 * K + r2];
+  const float* row = x + (r1 + m1 * K) * L + r2;
+  int m2 = mod_pos(-t2, l);
+  for (int n2 = 0; n2 < l; ++n2) {
+    out[(int64_t)n2 * Spad] = row[m2 * K] - mr;
+    if (++m2 == l) m2 = 0;
+  }
 }
 
 // Combine the per-group (max, sum) partials of pass 1 into lse2[i] (base 2, of the
@@ -485,9 +502,9 @@ void launch_prep_iter(srmra_ctx* c) {
       c->colm);
   c->launches += 2;
   if (c->AxT) {
-    dim3 grid((unsigned)ceil_div(g.Spad, 256), (unsigned)g.ldy);
+    dim3 grid((unsigned)ceil_div(g.Spad, 256), (unsigned)(g.l + 1));
     k_templates_T<<<grid, 256, 0, c->stream>>>(c->x, c->sub, g.L, g.K, g.l, g.S, g.Spad,
-                                                g.l2, c->AxT);
+                                                g.l2, g.ldy, c->AxT);
     c->launches++;
   } else if (c->prec == SRMRA_FFT32) {
     launch_templates_fft(c);
@@ -561,10 +578,12 @@ __global__ void k_pack_stats(const double* __restrict__ cfin, const float* __res
     for (int t = 0; t < n_ts; ++t) b += (double)bpart[(int64_t)t * S + j];
     out[2 * S + j] = b;
   }
-  if (j == 0) {
+  if (blockIdx.x == 0 && threadIdx.x < 32) {  // the same reduction tree as k_fin_counts
+    const int lane = threadIdx.x;
     double ll = 0.0;
-    for (int k = 0; k < ll_blocks; ++k) ll += llpart[k];
-    out[3 * S] = ll;
+    for (int k = lane; k < ll_blocks; k += 32) ll += llpart[k];
+    ll = warp_sum_f64(ll);
+    if (lane == 0) out[3 * S] = ll;
   }
 }
 

@@ -1150,25 +1150,44 @@ __device__ __forceinline__ int mod_pos(int a, int m) {
   return r < 0 ? r + m : r;
 }
 
-// Centred templates, shift-major bf16 hi / lo: T[s][n] = x'_r(s)[n - t(s)].
-__global__ void k_templates_bf16(const float* __restrict__ x, const double* __restrict__ sub,
-                                 int L, int K, int l, int S, int Spad, int l2, int ldk,
-                                 __nv_bfloat16* __restrict__ Ah,
-                                 __nv_bfloat16* __restrict__ Al) {
-  const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (idx >= (int64_t)Spad * ldk) return;
-  const int s = (int)(idx / ldk), n = (int)(idx % ldk);
-  float v = 0.f;
-  if (s < S && n < l2) {
-    const int s1 = s / L, s2 = s % L;
-    const int r1 = mod_pos(-s1, K), r2 = mod_pos(-s2, K);
-    const int t1 = ((s1 + r1) / K) % l, t2 = ((s2 + r2) / K) % l;
-    const int m1 = mod_pos(n / l - t1, l), m2 = mod_pos(n % l - t2, l);
-    v = (float)((double)x[(r1 + m1 * K) * L + r2 + m2 * K] - sub[r1 * K + r2]);
+// Centred templates, shift-major bf16 hi / lo: T[s][n] = x'_r(s)[n - t(s)], zero for
+// padding.  One warp per shift: the phase, lag and sub-image mean are per shift, the
+// lanes walk the pixels n2 of each row n1; the subtraction of the mean is float32 (a
+// rounding of the mean common to a sub-image cancels in <y', T'>, every y' sums to zero).
+__global__ void __launch_bounds__(256) k_templates_bf16(
+    const float* __restrict__ x, const double* __restrict__ sub, int L, int K, int l, int S,
+    int Spad, int l2, int ldk, __nv_bfloat16* __restrict__ Ah, __nv_bfloat16* __restrict__ Al) {
+  const int s = blockIdx.x * 8 + (threadIdx.x >> 5), lane = threadIdx.x & 31;
+  if (s >= Spad) return;
+  __nv_bfloat16* rh = Ah + (int64_t)s * ldk;
+  __nv_bfloat16* rl = Al ? Al + (int64_t)s * ldk : nullptr;
+  const __nv_bfloat16 zero = __float2bfloat16_rn(0.f);
+  if (s >= S) {
+    for (int n = lane; n < ldk; n += 32) {
+      rh[n] = zero;
+      if (rl) rl[n] = zero;
+    }
+    return;
   }
-  const __nv_bfloat16 h = __float2bfloat16_rn(v);
-  Ah[idx] = h;
-  if (Al) Al[idx] = __float2bfloat16_rn(v - __bfloat162float(h));
+  const int s1 = s / L, s2 = s % L;
+  const int r1 = mod_pos(-s1, K), r2 = mod_pos(-s2, K);
+  const int t1 = ((s1 + r1) / K) % l, t2 = ((s2 + r2) / K) % l;
+  const float mr = (float)sub[r1 * K + r2];
+  for (int n1 = 0; n1 < l; ++n1) {
+    const float* row = x + (r1 + mod_pos(n1 - t1, l) * K) * L + r2;
+    for (int n2 = lane; n2 < l; n2 += 32) {
+      int m2 = n2 - t2;
+      m2 += m2 < 0 ? l : 0;
+      const float v = row[m2 * K] - mr;
+      const __nv_bfloat16 h = __float2bfloat16_rn(v);
+      rh[n1 * l + n2] = h;
+      if (rl) rl[n1 * l + n2] = __float2bfloat16_rn(v - __bfloat162float(h));
+    }
+  }
+  for (int n = l2 + lane; n < ldk; n += 32) {
+    rh[n] = zero;
+    if (rl) rl[n] = zero;
+  }
 }
 
 PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
@@ -1332,8 +1351,7 @@ cudaError_t prep_obs_tc(srmra_ctx* c) {
 
 void launch_templates_tc(srmra_ctx* c) {
   const Geom& g = c->g;
-  const int64_t n = (int64_t)g.Spad * g.ldk;
-  k_templates_bf16<<<(unsigned)ceil_div(n, 256), 256, 0, c->stream>>>(
+  k_templates_bf16<<<(unsigned)ceil_div(g.Spad, 8), 256, 0, c->stream>>>(
       c->x, c->sub, g.L, g.K, g.l, g.S, g.Spad, g.l2, g.ldk, c->Ah,
       c->prec == SRMRA_BF16X3 ? c->Al : nullptr);
   c->launches++;
