@@ -714,7 +714,10 @@ srmra_status check_status(srmra_mom* m) {
   MCK(m, cudaMemcpyAsync(&status, m->status, sizeof(int), cudaMemcpyDeviceToHost,
                          m->ctx->stream));
   MCK(m, cudaStreamSynchronize(m->ctx->stream));
-  if (status & STATUS_NUMERIC) return mfail(m, SRMRA_ENUMERIC, "NaN or Inf in the objective");
+  if (status) {  // reported once, then cleared (as for a context's status word)
+    MCK(m, cudaMemsetAsync(m->status, 0, sizeof(int), m->ctx->stream));
+    if (status & STATUS_NUMERIC) return mfail(m, SRMRA_ENUMERIC, "NaN or Inf in the objective");
+  }
   return SRMRA_OK;
 }
 

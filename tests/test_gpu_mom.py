@@ -209,3 +209,21 @@ def test_argument_errors(S):
     assert m.run(0, 0, 1e-3, 1e-3).size == 0
     m.close()
     s.close()
+
+
+def test_non_finite_objective_is_reported_once(S):
+    """An estimate whose moments overflow float32 gives ENUMERIC; the status is cleared
+    after the report, so the next evaluation at a finite estimate succeeds."""
+    p = problem(16, 2, 200, 0.5)
+    s = P.make_solver(S, p)
+    m = S.Mom(s)
+    x, r1, r2, sbm, t = s.state()
+    s.set_state(np.full_like(x, 1e30), r1, r2, sbm, t)
+    with pytest.raises(S.SrmraError) as e:
+        m.eval()
+    assert e.value.status == S.SRMRA_ENUMERIC
+    s.set_state(x, r1, r2, sbm, t)
+    f, gx, _, _ = m.eval()
+    assert np.isfinite(f) and np.all(np.isfinite(gx))
+    m.close()
+    s.close()
