@@ -173,11 +173,13 @@ __global__ void __launch_bounds__(256) k_lse_combine(
   if (i < N) {
     float m = -INFINITY;
     for (int gI = 0; gI < groups; ++gI) m = fmaxf(m, pm[gI * Npad + i]);
+    // the group scale factors 2^(mg - m) lie in (0, 1]: float32 exp2 (float64
+    // transcendentals are slow on this GPU), sums in float64
     double s = 0.0;
     if (m != -INFINITY)
       for (int gI = 0; gI < groups; ++gI) {
         const float mg = pm[gI * Npad + i];
-        if (mg != -INFINITY) s += (double)ps[gI * Npad + i] * exp2((double)mg - (double)m);
+        if (mg != -INFINITY) s += (double)ps[gI * Npad + i] * (double)exp2f(mg - m);
       }
     const double l2v = (double)m + log2(s);
     lse2[i] = (float)l2v;
@@ -325,25 +327,27 @@ __global__ void __launch_bounds__(256) k_fin_b(const float* __restrict__ Zp, int
 // x_{t+1}[q] = (b'[q] + ZB_r) / A_r with b'[q] the fixed-order float64 sum of the
 // lag-range partials (Eq. x_EM); a pixel with A_r = 0 keeps its value (uncovered pixel).
 // One thread per (sub-image r, low-resolution pixel m): the partials are read coalesced.
-__global__ void k_fin_x(const float* __restrict__ bpart, int n_ts, int L, int K, int l,
-                        const double* __restrict__ Ar, float* __restrict__ x,
-                        int* __restrict__ status) {
+// x = b / A per pixel q = r + m K of sub-image r (pixels with A = 0 keep their value):
+// eight threads per pixel sum the t-range partials of b' (thread g takes partials g,
+// g + 8, ...), then combine them with a fixed butterfly.
+__global__ void __launch_bounds__(256) k_fin_x(const float* __restrict__ bpart, int n_ts, int L,
+                                               int K, int l, const double* __restrict__ Ar,
+                                               float* __restrict__ x, int* __restrict__ status) {
   const int l2 = l * l;
-  const int idx = blockIdx.x * blockDim.x + threadIdx.x;  // r * l2 + m
-  if (idx >= K * K * l2) return;
-  const int r = idx / l2, m = idx % l2;
-  double b[4] = {0.0, 0.0, 0.0, 0.0};
-  int ts = 0;
-  for (; ts + 4 <= n_ts; ts += 4) {
+  const int gid = blockIdx.x * blockDim.x + threadIdx.x;
+  const int idx = gid >> 3, g = gid & 7;  // idx = r * l2 + m
+  const bool valid = idx < K * K * l2;
+  double b = 0.0;
+  if (valid)
+    for (int ts = g; ts < n_ts; ts += 8) b += (double)bpart[(int64_t)ts * K * K * l2 + idx];
 #pragma unroll
-    for (int k = 0; k < 4; ++k) b[k] += (double)bpart[(int64_t)(ts + k) * K * K * l2 + idx];
-  }
-  for (; ts < n_ts; ++ts) b[0] += (double)bpart[(int64_t)ts * K * K * l2 + idx];
-  const double bsum = (b[0] + b[1]) + (b[2] + b[3]);
+  for (int o = 1; o < 8; o <<= 1) b += __shfl_xor_sync(0xffffffffu, b, o);
+  if (!valid || g != 0) return;
+  const int r = idx / l2, m = idx % l2;
   const int q = ((r / K) + (m / l) * K) * L + (r % K) + (m % l) * K;
   const double A = Ar[r];
   if (A > 0.0) {
-    const double v = (bsum + Ar[K * K + r]) / A;
+    const double v = (b + Ar[K * K + r]) / A;
     x[q] = (float)v;
     if (!isfinite(v)) atomicOr(status, STATUS_NUMERIC);
   }
@@ -552,8 +556,8 @@ void launch_mstep(srmra_ctx* c, const double* cfin, const float* bpart, int n_ts
   const Geom& g = c->g;
   k_fin_counts<<<(unsigned)(g.K * g.K + 1), 1024, 0, stream>>>(
       cfin, g.Spad, g.S, g.L, g.K, g.l, llpart, ll_blocks, rho1, rho2, Ar, ll_out, status);
-  k_fin_x<<<(unsigned)ceil_div(g.S, 256), 256, 0, stream>>>(bpart, n_ts, g.L, g.K, g.l, Ar,
-                                                            x, status);
+  k_fin_x<<<(unsigned)ceil_div(8 * (int64_t)g.S, 256), 256, 0, stream>>>(bpart, n_ts, g.L, g.K,
+                                                                         g.l, Ar, x, status);
   c->launches += 2;
 }
 
