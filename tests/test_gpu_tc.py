@@ -141,3 +141,23 @@ def test_cluster_and_per_chunk_pass2_agree(S, L, K, N, sigma):
     # the two agree to float32 rounding, well inside the mixed form's 1e-4 target
     assert rel(out[0][0], out[1][0]) < 1e-5
     assert rel(out[0][1], out[1][1]) < 1e-5 and rel(out[0][2], out[1][2]) < 1e-5
+
+
+def test_largest_request_full_size(S):
+    """The largest problem of the serving mix at full size (L = 128, K = 2: l^2 = 4096,
+    sixteen pixel chunks, clusters of up to 8; N = 1e5): one bf16x3 iteration element-wise
+    against the FFT oracle (pinned to the dense oracle), x, rho and every lse_i."""
+    p = synth.workload_problem("largest_request_L128_K2_N1e5")
+    s = S.Solver(p.L, p.K, p.sigma, p.y, prec="bf16x3", x0=p.x0, rho1=p.rho1_0,
+                 rho2=p.rho2_0)
+    ll = s.em_iter(1)[0]
+    lse, _ = s.estep()
+    x, r1, r2, _, _ = s.state()
+    s.close()
+    xo, r1o, r2o, llo, aux = FO.em_iter_fft(p.y, p.x0, p.rho1_0, p.rho2_0, p.sigma, p.K)
+    yscale = (p.y.astype(np.float64) ** 2).sum(axis=(1, 2)) / (2 * p.sigma ** 2)
+    tol = TOL["bf16x3"]
+    assert rel(x, xo) < tol, rel(x, xo)
+    assert rel(r1, r1o) < tol and rel(r2, r2o) < tol
+    assert np.max(np.abs(lse - aux["lse"]) / (1.0 + np.abs(aux["lse"]) + yscale)) < tol
+    assert abs(ll - llo) / (abs(llo) + yscale.sum()) < tol
