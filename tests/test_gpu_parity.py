@@ -133,6 +133,26 @@ def test_zero_rho_entries(S):
     s.close()
 
 
+@pytest.mark.parametrize("prec", ["fp32", "bf16x3", "fft32"])
+def test_pixels_without_coverage_keep_their_value(S, prec):
+    """With zero prior weight on every even first-axis shift, the sub-images of phase
+    r1 = 0 get no coverage (A = 0): their pixels keep the previous value exactly
+    (reading R6) and the others follow the oracle."""
+    p = synth.make_problem(32, 2, 300, 0.4, seed=43)
+    r1 = np.array(p.rho1_true)
+    r1[0::2] = 0.0
+    r1 /= r1.sum()
+    s = S.Solver(p.L, p.K, p.sigma, p.y, prec=prec, x0=p.x0, rho1=r1, rho2=p.rho2_0)
+    s.em_iter(1)
+    x, g1, _, _, _ = s.state()
+    s.close()
+    xo, r1o, _, _, aux = O.em_iter(p.y, p.x0, r1, p.rho2_0, p.sigma, p.K)
+    assert np.all(aux["A"][0::2] == 0.0) and np.all(aux["A"][1::2] > 0.0)
+    assert np.array_equal(x[0::2], p.x0[0::2])  # first-axis pixels q1 = 0 mod 2
+    tol = {"fp32": 1e-5, "fft32": 1e-5, "bf16x3": 1e-4}[prec]
+    assert rel(x[1::2], xo[1::2]) < tol and rel(g1, r1o) < tol
+
+
 def test_full_plain_em_run_fp32(S):
     """20 plain EM iterations at L=16, K=2, N=500, sigma=0.1 from the same start:
     x, rho after the run and the LL trajectory match the oracle; LL never decreases.
