@@ -28,7 +28,8 @@ def rel(a, b):
 
 
 SPECS = [(32, 2, 1500, 0.3), (48, 4, 900, 0.6), (64, 2, 700, 0.2), (32, 4, 2000, 1.0),
-         (16, 2, 300, 0.1)]
+         (16, 2, 300, 0.1),
+         (96, 2, 400, 0.5)]  # l^2 = 2304: nine pixel chunks, clusters of more than 4
 
 
 def problems():
