@@ -16,8 +16,9 @@ the bench's CPU leg only; shares no code with the CUDA path).
         df/dx     = sum_s rho_s (P R_s)^T (4 R t_s + 2 lambda r),
     and for the product form df/drho1[a] = sum_b df/drho_(a,b) rho2[b], likewise rho2.
   * Algorithm 1 with the reading
-    R14 "F BFGS (or alternative gradient-based algorithm) steps" is taken as F steps of
-        the fixed-step gradient iteration the paper analyses (Sec. 4, Eq. (pgm)):
+    R14 the inner minimiser of Algorithm 1 (F quasi-Newton iterations per outer step, for
+        which the paper allows any gradient method) is taken as F steps of the fixed-step
+        gradient iteration the paper analyses (Sec. 4, Eq. (pgm)):
         x <- x - mu_x df/dx; rho1, rho2 <- their Euclidean projections onto the
         probability simplex after a step mu_rho of their gradients; then
         x <- D(x, sigma_BM) and sigma_BM <- 2^(-1/10) sigma_BM (Eq. decaying_function).
