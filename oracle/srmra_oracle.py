@@ -35,7 +35,8 @@ Readings where the paper is silent or ambiguous:
       DCT-II, the DC coefficient always kept, an AC coefficient kept iff
       |c| > 2.7 * sigma_BM (ties are zeroed), no clipping.
   R10 the projection runs after the M-step of every F-th iteration; F = 0 means none.
-  R11 a fixed iteration count replaces "until a stopping criterion is met".
+  R11 the loops of Algorithms 1 and 2 run for a fixed number of iterations (the paper
+      leaves the stopping rule open).
   R13 online EM (the online strategy the paper suggests for large N, Sec. 6, without an
       algorithm): mini-batch EM with stochastic-approximation sufficient statistics.
       The statistics of Eqs. (x_EM) and (rho_EM) are the per-shift sums
