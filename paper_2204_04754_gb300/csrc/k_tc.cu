@@ -660,7 +660,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
 }
 
 // ------------------------------------------------------------------------------ pass 2,
-// cluster form.  A cluster of G CTAs (G = 2..8) shares one 128-shift tile and one range
+// cluster form.  A cluster of G CTAs (G = 2..16) shares one 128-shift tile and one range
 // of observation blocks; CTA `rank` owns pixel chunk cg*G + rank of Z'.  In each round
 // every CTA computes the logits of ITS OWN 128-observation block (no CTA recomputes
 // another's), turns them into the fp16 weight tile, and the tile reaches the other CTAs
@@ -671,7 +671,10 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
 // of the round.  The weights of one (shift tile, observation block) are thus computed
 // once instead of once per pixel chunk.
 constexpr int P2C_SLOTS = 7;
-constexpr int P2C_MAX_G = 8;  // largest cluster (the portable limit); mailbox row width
+// largest cluster, and the mailbox row width; clusters above 8 CTAs (the portable limit)
+// need the non-portable cluster-size attribute and fit only where a GPC has 16 free SMs
+constexpr int P2C_MAX_G = 16;
+constexpr int P2C_PORTABLE_G = 8;
 // Mailbox rows, one per use: a producer leads a peer's epilogue by at most one row per ring
 // slot it holds for that peer (the slot is freed only after the peer has read the row and
 // sent its tile), so more rows than ring slots keep a row from being reused before it is
@@ -680,10 +683,11 @@ constexpr int P2C_MAX_G = 8;  // largest cluster (the portable limit); mailbox r
 constexpr int MBOX_DEPTH = 8;
 static_assert(MBOX_DEPTH > P2C_SLOTS, "a mailbox row could be reused before it is read");
 // barriers: full, empty (ring), sfull, sempty, zfull, zempty, mfull (rows), drain, wready;
-// then the mailbox, the TMEM address and the abort flag, in 512 bytes after the ring
+// then the mailbox, the TMEM address and the abort flag, in P2C_BOOK bytes after the ring
+constexpr int P2C_BOOK = 768;
 static_assert((2 * P2C_SLOTS + 2 + 2 + 1 + 1 + MBOX_DEPTH + 1 + 1) * 8 +
-                      MBOX_DEPTH * P2C_MAX_G * 4 + 4 + 4 <= 512,
-              "cluster pass-2 bookkeeping exceeds its 512 bytes");
+                      MBOX_DEPTH * P2C_MAX_G * 4 + 4 + 4 <= P2C_BOOK,
+              "cluster pass-2 bookkeeping exceeds its P2C_BOOK bytes");
 
 template <int NPROD>
 __global__ void __launch_bounds__(TC_THREADS, 1)
@@ -955,7 +959,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     const int q = warp & 3;
     const int row = q * 32 + lane;
     const uint32_t lane_addr = tbase + ((uint32_t)(q * 32) << 16);
-    float2* wobs = (float2*)(smem + P2C_SLOTS * SLOT + 512) + q * 32;  // this warp's staging
+    float2* wobs = (float2*)(smem + P2C_SLOTS * SLOT + P2C_BOOK) + q * 32;  // warp's staging
     uint32_t sc = 0, mr = 0, uc = 0;
     bool ok = true;
     for (int64_t u = cid; ok && u < total; u += ncl) {
@@ -1101,10 +1105,10 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
   cluster_sync_all();  // no CTA leaves while a peer may still copy into it
 }
 
-// ring + bookkeeping (30 mbarriers, 8 x 8 mailbox, TMEM address, abort flag: 504 of the
-// 512 bytes) +
+// ring + bookkeeping (30 mbarriers, 8 x 16 mailbox, TMEM address, abort flag: 760 of the
+// 768 bytes) +
 // per-warp staging of one 32-observation chunk's (ybar, lse2) (4 x 256 bytes)
-constexpr size_t P2C_SMEM = 1024 + P2C_SLOTS * SLOT + 512 + 1024;
+constexpr size_t P2C_SMEM = 1024 + P2C_SLOTS * SLOT + P2C_BOOK + 1024;
 static_assert(P2C_SMEM <= 232448, "exceeds the shared memory of one CTA");
 
 constexpr size_t P1_SMEM = 1024 + P1_SLOTS * SLOT + 256 + 1024;
@@ -1225,9 +1229,18 @@ cudaError_t set_smem(K kernel, size_t bytes) {
   return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
 }
 
+// the clustered pass-2 kernel: its shared memory, and clusters above the portable size
+template <int NPROD>
+cudaError_t set_p2c_attrs() {
+  cudaError_t e = set_smem(k_p2c_tc<NPROD>, P2C_SMEM);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_p2c_tc<NPROD>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+  return e;
+}
+
 }  // namespace
 
-int choose_p2_cluster(int chunks, int prec, int num_sms);
+int choose_p2_cluster(int chunks, int l2, int64_t n_iblk, int prec, int num_sms);
 template <int NPROD>
 int max_clusters_p2(int G, int num_sms);
 
@@ -1267,7 +1280,7 @@ void plan_tc(srmra_ctx* c, int s1, int s2) {
   const int chunks = (int)ceil_div(g.l2, 256);
   const int n_iblk = (int)(g.Npad / 128);
   // cluster size of pass 2: CTAs that share each weight tile, one pixel chunk each
-  const int G = c->no_cluster ? 1 : choose_p2_cluster(chunks, c->prec, sms);
+  const int G = c->no_cluster ? 1 : choose_p2_cluster(chunks, g.l2, n_iblk, c->prec, sms);
   // observation splits of pass 2: each split adds a partial Z' (Spad x l2 float32) that
   // pass 2 writes and the finalize reads, so take the split count that minimises the
   // busiest cluster's block-rounds plus the partials' cost in the same units (a partial
@@ -1316,11 +1329,11 @@ cudaError_t tc_set_attributes(int prec) {
   if (prec == SRMRA_BF16X3) {
     e = set_smem(k_p1_tc<3>, P1_SMEM);
     if (e == cudaSuccess) e = set_smem(k_p2_tc<3>, P2_SMEM);
-    if (e == cudaSuccess) e = set_smem(k_p2c_tc<3>, P2C_SMEM);
+    if (e == cudaSuccess) e = set_p2c_attrs<3>();
   } else {
     e = set_smem(k_p1_tc<1>, P1_SMEM);
     if (e == cudaSuccess) e = set_smem(k_p2_tc<1>, P2_SMEM);
-    if (e == cudaSuccess) e = set_smem(k_p2c_tc<1>, P2C_SMEM);
+    if (e == cudaSuccess) e = set_p2c_attrs<1>();
   }
   return e;
 }
@@ -1412,13 +1425,14 @@ void fill_inst(const srmra_ctx* c, TcInst* I) {
   b.status = c->status;
 }
 
-// Co-resident clusters of G CTAs of the clustered pass-2 kernel (queried once per G).
+// Co-resident clusters of G CTAs of the clustered pass-2 kernel (queried once per G); 0
+// for a cluster size above the portable limit that the GPU cannot place.
 template <int NPROD>
 int max_clusters(int G, int num_sms) {
   static int cache[P2C_MAX_G + 1] = {};
-  if (cache[G] > 0) return cache[G];
+  if (cache[G] != 0) return cache[G] > 0 ? cache[G] : 0;
   cudaGetLastError();
-  set_smem(k_p2c_tc<NPROD>, P2C_SMEM);
+  set_p2c_attrs<NPROD>();
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3((unsigned)(G * (num_sms / G)), 1, 1);
   cfg.blockDim = dim3(TC_THREADS, 1, 1);
@@ -1433,6 +1447,10 @@ int max_clusters(int G, int num_sms) {
   int n = 0;
   if (cudaOccupancyMaxActiveClusters(&n, k_p2c_tc<NPROD>, &cfg) != cudaSuccess || n < 1) {
     cudaGetLastError();
+    if (G > P2C_PORTABLE_G) {
+      cache[G] = -1;
+      return 0;
+    }
     n = num_sms / G / 2 > 0 ? num_sms / G / 2 : 1;
   }
   cache[G] = n;
@@ -1444,11 +1462,12 @@ cudaError_t launch_cluster_p2(int G, const TcInst* d_insts, const int64_t* d_ust
                               int64_t total, int* status, cudaStream_t stream, int num_sms) {
   static bool attr = false;
   if (!attr) {
-    cudaError_t e = set_smem(k_p2c_tc<NPROD>, P2C_SMEM);
+    cudaError_t e = set_p2c_attrs<NPROD>();
     if (e != cudaSuccess) return e;
     attr = true;
   }
   int ncl = max_clusters<NPROD>(G, num_sms);
+  if (ncl < 1) return cudaErrorInvalidConfiguration;  // chosen only where it can be placed
   if (total < ncl) ncl = (int)total;
   if (ncl < 1) return cudaSuccess;
   cudaLaunchConfig_t cfg = {};
@@ -1500,22 +1519,32 @@ int max_clusters_p2(int G, int num_sms) {
 template int max_clusters_p2<1>(int, int);
 template int max_clusters_p2<3>(int, int);
 
-// Cluster size of pass 2 for `chunks` 256-pixel chunks of Z'.  Up to 4 chunks one cluster
-// covers them all (G = chunks).  Beyond, the weights of a (shift tile, observation block)
-// are computed once per group of G chunks, so G trades recompute against how many
-// clusters of G co-reside (GPC packing): the G in 2..8 (and <= chunks) that minimises the
-// executed work per co-resident CTA, (NPROD groups + 1) / (G clusters(G)) with
-// groups = ceil(chunks / G) (NPROD logit products, one Z' product per pair and pixel).
-int choose_p2_cluster(int chunks, int prec, int num_sms) {
+// Cluster size of pass 2 for `chunks` 256-pixel chunks of Z' (l2 pixels, n_iblk blocks of
+// 128 observations).  Up to 4 chunks one cluster covers them all (G = chunks).  Beyond,
+// the weights of a (shift tile, observation block) are computed once per group of G
+// chunks, and G trades that recompute against the cost of a round and how many clusters
+// of G co-reside (GPC packing).  A cluster round takes about a * NPROD * l2 (the logits
+// of the CTA's own block) + b * G (one weight tile handed over per member), a = 2.24 ns
+// and b = 5.2 us, fitted to measured pass-2 times of 11 shapes (L = 72..128, K = 2,
+// G = 3..13, within 12% of the best size measured); the busiest cluster runs
+// groups * ceil(n_iblk / G) / clusters(G) rounds per shift tile.  Clusters of 16 (one per
+// GPC) measured 28-43% slower than this estimate, so sizes above 13 are not considered.
+constexpr int P2C_RULE_MAX_G = 13;
+static_assert(P2C_RULE_MAX_G <= P2C_MAX_G, "the rule may pick a size the kernel lacks");
+
+int choose_p2_cluster(int chunks, int l2, int64_t n_iblk, int prec, int num_sms) {
   if (chunks <= 1) return 1;
   if (chunks <= 4) return chunks;
   const int nprod = prec == SRMRA_BF16X3 ? 3 : 1;
+  constexpr double a_us = 2.24e-3, b_us = 5.2;
   int best = 4;
   double best_cost = 0.0;
-  for (int G = 2; G <= P2C_MAX_G && G <= chunks; ++G) {
-    const int groups = (chunks + G - 1) / G;
+  for (int G = 2; G <= P2C_RULE_MAX_G && G <= chunks; ++G) {
     const int ncl = nprod == 3 ? max_clusters<3>(G, num_sms) : max_clusters<1>(G, num_sms);
-    const double cost = (double)(nprod * groups + 1) / ((double)G * (double)ncl);
+    if (ncl < 1) continue;
+    const double groups = (double)((chunks + G - 1) / G);
+    const double rounds = groups * (double)((n_iblk + G - 1) / G) / (double)ncl;
+    const double cost = rounds * (a_us * nprod * l2 + b_us * G);
     if (best_cost == 0.0 || cost < best_cost) {
       best = G;
       best_cost = cost;

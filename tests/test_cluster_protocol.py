@@ -4,7 +4,7 @@ Each CTA of a cluster of G runs three roles: a producer that reserves slots of a
 7-deep shared-memory ring (TMA tiles, and slots into which the other CTAs send their
 weight tiles), an MMA issuer that consumes the ring in the same order, and an epilogue
 that turns the logits of its own observation block into a weight tile and sends it to
-the slots the other CTAs reserved for it (announced through a 4-row mailbox).  The
+the slots the other CTAs reserved for it (announced through an 8-row mailbox).  The
 model runs the roles as coroutines under random schedules, with the kernel's slot
 order, and reports a deadlock when no role can move.  It checks the order the kernel
 uses, and that the model does catch the order that deadlocks (all weight slots of a
@@ -181,7 +181,7 @@ def cvalid_patterns(G):
             [k < (G + 1) // 2 for k in range(G)]]
 
 
-@pytest.mark.parametrize("G", [2, 3, 4, 5, 6, 7, 8])
+@pytest.mark.parametrize("G", [2, 3, 4, 5, 6, 7, 8, 9, 12, 13, 16])
 def test_kernel_slot_order_never_deadlocks(G):
     for units in UNITS:
         for cvalid in cvalid_patterns(G):

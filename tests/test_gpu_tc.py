@@ -124,11 +124,14 @@ def test_precision_workload_full_size_sampled(S, name):
 
 
 @pytest.mark.parametrize("L,K,N,sigma", [(64, 2, 900, 0.3), (48, 1, 400, 0.8), (96, 4, 600, 0.5),
-                                         (128, 2, 500, 0.5), (112, 2, 300, 0.7)])
+                                         (128, 2, 500, 0.5), (112, 2, 300, 0.7),
+                                         (96, 2, 1000, 0.5), (128, 2, 1250, 0.6)])
 def test_cluster_and_per_chunk_pass2_agree(S, L, K, N, sigma):
     """The cluster form of pass 2 (weights computed once per observation block and
     shared through distributed shared memory) and the per-chunk form (weights
-    recomputed for every pixel chunk) give the same iteration."""
+    recomputed for every pixel chunk) give the same iteration.  The shapes take clusters
+    of 2 to 10 CTAs (L=96, K=2 with 1000 observations: 9, above the portable 8; L=128,
+    K=2 with 1250: 10, two chunk groups of 10 and 6)."""
     p = synth.make_problem(L, K, N, sigma, seed=synth.seed_for(3, 900 + L))
     out = []
     for flags in (0, 2):  # 2 = SRMRA_FLAG_NO_CLUSTER
@@ -145,7 +148,8 @@ def test_cluster_and_per_chunk_pass2_agree(S, L, K, N, sigma):
 
 def test_largest_request_full_size(S):
     """The largest problem of the serving mix at full size (L = 128, K = 2: l^2 = 4096,
-    sixteen pixel chunks, clusters of up to 8; N = 1e5): one bf16x3 iteration element-wise
+    sixteen pixel chunks in two groups of a 9-CTA cluster; N = 1e5): one bf16x3 iteration
+    element-wise
     against the FFT oracle (pinned to the dense oracle), x, rho and every lse_i."""
     p = synth.workload_problem("largest_request_L128_K2_N1e5")
     s = S.Solver(p.L, p.K, p.sigma, p.y, prec="bf16x3", x0=p.x0, rho1=p.rho1_0,
