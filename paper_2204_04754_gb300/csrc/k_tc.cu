@@ -660,34 +660,42 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
 }
 
 // ------------------------------------------------------------------------------ pass 2,
-// cluster form.  A cluster of G CTAs (G = 2..16) shares one 128-shift tile and one range
-// of observation blocks; CTA `rank` owns pixel chunk cg*G + rank of Z'.  In each round
-// every CTA computes the logits of ITS OWN 128-observation block (no CTA recomputes
-// another's), turns them into the fp16 weight tile, and the tile reaches the other CTAs
-// through distributed shared memory: each CTA's producer reserves a ring slot for every
-// peer's tile and mails the slot index to that peer; the peer writes its tile into its
-// own reserved slot and bulk-copies it into the slots the others reserved, completing
-// on their ring barriers.  Each CTA then accumulates Z'[s, its chunk] over the G blocks
+// cluster forms.  A cluster of G CTAs shares one 128-shift tile and one range of
+// observation blocks; CTA `rank` owns pixel chunk cg*G + rank of Z'.  In each round every
+// CTA computes the logits of ITS OWN 128-observation block (no CTA recomputes another's),
+// turns them into an fp16 weight tile, and the tile reaches the other CTAs through
+// distributed shared memory; each CTA then accumulates Z'[s, its chunk] over the blocks
 // of the round.  The weights of one (shift tile, observation block) are thus computed
-// once instead of once per pixel chunk.
-constexpr int P2C_SLOTS = 7;
-// largest cluster, and the mailbox row width; clusters above 8 CTAs (the portable limit)
-// need the non-portable cluster-size attribute and fit only where a GPC has 16 free SMs
+// once per group of G chunks instead of once per pixel chunk.  Two forms:
+// - ring form (G <= 4): every weight tile, the own one included, goes through the
+//   7-slot operand ring.  Each CTA's producer reserves a slot for every tile of the
+//   round and mails the slot index to the tile's owner; once all G reservations are in,
+//   the owner writes its tile into its own slot and bulk-copies it into the others'.
+// - staged form (G >= 5): the own tile is written to a staging slot beside a 6-slot ring,
+//   and a sender warp copies it to each peer as soon as that peer's reservation
+//   arrives, so that the CTAs no longer wait for the slowest reservation of each tile.
+// The deeper ring is worth more to small clusters (their logits dominate a round); the
+// per-peer hand-off to large ones (one weight tile per member per round).
+// largest cluster; clusters above 8 CTAs (the portable limit) need the non-portable
+// cluster-size attribute and fit only where a GPC has the free SMs
 constexpr int P2C_MAX_G = 16;
 constexpr int P2C_PORTABLE_G = 8;
-// Mailbox rows, one per use: a producer leads a peer's epilogue by at most one row per ring
-// slot it holds for that peer (the slot is freed only after the peer has read the row and
-// sent its tile), so more rows than ring slots keep a row from being reused before it is
-// read, whatever the cluster's chunk ownership (CTAs without a pixel chunk hold one slot
-// per single-block unit and can run up to P2C_SLOTS units ahead).
+constexpr int P2R_MAX_G = 4;  // ring form: clusters up to 4
+// Mailbox rows, one per use of a tile.  A producer can announce at most one use per ring
+// slot it holds for a peer (the slot is freed only after the peer has read the
+// announcement and sent its tile), so more rows than ring slots keep a row from being
+// reused before it is read, whatever the cluster's chunk ownership.
 constexpr int MBOX_DEPTH = 8;
-static_assert(MBOX_DEPTH > P2C_SLOTS, "a mailbox row could be reused before it is read");
+
+// ---- ring form
+constexpr int P2R_SLOTS = 7;
+static_assert(MBOX_DEPTH > P2R_SLOTS, "a mailbox row could be reused before it is read");
 // barriers: full, empty (ring), sfull, sempty, zfull, zempty, mfull (rows), drain, wready;
-// then the mailbox, the TMEM address and the abort flag, in P2C_BOOK bytes after the ring
-constexpr int P2C_BOOK = 768;
-static_assert((2 * P2C_SLOTS + 2 + 2 + 1 + 1 + MBOX_DEPTH + 1 + 1) * 8 +
-                      MBOX_DEPTH * P2C_MAX_G * 4 + 4 + 4 <= P2C_BOOK,
-              "cluster pass-2 bookkeeping exceeds its P2C_BOOK bytes");
+// then the mailbox, the TMEM address and the abort flag, in P2R_BOOK bytes after the ring
+constexpr int P2R_BOOK = 512;
+static_assert((2 * P2R_SLOTS + 2 + 2 + 1 + 1 + MBOX_DEPTH + 1 + 1) * 8 +
+                      MBOX_DEPTH * P2R_MAX_G * 4 + 4 + 4 <= P2R_BOOK,
+              "ring-form bookkeeping exceeds its P2R_BOOK bytes");
 
 template <int NPROD>
 __global__ void __launch_bounds__(TC_THREADS, 1)
@@ -695,24 +703,24 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
              int G, int* status) {
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = align1024(smem_raw);
-  uint64_t* full = (uint64_t*)(smem + P2C_SLOTS * SLOT);
-  uint64_t* empty = full + P2C_SLOTS;
-  uint64_t* sfull = empty + P2C_SLOTS;
+  uint64_t* full = (uint64_t*)(smem + P2R_SLOTS * SLOT);
+  uint64_t* empty = full + P2R_SLOTS;
+  uint64_t* sfull = empty + P2R_SLOTS;
   uint64_t* sempty = sfull + 2;
   uint64_t* zfull = sempty + 2;
   uint64_t* zempty = zfull + 1;
   uint64_t* mfull = zempty + 1;  // [MBOX_DEPTH]: one barrier per mailbox row
   uint64_t* drain = mfull + MBOX_DEPTH;
   uint64_t* wready = drain + 1;  // the 128 epilogue threads have written the weight tile
-  uint32_t* mbox = (uint32_t*)(wready + 1);  // [MBOX_DEPTH][P2C_MAX_G] reserved slots
-  uint32_t* tptr = mbox + MBOX_DEPTH * P2C_MAX_G;
+  uint32_t* mbox = (uint32_t*)(wready + 1);  // [MBOX_DEPTH][P2R_MAX_G] reserved slots
+  uint32_t* tptr = mbox + MBOX_DEPTH * P2R_MAX_G;
   volatile int* abort = (volatile int*)(tptr + 1);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const uint32_t rank = cluster_rank();
   const int64_t cid = blockIdx.x / G, ncl = gridDim.x / G;
 
   if (threadIdx.x == 0) {
-    for (int k = 0; k < P2C_SLOTS; ++k) {
+    for (int k = 0; k < P2R_SLOTS; ++k) {
       mbar_init(&full[k], 1);
       mbar_init(&empty[k], 1);
     }
@@ -741,11 +749,11 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
 
   if (warp == 0) {
     if (lane == 0) {
-      uint32_t it = 0, sent[P2C_MAX_G] = {};
+      uint32_t it = 0, sent[P2R_MAX_G] = {};
       bool ok = true;
       auto reserve = [&](bool expect_copy) -> int {
-        const int st = it % P2C_SLOTS;
-        if (!mbar_wait(&empty[st], ((it / P2C_SLOTS) & 1) ^ 1, abort)) {
+        const int st = it % P2R_SLOTS;
+        if (!mbar_wait(&empty[st], ((it / P2R_SLOTS) & 1) ^ 1, abort)) {
           ok = false;
           return -1;
         }
@@ -795,7 +803,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
           // the slots of round j - 1: the weight tile of block rp + kq (filled by CTA kq)
           // is reserved one block ahead of the two Y'^T tiles it multiplies, i.e. in the
           // order W0 W1 T0 T0 W2 T1 T1 W3 T2 T2 T3 T3.  Every Y'^T tile then lies within
-          // P2C_SLOTS - 1 places of its weight slot, so no fill waits for a slot that is
+          // P2R_SLOTS - 1 places of its weight slot, so no fill waits for a slot that is
           // only freed by the products that need that fill, while the tiles of the other
           // CTAs can still be sent early.
           const int rp = (j - 1) * G, nqp = j >= 1 ? min(G, nb - rp) : 0;
@@ -805,7 +813,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             // row sent % DEPTH of peer kq's mailbox, and that row's own barrier, so the
             // arrivals of different rounds can never complete each other's phases
             const uint32_t row = sent[kq] % MBOX_DEPTH;
-            st_cluster_u32(mapa(smem_u32(mbox + row * P2C_MAX_G + rank), kq), (uint32_t)st);
+            st_cluster_u32(mapa(smem_u32(mbox + row * P2R_MAX_G + rank), kq), (uint32_t)st);
             mbar_arrive_cluster(mapa(smem_u32(&mfull[row]), kq));
             ++sent[kq];
             ++it;
@@ -826,10 +834,10 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
       }
       if (!ok) {
         raise_timeout(abort, status);
-        const uint32_t lo = it > P2C_SLOTS ? it - P2C_SLOTS : 0;
+        const uint32_t lo = it > P2R_SLOTS ? it - P2R_SLOTS : 0;
         int zero = 0;
         for (uint32_t k = lo; k < it; ++k)
-          mbar_wait(&full[k % P2C_SLOTS], (k / P2C_SLOTS) & 1, (volatile int*)&zero);
+          mbar_wait(&full[k % P2R_SLOTS], (k / P2R_SLOTS) & 1, (volatile int*)&zero);
       }
     }
   } else if (warp == 1) {
@@ -839,8 +847,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
       uint32_t it = 0, sc = 0, uc = 0;
       bool ok = true;
       auto wait_slot = [&]() -> int {
-        const int st = it % P2C_SLOTS;
-        if (!mbar_wait(&full[st], (it / P2C_SLOTS) & 1, abort)) {
+        const int st = it % P2R_SLOTS;
+        if (!mbar_wait(&full[st], (it / P2R_SLOTS) & 1, abort)) {
           ok = false;
           return -1;
         }
@@ -905,7 +913,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
           }
           const int nqp = j >= 1 ? min(G, nb - (j - 1) * G) : 0;
           // same slot order as the producer: W0 W1 T0 T0 W2 T1 T1 W3 T2 T2 T3 T3
-          int stPs[P2C_MAX_G] = {};
+          int stPs[P2R_MAX_G] = {};
           if (nqp > 0) {
             stPs[0] = wait_slot();
             ++it;
@@ -959,7 +967,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     const int q = warp & 3;
     const int row = q * 32 + lane;
     const uint32_t lane_addr = tbase + ((uint32_t)(q * 32) << 16);
-    float2* wobs = (float2*)(smem + P2C_SLOTS * SLOT + P2C_BOOK) + q * 32;  // warp's staging
+    float2* wobs = (float2*)(smem + P2R_SLOTS * SLOT + P2R_BOOK) + q * 32;  // warp's staging
     uint32_t sc = 0, mr = 0, uc = 0;
     bool ok = true;
     for (int64_t u = cid; ok && u < total; u += ncl) {
@@ -1031,7 +1039,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         ok = __all_sync(0xffffffffu,
                         mbar_wait_cluster(&mfull[mr % MBOX_DEPTH], (mr / MBOX_DEPTH) & 1, abort));
         if (!ok) break;
-        const uint32_t* mrow = mbox + (mr % MBOX_DEPTH) * P2C_MAX_G;
+        const uint32_t* mrow = mbox + (mr % MBOX_DEPTH) * P2R_MAX_G;
         const int own = (int)mrow[rank];
         uint8_t* prow = smem + own * SLOT + row * 128;
 #pragma unroll
@@ -1105,11 +1113,519 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
   cluster_sync_all();  // no CTA leaves while a peer may still copy into it
 }
 
-// ring + bookkeeping (30 mbarriers, 8 x 16 mailbox, TMEM address, abort flag: 760 of the
-// 768 bytes) +
+// ring + bookkeeping (30 mbarriers, 8 x 4 mailbox, TMEM address, abort flag: 376 of the
+// 512 bytes) +
 // per-warp staging of one 32-observation chunk's (ybar, lse2) (4 x 256 bytes)
-constexpr size_t P2C_SMEM = 1024 + P2C_SLOTS * SLOT + P2C_BOOK + 1024;
-static_assert(P2C_SMEM <= 232448, "exceeds the shared memory of one CTA");
+constexpr size_t P2R_SMEM = 1024 + P2R_SLOTS * SLOT + P2R_BOOK + 1024;
+static_assert(P2R_SMEM <= 232448, "exceeds the shared memory of one CTA");
+
+// ---- staged form
+constexpr int P2S_SLOTS = 6;  // ring slots; the own weight tile has a staging slot besides
+constexpr int P2S_THREADS = 224;  // producer, MMA, 4 epilogue warps, sender
+static_assert(MBOX_DEPTH > P2S_SLOTS, "a mailbox row could be reused before it is read");
+constexpr uint32_t MBOX_TAG_MASK = 0x0FFFFFFFu;  // entry = tag << 4 | slot, tag = use + 1
+// barriers: full, empty (ring), sfull, sempty, zfull, zempty, wfull, wfree, cdone, drain;
+// then the mailbox (tagged entries, one row per use of this CTA's tile), the TMEM address
+// and the abort flag, in P2S_BOOK bytes
+constexpr int P2S_BOOK = 768;
+static_assert((2 * P2S_SLOTS + 2 + 2 + 1 + 1 + 1 + 1 + 1 + 1) * 8 +
+                      MBOX_DEPTH * P2C_MAX_G * 4 + 4 + 4 <= P2S_BOOK,
+              "staged-form bookkeeping exceeds its P2S_BOOK bytes");
+static_assert(P2S_SLOTS < 16, "a slot index must fit the mailbox entry's 4 bits");
+
+// The blocks of a round in this CTA's order: its own block first (rank < nq), then the
+// next ranks cyclically; a CTA without a block of the round starts at rank mod nq.
+__device__ __forceinline__ int p2c_block(int rank, int nq, int i) {
+  return (rank % nq + i) % nq;
+}
+
+template <int NPROD>
+__global__ void __launch_bounds__(P2S_THREADS, 1)
+    k_p2s_tc(const TcInst* __restrict__ insts, const int64_t* __restrict__ ustart, int n_inst,
+             int G, int* status) {
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* smem = align1024(smem_raw);
+  uint8_t* stage = smem + P2S_SLOTS * SLOT;  // this CTA's weight tile
+  uint64_t* full = (uint64_t*)(stage + SLOT);
+  uint64_t* empty = full + P2S_SLOTS;
+  uint64_t* sfull = empty + P2S_SLOTS;
+  uint64_t* sempty = sfull + 2;
+  uint64_t* zfull = sempty + 2;
+  uint64_t* zempty = zfull + 1;
+  uint64_t* wfull = zempty + 1;  // the 128 epilogue threads have written the staged tile
+  uint64_t* wfree = wfull + 1;   // the MMAs that read the staged tile have completed
+  uint64_t* cdone = wfree + 1;   // the copies of the staged tile have read it
+  uint64_t* drain = cdone + 1;
+  uint32_t* mbox = (uint32_t*)(drain + 1);  // [MBOX_DEPTH][P2C_MAX_G]
+  uint32_t* tptr = mbox + MBOX_DEPTH * P2C_MAX_G;
+  volatile int* abort = (volatile int*)(tptr + 1);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const uint32_t rank = cluster_rank();
+  const int64_t cid = blockIdx.x / G, ncl = gridDim.x / G;
+
+  if (threadIdx.x == 0) {
+    for (int k = 0; k < P2S_SLOTS; ++k) {
+      mbar_init(&full[k], 1);
+      mbar_init(&empty[k], 1);
+    }
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(&sfull[b], 1);
+      mbar_init(&sempty[b], 128);
+    }
+    mbar_init(zfull, 1);
+    mbar_init(zempty, 128);
+    mbar_init(wfull, 128);
+    mbar_init(wfree, 1);
+    mbar_init(cdone, 1);
+    mbar_init(drain, 1);
+    for (int k = 0; k < MBOX_DEPTH * P2C_MAX_G; ++k) mbox[k] = 0u;  // tag 0: no use yet
+    *abort = 0;
+    fence_mbar_init();
+  }
+  if (warp == 1) {
+    tmem_alloc(tptr, 512);
+    tmem_relinquish();
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  cluster_sync_all();  // every CTA's barriers and mailbox exist before any peer uses them
+  const uint32_t tbase = *tptr;
+  const int64_t total = ustart[n_inst];
+
+  if (warp == 0) {
+    if (lane == 0) {
+      uint32_t it = 0, sent[P2C_MAX_G] = {};
+      bool ok = true;
+      auto reserve = [&](bool expect_copy) -> int {
+        const int st = it % P2S_SLOTS;
+        if (!mbar_wait(&empty[st], ((it / P2S_SLOTS) & 1) ^ 1, abort)) {
+          ok = false;
+          return -1;
+        }
+        if (expect_copy) mbar_expect_tx(&full[st], 32768);
+        return st;
+      };
+      for (int64_t u = cid; ok && u < total; u += ncl) {
+        const int ki = find_inst(ustart, n_inst, u);
+        const TcInst* I = insts + ki;
+        const TcP2Args& a = I->p2;
+        const int64_t lu = u - ustart[ki];
+        const int ncg = (a.n_chunks + G - 1) / G;
+        const int per_split = a.n_stiles * ncg;
+        const int split = (int)(lu / per_split), rem = (int)(lu % per_split);
+        const int stile = rem / ncg, chunk = (rem % ncg) * G + (int)rank;
+        const bool cvalid = chunk < a.n_chunks;
+        const int jb0 = split * a.iblk_per_split;
+        const int nb = min(a.n_iblk, jb0 + a.iblk_per_split) - jb0;
+        const int rounds = (nb + G - 1) / G;
+        // software-pipelined order: logits of round j, then the Z' fills of round j - 1
+        for (int j = 0; ok && j <= rounds; ++j) {
+          const int r0 = j * G, nq = j < rounds ? min(G, nb - r0) : 0;
+          if ((int)rank < nq) {  // logits of this CTA's own block
+            const int ib = (jb0 + r0 + (int)rank) * 128;
+            for (int kb = 0; ok && kb < a.nk; ++kb) {
+              if (NPROD == 3) {
+                int st = reserve(true);
+                if (!ok) break;
+                tma_load_2d(smem + st * SLOT, &I->tmA128, &full[st], kb * 64, stile * 128);
+                tma_load_2d(smem + st * SLOT + 16384, &I->tmAl128, &full[st], kb * 64,
+                            stile * 128);
+                ++it;
+                st = reserve(true);
+                if (!ok) break;
+                tma_load_2d(smem + st * SLOT, &I->tmY, &full[st], kb * 64, ib);
+                tma_load_2d(smem + st * SLOT + 16384, &I->tmYl, &full[st], kb * 64, ib);
+                ++it;
+              } else {
+                const int st = reserve(true);
+                if (!ok) break;
+                tma_load_2d(smem + st * SLOT, &I->tmA128, &full[st], kb * 64, stile * 128);
+                tma_load_2d(smem + st * SLOT + 16384, &I->tmY, &full[st], kb * 64, ib);
+                ++it;
+              }
+            }
+          }
+          const int rp = (j - 1) * G, nqp = j >= 1 ? min(G, nb - rp) : 0;
+          if (!cvalid) {
+            // no pixel chunk in this unit: no weight tiles and no Z' products, but the
+            // uses of the peers' tiles still count, so that later announcements carry
+            // the tags their senders expect
+            for (int kq = 0; kq < nqp; ++kq)
+              if (kq != (int)rank) ++sent[kq];
+            continue;
+          }
+          // round j - 1: a ring slot for each peer's weight tile, reserved one block ahead
+          // of the two Y'^T tiles it multiplies (W1 T0 T0 W2 T1 T1 ... in this CTA's block
+          // order, its own tile staged apart).  Every Y'^T tile then lies within
+          // P2S_SLOTS - 1 places of its weight slot, so no fill waits for a slot that is
+          // only freed by the products that need that fill.
+          auto reserve_w = [&](int kq) {
+            const int st = reserve(true);
+            if (!ok) return;
+            const uint32_t row = sent[kq] % MBOX_DEPTH;
+            const uint32_t tag = (sent[kq] + 1u) & MBOX_TAG_MASK;
+            st_release_cluster_u32(mapa(smem_u32(mbox + row * P2C_MAX_G + rank), kq),
+                                   (tag << 4) | (uint32_t)st);
+            ++sent[kq];
+            ++it;
+          };
+          if (nqp > 0 && p2c_block((int)rank, nqp, 0) != (int)rank)
+            reserve_w(p2c_block((int)rank, nqp, 0));
+          for (int i = 0; ok && i < nqp; ++i) {
+            if (i + 1 < nqp) reserve_w(p2c_block((int)rank, nqp, i + 1));  // never own
+            const int ib = (jb0 + rp + p2c_block((int)rank, nqp, i)) * 128;
+            for (int h = 0; ok && h < 2; ++h) {
+              const int s2 = reserve(true);
+              if (!ok) break;
+              tma_load_2d(smem + s2 * SLOT, &I->tmYT, &full[s2], ib + h * 64, chunk * 256);
+              ++it;
+            }
+          }
+        }
+      }
+      if (!ok) {
+        raise_timeout(abort, status);
+        const uint32_t lo = it > P2S_SLOTS ? it - P2S_SLOTS : 0;
+        int zero = 0;
+        for (uint32_t k = lo; k < it; ++k)
+          mbar_wait(&full[k % P2S_SLOTS], (k / P2S_SLOTS) & 1, (volatile int*)&zero);
+      }
+    }
+  } else if (warp == 1) {
+    if (lane == 0) {
+      constexpr uint32_t idS = idesc_bf16_f32(128, 128);
+      constexpr uint32_t idZ = idesc_f16_f32(128, 256);
+      uint32_t it = 0, sc = 0, uc = 0, ow = 0;
+      bool ok = true;
+      auto wait_slot = [&]() -> int {
+        const int st = it % P2S_SLOTS;
+        if (!mbar_wait(&full[st], (it / P2S_SLOTS) & 1, abort)) {
+          ok = false;
+          return -1;
+        }
+        return st;
+      };
+      for (int64_t u = cid; ok && u < total; u += ncl) {
+        const int ki = find_inst(ustart, n_inst, u);
+        const TcInst* I = insts + ki;
+        const TcP2Args& a = I->p2;
+        const int64_t lu = u - ustart[ki];
+        const int ncg = (a.n_chunks + G - 1) / G;
+        const int per_split = a.n_stiles * ncg;
+        const int rem = (int)(lu % per_split);
+        const int chunk = (rem % ncg) * G + (int)rank;
+        const bool cvalid = chunk < a.n_chunks;
+        const int split = (int)(lu / per_split);
+        const int jb0 = split * a.iblk_per_split;
+        const int nb = min(a.n_iblk, jb0 + a.iblk_per_split) - jb0;
+        bool first_z = true;
+        const int rounds = (nb + G - 1) / G;
+        for (int j = 0; ok && j <= rounds; ++j) {
+          const int r0 = j * G, nq = j < rounds ? min(G, nb - r0) : 0;
+          if ((int)rank < nq) {
+            const int b = sc & 1;
+            if (!mbar_wait(&sempty[b], ((sc >> 1) & 1) ^ 1, abort)) {
+              ok = false;
+              break;
+            }
+            tc_fence_after();
+            const uint32_t d = tbase + (uint32_t)(b * 128);
+            for (int kb = 0; ok && kb < a.nk; ++kb) {
+              const int stA = wait_slot();
+              if (!ok) break;
+              uint8_t* sA = smem + stA * SLOT;
+              uint8_t* sY = sA + 16384;
+              int stY = stA;
+              if (NPROD == 3) {
+                ++it;
+                stY = wait_slot();
+                if (!ok) break;
+                sY = smem + stY * SLOT;
+              }
+              tc_fence_after();
+              const uint64_t dA = desc_sw128(sA), dY = desc_sw128(sY);
+#pragma unroll
+              for (int k4 = 0; k4 < 4; ++k4) {
+                mma_bf16(d, desc_advance(dA, k4), desc_advance(dY, k4), idS,
+                         (kb > 0 || k4 > 0) ? 1u : 0u);
+                if (NPROD == 3) {
+                  const uint64_t dAl = desc_sw128(sA + 16384), dYl = desc_sw128(sY + 16384);
+                  mma_bf16(d, desc_advance(dA, k4), desc_advance(dYl, k4), idS, 1u);
+                  mma_bf16(d, desc_advance(dAl, k4), desc_advance(dY, k4), idS, 1u);
+                }
+              }
+              mma_commit(&empty[stA]);
+              if (NPROD == 3) mma_commit(&empty[stY]);
+              ++it;
+            }
+            if (!ok) break;
+            mma_commit(&sfull[b]);
+            ++sc;
+          }
+          const int nqp = j >= 1 ? min(G, nb - (j - 1) * G) : 0;
+          // same order as the producer: the own tile from the staging slot, the others'
+          // ring slots taken one block ahead
+          int stPs[P2C_MAX_G];
+          if (cvalid && nqp > 0 && p2c_block((int)rank, nqp, 0) != (int)rank) {
+            stPs[0] = wait_slot();
+            ++it;
+          }
+          for (int i = 0; ok && i < nqp; ++i) {
+            if (cvalid && i + 1 < nqp) {
+              stPs[i + 1] = wait_slot();
+              ++it;
+              if (!ok) break;
+            }
+            const bool own = p2c_block((int)rank, nqp, i) == (int)rank;
+            if (own) {
+              // the staged tile of this round is written (tiles without a chunk are
+              // still consumed, so that the staging slot is released in order)
+              if (!mbar_wait(wfull, ow & 1, abort)) {
+                ok = false;
+                break;
+              }
+              tc_fence_after();
+            }
+            if (cvalid) {
+              if (first_z && !mbar_wait(zempty, (uc & 1) ^ 1, abort)) {
+                ok = false;
+                break;
+              }
+              tc_fence_after();
+              const uint32_t dZ = tbase + 256u;
+              const uint8_t* wt = own ? stage : smem + stPs[i] * SLOT;
+              for (int h = 0; ok && h < 2; ++h) {
+                const int stT = wait_slot();
+                if (!ok) break;
+                tc_fence_after();
+                const uint64_t dP = desc_sw128(wt + h * 16384);
+                const uint64_t dT = desc_sw128(smem + stT * SLOT);
+#pragma unroll
+                for (int k4 = 0; k4 < 4; ++k4)
+                  mma_bf16(dZ, desc_advance(dP, k4), desc_advance(dT, k4), idZ,
+                           (!first_z || h > 0 || k4 > 0) ? 1u : 0u);
+                mma_commit(&empty[stT]);
+                ++it;
+              }
+              first_z = false;
+            }
+            if (own) {
+              mma_commit(wfree);
+              ++ow;
+            } else if (cvalid) {
+              mma_commit(&empty[stPs[i]]);
+            }
+          }
+        }
+        if (!ok) break;
+        if (cvalid) {
+          mma_commit(zfull);
+          ++uc;
+        }
+      }
+      if (!ok) {
+        raise_timeout(abort, status);
+        mma_commit(drain);
+        int zero = 0;
+        mbar_wait(drain, 0, (volatile int*)&zero);
+      }
+    }
+  } else if (warp < 6) {
+    const int q = warp & 3;
+    const int row = q * 32 + lane;
+    const uint32_t lane_addr = tbase + ((uint32_t)(q * 32) << 16);
+    float2* wobs = (float2*)(stage + SLOT + P2S_BOOK) + q * 32;  // this warp's staging
+    uint32_t sc = 0, m = 0, uc = 0;
+    bool ok = true;
+    for (int64_t u = cid; ok && u < total; u += ncl) {
+      const int ki = find_inst(ustart, n_inst, u);
+      const TcInst* I = insts + ki;
+      const TcP2Args& a = I->p2;
+      const int64_t lu = u - ustart[ki];
+      const int ncg = (a.n_chunks + G - 1) / G;
+      const int per_split = a.n_stiles * ncg;
+      const int split = (int)(lu / per_split), rem = (int)(lu % per_split);
+      const int stile = rem / ncg, cgrp = rem % ncg;
+      const int chunk = cgrp * G + (int)rank;
+      const bool cvalid = chunk < a.n_chunks;
+      const int jb0 = split * a.iblk_per_split;
+      const int nb = min(a.n_iblk, jb0 + a.iblk_per_split) - jb0;
+      const int s = stile * 128 + row;
+      const float cb = a.colb[s], cm = a.colm[s];
+      const float a2 = a.a2, c2 = a.c2;
+      float cacc = 0.f, zacc = 0.f;
+      for (int r0 = 0; ok && r0 < nb; r0 += G) {
+        const int nq = min(G, nb - r0);
+        if ((int)rank >= nq) continue;
+        const int64_t ib = (int64_t)(jb0 + r0 + (int)rank) * 128;
+        const int b = sc & 1;
+        // (ybar, lse2) of the next 32-observation chunk, loaded one chunk ahead of its
+        // use; lse2 = +inf past N gives weight 0
+        float ny = a.ybar[ib + lane];
+        float nl = (ib + lane < a.N) ? a.lse2[ib + lane] : INFINITY;
+        ok = __all_sync(0xffffffffu, mbar_wait(&sfull[b], (sc >> 1) & 1, abort));
+        if (!ok) break;
+        tc_fence_after();
+        // the weights of this row, as fp16 pairs in the order of the tile's columns; they
+        // are computed before the staging slot is free, so that the logit buffer is
+        // released early
+        uint32_t packed[64];
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+          __syncwarp();  // the warp is done with the previous chunk's terms
+          wobs[lane] = make_float2(ny, nl);
+          __syncwarp();
+          if (c < 3) {
+            const int64_t io = ib + (c + 1) * 32 + lane;
+            ny = a.ybar[io];
+            nl = (io < a.N) ? a.lse2[io] : INFINITY;
+          }
+          float v[32];
+          tmem_ld32(lane_addr + (uint32_t)(b * 128 + c * 32), v);
+          tmem_ld_wait();
+#pragma unroll
+          for (int e = 0; e < 32; e += 2) {
+            float w2[2];
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+              const float2 yl = wobs[e + h];
+              const float ybi = yl.x;
+              const float dd = ybi - cm;
+              const float val = fmaf(v[e + h], a2, cb - yl.y) - c2 * dd * dd;
+              const float w = exp2f(val) * W_SCALE;
+              w2[h] = __half2float(__float2half_rn(w));
+              cacc += w2[h];
+              zacc = fmaf(w2[h], ybi, zacc);
+            }
+            const __half2 pr = __floats2half2_rn(w2[0], w2[1]);
+            packed[c * 16 + (e >> 1)] = *reinterpret_cast<const uint32_t*>(&pr);
+          }
+        }
+        tc_fence_before();
+        mbar_arrive(&sempty[b]);  // the logits are no longer needed
+        // the staging slot is free once the MMAs and the copies of the previous tile
+        // have read it
+        ok = __all_sync(0xffffffffu, mbar_wait(wfree, (m & 1) ^ 1, abort) &&
+                                         mbar_wait(cdone, (m & 1) ^ 1, abort));
+        if (!ok) break;
+        uint8_t* prow = stage + row * 128;
+#pragma unroll
+        for (int col16 = 0; col16 < 16; ++col16) {  // 16-byte units along the observations
+          const int kb2 = col16 >> 3, cc = col16 & 7;
+          *reinterpret_cast<uint4*>(prow + kb2 * 16384 + ((cc ^ (row & 7)) << 4)) =
+              make_uint4(packed[4 * col16], packed[4 * col16 + 1], packed[4 * col16 + 2],
+                         packed[4 * col16 + 3]);
+        }
+        fence_proxy_async_smem();
+        mbar_arrive(wfull);
+        ++sc;
+        ++m;
+      }
+      if (!ok) break;
+      if (cvalid) {
+        ok = __all_sync(0xffffffffu, mbar_wait(zfull, uc & 1, abort));
+        if (!ok) break;
+        tc_fence_after();
+        float* zrow = a.Zp + ((int64_t)split * a.Spad + s) * a.ldy;
+#pragma unroll 1
+        for (int c = 0; c < 8; ++c) {
+          float v[32];
+          tmem_ld32(lane_addr + (uint32_t)(256 + c * 32), v);
+          tmem_ld_wait();
+          const int p0 = chunk * 256 + c * 32;
+          if (p0 < a.ldy) {
+#pragma unroll
+            for (int e = 0; e < 32; e += 4)
+              if (p0 + e < a.ldy)
+                *reinterpret_cast<float4*>(zrow + p0 + e) =
+                    make_float4(v[e] * W_UNSCALE, v[e + 1] * W_UNSCALE, v[e + 2] * W_UNSCALE,
+                                v[e + 3] * W_UNSCALE);
+          }
+        }
+        tc_fence_before();
+        mbar_arrive(zempty);
+        ++uc;
+      }
+      if (cgrp == 0) {
+        const int64_t part = (int64_t)split * G + rank;
+        a.cp[part * a.Spad + s] = cacc * W_UNSCALE;
+        a.zbp[part * a.Spad + s] = zacc * W_UNSCALE;
+      }
+    }
+    if (!ok) raise_timeout(abort, status);
+  } else if (lane == 0) {
+    // sender: each staged tile goes to every peer that owns a pixel chunk, into the ring
+    // slot that peer announced for this use of the tile, in the order the announcements
+    // arrive
+    uint32_t m = 0;
+    bool ok = true;
+    for (int64_t u = cid; ok && u < total; u += ncl) {
+      const int ki = find_inst(ustart, n_inst, u);
+      const TcP2Args& a = insts[ki].p2;
+      const int64_t lu = u - ustart[ki];
+      const int ncg = (a.n_chunks + G - 1) / G;
+      const int per_split = a.n_stiles * ncg;
+      const int split = (int)(lu / per_split), rem = (int)(lu % per_split);
+      const int cgrp = rem % ncg;
+      const int jb0 = split * a.iblk_per_split;
+      const int nb = min(a.n_iblk, jb0 + a.iblk_per_split) - jb0;
+      uint32_t peers = 0;  // peers with a pixel chunk in this chunk group
+      for (int k = 0; k < G; ++k)
+        if (k != (int)rank && cgrp * G + k < a.n_chunks) peers |= 1u << k;
+      for (int r0 = 0; ok && r0 < nb; r0 += G) {
+        if ((int)rank >= min(G, nb - r0)) continue;
+        if (!mbar_wait(wfull, m & 1, abort)) {
+          ok = false;
+          break;
+        }
+        const uint32_t* mrow = mbox + (m % MBOX_DEPTH) * P2C_MAX_G;
+        const uint32_t expect = (m + 1u) & MBOX_TAG_MASK;
+        uint32_t pending = peers;
+        const uint64_t t0 = globaltimer();
+        while (pending) {
+          const uint32_t before = pending;
+          for (uint32_t pm = pending; pm; pm &= pm - 1) {
+            const int k = __ffs(pm) - 1;
+            const uint32_t v = ld_acquire_cluster_u32(mrow + k);
+            if ((v >> 4) == expect) {
+              const uint32_t slot = v & 15u;
+              bulk_copy_to_peer(mapa(smem_u32(smem + slot * SLOT), k), stage, 32768,
+                                mapa(smem_u32(&full[slot]), k));
+              pending &= ~(1u << k);
+            }
+          }
+          if (pending && (*abort || globaltimer() - t0 > kWaitTimeoutNs)) {
+            ok = false;
+            break;
+          }
+          // nothing announced: back off, so that the polling does not take shared-memory
+          // bandwidth from the MMAs
+          if (pending == before) __nanosleep(128);
+        }
+        bulk_commit();
+        bulk_wait_read0();
+        if (!ok) break;
+        mbar_arrive(cdone);
+        ++m;
+      }
+    }
+    bulk_wait0();  // no copy is still landing in a peer when the cluster leaves
+    if (!ok) raise_timeout(abort, status);
+  }
+  __syncthreads();
+  if (warp == 1) {
+    tc_fence_after();
+    tmem_dealloc(tbase, 512);
+  }
+  cluster_sync_all();  // no CTA leaves while a peer may still copy into it
+}
+
+// ring + staging slot + bookkeeping (22 mbarriers, 8 x 16 mailbox, TMEM address, abort
+// flag: 696 of the 768 bytes) + per-warp staging of one 32-observation chunk's
+// (ybar, lse2) (4 x 256 bytes)
+constexpr size_t P2S_SMEM = 1024 + (P2S_SLOTS + 1) * SLOT + P2S_BOOK + 1024;
+static_assert(P2S_SMEM <= 232448, "exceeds the shared memory of one CTA");
 
 constexpr size_t P1_SMEM = 1024 + P1_SLOTS * SLOT + 256 + 1024;
 constexpr size_t P2_SMEM = 1024 + P2_SLOTS * SLOT + 2 * SLOT + 256 + 1024;
@@ -1229,13 +1745,30 @@ cudaError_t set_smem(K kernel, size_t bytes) {
   return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
 }
 
-// the clustered pass-2 kernel: its shared memory, and clusters above the portable size
+// the clustered pass-2 kernels: their shared memory, and clusters above the portable
+// size for the staged form
 template <int NPROD>
 cudaError_t set_p2c_attrs() {
-  cudaError_t e = set_smem(k_p2c_tc<NPROD>, P2C_SMEM);
+  cudaError_t e = set_smem(k_p2c_tc<NPROD>, P2R_SMEM);
+  if (e == cudaSuccess) e = set_smem(k_p2s_tc<NPROD>, P2S_SMEM);
   if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(k_p2c_tc<NPROD>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+    e = cudaFuncSetAttribute(k_p2s_tc<NPROD>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
   return e;
+}
+
+// The launch shape of the cluster form used for clusters of G: the ring form up to
+// P2R_MAX_G, the staged form above.
+template <int NPROD>
+void p2c_form(int G, const void** fn, int* threads, size_t* smem) {
+  if (G <= P2R_MAX_G) {
+    *fn = (const void*)k_p2c_tc<NPROD>;
+    *threads = TC_THREADS;
+    *smem = P2R_SMEM;
+  } else {
+    *fn = (const void*)k_p2s_tc<NPROD>;
+    *threads = P2S_THREADS;
+    *smem = P2S_SMEM;
+  }
 }
 
 }  // namespace
@@ -1425,18 +1958,22 @@ void fill_inst(const srmra_ctx* c, TcInst* I) {
   b.status = c->status;
 }
 
-// Co-resident clusters of G CTAs of the clustered pass-2 kernel (queried once per G); 0
-// for a cluster size above the portable limit that the GPU cannot place.
+// Co-resident clusters of G CTAs of the clustered pass-2 kernel of that size (queried
+// once per G); 0 for a cluster size above the portable limit that the GPU cannot place.
 template <int NPROD>
 int max_clusters(int G, int num_sms) {
   static int cache[P2C_MAX_G + 1] = {};
   if (cache[G] != 0) return cache[G] > 0 ? cache[G] : 0;
   cudaGetLastError();
   set_p2c_attrs<NPROD>();
+  const void* fn;
+  int threads;
+  size_t smem;
+  p2c_form<NPROD>(G, &fn, &threads, &smem);
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3((unsigned)(G * (num_sms / G)), 1, 1);
-  cfg.blockDim = dim3(TC_THREADS, 1, 1);
-  cfg.dynamicSmemBytes = P2C_SMEM;
+  cfg.blockDim = dim3((unsigned)threads, 1, 1);
+  cfg.dynamicSmemBytes = smem;
   cudaLaunchAttribute attr[1];
   attr[0].id = cudaLaunchAttributeClusterDimension;
   attr[0].val.clusterDim.x = (unsigned)G;
@@ -1445,7 +1982,7 @@ int max_clusters(int G, int num_sms) {
   cfg.attrs = attr;
   cfg.numAttrs = 1;
   int n = 0;
-  if (cudaOccupancyMaxActiveClusters(&n, k_p2c_tc<NPROD>, &cfg) != cudaSuccess || n < 1) {
+  if (cudaOccupancyMaxActiveClusters(&n, fn, &cfg) != cudaSuccess || n < 1) {
     cudaGetLastError();
     if (G > P2C_PORTABLE_G) {
       cache[G] = -1;
@@ -1466,14 +2003,19 @@ cudaError_t launch_cluster_p2(int G, const TcInst* d_insts, const int64_t* d_ust
     if (e != cudaSuccess) return e;
     attr = true;
   }
+  if (G < 2 || G > P2C_MAX_G) return cudaErrorInvalidValue;
   int ncl = max_clusters<NPROD>(G, num_sms);
   if (ncl < 1) return cudaErrorInvalidConfiguration;  // chosen only where it can be placed
   if (total < ncl) ncl = (int)total;
   if (ncl < 1) return cudaSuccess;
+  const void* fn;
+  int threads;
+  size_t smem;
+  p2c_form<NPROD>(G, &fn, &threads, &smem);
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3((unsigned)(G * ncl), 1, 1);
-  cfg.blockDim = dim3(TC_THREADS, 1, 1);
-  cfg.dynamicSmemBytes = P2C_SMEM;
+  cfg.blockDim = dim3((unsigned)threads, 1, 1);
+  cfg.dynamicSmemBytes = smem;
   cfg.stream = stream;
   cudaLaunchAttribute at[1];
   at[0].id = cudaLaunchAttributeClusterDimension;
@@ -1482,7 +2024,9 @@ cudaError_t launch_cluster_p2(int G, const TcInst* d_insts, const int64_t* d_ust
   at[0].val.clusterDim.z = 1;
   cfg.attrs = at;
   cfg.numAttrs = 1;
-  return cudaLaunchKernelEx(&cfg, k_p2c_tc<NPROD>, d_insts, d_ustart, n, G, status);
+  if (G <= P2R_MAX_G)
+    return cudaLaunchKernelEx(&cfg, k_p2c_tc<NPROD>, d_insts, d_ustart, n, G, status);
+  return cudaLaunchKernelEx(&cfg, k_p2s_tc<NPROD>, d_insts, d_ustart, n, G, status);
 }
 
 template <int NPROD>
@@ -1520,30 +2064,27 @@ template int max_clusters_p2<1>(int, int);
 template int max_clusters_p2<3>(int, int);
 
 // Cluster size of pass 2 for `chunks` 256-pixel chunks of Z' (l2 pixels, n_iblk blocks of
-// 128 observations).  Up to 4 chunks one cluster covers them all (G = chunks).  Beyond,
-// the weights of a (shift tile, observation block) are computed once per group of G
-// chunks, and G trades that recompute against the cost of a round and how many clusters
-// of G co-reside (GPC packing).  A cluster round takes about a * NPROD * l2 (the logits
-// of the CTA's own block) + b * G (one weight tile handed over per member), a = 2.24 ns
-// and b = 5.2 us, fitted to measured pass-2 times of 11 shapes (L = 72..128, K = 2,
-// G = 3..13, within 12% of the best size measured); the busiest cluster runs
-// groups * ceil(n_iblk / G) / clusters(G) rounds per shift tile.  Clusters of 16 (one per
-// GPC) measured 28-43% slower than this estimate, so sizes above 13 are not considered.
-constexpr int P2C_RULE_MAX_G = 13;
-static_assert(P2C_RULE_MAX_G <= P2C_MAX_G, "the rule may pick a size the kernel lacks");
-
+// 128 observations).  Up to 4 chunks one cluster covers them all (G = chunks, ring form).
+// Beyond, the weights of a (shift tile, observation block) are computed once per group
+// of G chunks, and G trades that recompute against the cost of a round and how many
+// clusters of G co-reside (GPC packing).  A cluster round takes about a * NPROD * l2 (the
+// logits of the CTA's own block) + b * G (one weight tile handed over per member), with
+// a = 2.93 ns and b = 4.3 us (ring form, G <= 4) or 4.0 us (staged form), fitted to
+// measured pass-2 times of both forms (L = 72..128, K = 2, G = 3..16); the busiest
+// cluster runs groups * ceil(n_iblk / G) / clusters(G) rounds per shift tile.
 int choose_p2_cluster(int chunks, int l2, int64_t n_iblk, int prec, int num_sms) {
   if (chunks <= 1) return 1;
-  if (chunks <= 4) return chunks;
+  if (chunks <= P2R_MAX_G) return chunks;
   const int nprod = prec == SRMRA_BF16X3 ? 3 : 1;
-  constexpr double a_us = 2.24e-3, b_us = 5.2;
-  int best = 4;
+  constexpr double a_us = 2.93e-3, b_ring_us = 4.3, b_staged_us = 4.0;
+  int best = P2R_MAX_G;
   double best_cost = 0.0;
-  for (int G = 2; G <= P2C_RULE_MAX_G && G <= chunks; ++G) {
+  for (int G = 2; G <= P2C_MAX_G && G <= chunks; ++G) {
     const int ncl = nprod == 3 ? max_clusters<3>(G, num_sms) : max_clusters<1>(G, num_sms);
     if (ncl < 1) continue;
     const double groups = (double)((chunks + G - 1) / G);
     const double rounds = groups * (double)((n_iblk + G - 1) / G) / (double)ncl;
+    const double b_us = G <= P2R_MAX_G ? b_ring_us : b_staged_us;
     const double cost = rounds * (a_us * nprod * l2 + b_us * G);
     if (best_cost == 0.0 || cost < best_cost) {
       best = G;

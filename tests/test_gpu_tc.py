@@ -130,8 +130,9 @@ def test_cluster_and_per_chunk_pass2_agree(S, L, K, N, sigma):
     """The cluster form of pass 2 (weights computed once per observation block and
     shared through distributed shared memory) and the per-chunk form (weights
     recomputed for every pixel chunk) give the same iteration.  The shapes take clusters
-    of 2 to 10 CTAs (L=96, K=2 with 1000 observations: 9, above the portable 8; L=128,
-    K=2 with 1250: 10, two chunk groups of 10 and 6)."""
+    of 2 to 10 CTAs, in the ring form (up to 4) and the staged form (L=48, K=1 with 400
+    observations: 5; L=96, K=2 with 1000: 9, above the portable 8; L=128, K=2 with 1250:
+    10, two chunk groups of 10 and 6, so that chunk ownership changes between units)."""
     p = synth.make_problem(L, K, N, sigma, seed=synth.seed_for(3, 900 + L))
     out = []
     for flags in (0, 2):  # 2 = SRMRA_FLAG_NO_CLUSTER
@@ -148,8 +149,8 @@ def test_cluster_and_per_chunk_pass2_agree(S, L, K, N, sigma):
 
 def test_largest_request_full_size(S):
     """The largest problem of the serving mix at full size (L = 128, K = 2: l^2 = 4096,
-    sixteen pixel chunks in two groups of a 9-CTA cluster; N = 1e5): one bf16x3 iteration
-    element-wise
+    sixteen pixel chunks, one 16-CTA cluster of the staged form; N = 1e5): one bf16x3
+    iteration element-wise
     against the FFT oracle (pinned to the dense oracle), x, rho and every lse_i."""
     p = synth.workload_problem("largest_request_L128_K2_N1e5")
     s = S.Solver(p.L, p.K, p.sigma, p.y, prec="bf16x3", x0=p.x0, rho1=p.rho1_0,
