@@ -82,8 +82,9 @@ def test_em_step_parity_bf16x3(S, L, K, N, sigma):
 
 
 @pytest.mark.parametrize("L,K,N,sigma", [(16, 2, 500, 0.5), (64, 2, 700, 1.0),
-                                         (12, 3, 333, 0.8)])
+                                         (12, 3, 333, 0.8), (96, 2, 900, 0.6)])
 def test_em_step_bf16(S, L, K, N, sigma):
+    """The last shape (nine pixel chunks) runs pass 2 in the staged cluster form."""
     p = synth.make_problem(L, K, N, sigma, seed=synth.seed_for(3, L * 7 + K))
     w = one_step(S, p, "bf16")
     tol = TOL["bf16"]
