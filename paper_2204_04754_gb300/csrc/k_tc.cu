@@ -671,20 +671,23 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
 //   7-slot operand ring.  Each CTA's producer reserves a slot for every tile of the
 //   round and mails the slot index to the tile's owner; once all G reservations are in,
 //   the owner writes its tile into its own slot and bulk-copies it into the others'.
-// - staged form (G >= 5): the own tile is written to a staging slot beside a 6-slot ring,
-//   and a sender warp copies it to each peer as soon as that peer's reservation
-//   arrives, so that the CTAs no longer wait for the slowest reservation of each tile.
-// The deeper ring is worth more to small clusters (their logits dominate a round); the
-// per-peer hand-off to large ones (one weight tile per member per round).
+// - interleaved form (G >= 5): the own tile is written to a staging slot, a sender warp
+//   copies it to each peer as soon as that peer's reservation arrives (the CTAs no
+//   longer wait for the slowest reservation of each tile), the peers' tiles land in a
+//   weight ring of their own, and the Z' blocks of a round are interleaved with the
+//   logit k-blocks of the next one.
+// The deeper operand ring is worth more to small clusters (their logits dominate a
+// round); the early per-peer hand-off to large ones (one weight tile per member per
+// round).
 // largest cluster; clusters above 8 CTAs (the portable limit) need the non-portable
 // cluster-size attribute and fit only where a GPC has the free SMs
 constexpr int P2C_MAX_G = 16;
 constexpr int P2C_PORTABLE_G = 8;
 constexpr int P2R_MAX_G = 4;  // ring form: clusters up to 4
-// Mailbox rows, one per use of a tile.  A producer can announce at most one use per ring
-// slot it holds for a peer (the slot is freed only after the peer has read the
-// announcement and sent its tile), so more rows than ring slots keep a row from being
-// reused before it is read, whatever the cluster's chunk ownership.
+// Mailbox rows, one per use of a tile.  In the ring form a producer can announce at most
+// one use per ring slot it holds for a peer (the slot is freed only after the peer has
+// read the announcement and sent its tile), so more rows than ring slots keep a row from
+// being reused before it is read, whatever the cluster's chunk ownership.
 constexpr int MBOX_DEPTH = 8;
 
 // ---- ring form
@@ -1119,19 +1122,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
 constexpr size_t P2R_SMEM = 1024 + P2R_SLOTS * SLOT + P2R_BOOK + 1024;
 static_assert(P2R_SMEM <= 232448, "exceeds the shared memory of one CTA");
 
-// ---- staged form
-constexpr int P2S_SLOTS = 6;  // ring slots; the own weight tile has a staging slot besides
-constexpr int P2S_THREADS = 224;  // producer, MMA, 4 epilogue warps, sender
-static_assert(MBOX_DEPTH > P2S_SLOTS, "a mailbox row could be reused before it is read");
+// ---- interleaved form
 constexpr uint32_t MBOX_TAG_MASK = 0x0FFFFFFFu;  // entry = tag << 4 | slot, tag = use + 1
-// barriers: full, empty (ring), sfull, sempty, zfull, zempty, wfull, wfree, cdone, drain;
-// then the mailbox (tagged entries, one row per use of this CTA's tile), the TMEM address
-// and the abort flag, in P2S_BOOK bytes
-constexpr int P2S_BOOK = 768;
-static_assert((2 * P2S_SLOTS + 2 + 2 + 1 + 1 + 1 + 1 + 1 + 1) * 8 +
-                      MBOX_DEPTH * P2C_MAX_G * 4 + 4 + 4 <= P2S_BOOK,
-              "staged-form bookkeeping exceeds its P2S_BOOK bytes");
-static_assert(P2S_SLOTS < 16, "a slot index must fit the mailbox entry's 4 bits");
 
 // The blocks of a round in this CTA's order: its own block first (rank < nq), then the
 // next ranks cyclically; a CTA without a block of the round starts at rank mod nq.
@@ -1139,16 +1131,45 @@ __device__ __forceinline__ int p2c_block(int rank, int nq, int i) {
   return (rank % nq + i) % nq;
 }
 
+// Each CTA's own weight tile is written to a staging slot, from which its MMAs read it
+// first in the round and a sender warp bulk-copies it to each peer with a pixel chunk as
+// soon as that peer's slot is announced (a tagged entry in the sender's mailbox).  The
+// peers' tiles land in a 2-slot weight ring of their own, whose slots a weight-producer
+// thread announces as soon as they are free, at most about a round ahead of the main
+// producer.  The Z' blocks of round j - 1 are interleaved with the logit k-blocks of
+// round j, so that a tile is needed several k-blocks after its slot was announced.  The
+// main ring (logit operands and Y'^T tiles) has 4 slots.
+constexpr int P2I_SLOTS = 4;
+constexpr int P2I_WSLOTS = 2;
+constexpr int P2I_THREADS = 256;  // producer, MMA, 4 epilogue warps, sender, weight producer
+// barriers: full, empty (main ring), wrfull, wrempty (weight ring), sfull, sempty, zfull,
+// zempty, wfull, wfree, cdone, drain; then the mailbox, the TMEM address, the abort flag
+// and the round counter, in P2I_BOOK bytes
+constexpr int P2I_BOOK = 768;
+static_assert((2 * P2I_SLOTS + 2 * P2I_WSLOTS + 2 + 2 + 1 + 1 + 1 + 1 + 1 + 1) * 8 +
+                      MBOX_DEPTH * P2C_MAX_G * 4 + 4 + 4 + 4 <= P2I_BOOK,
+              "interleaved-form bookkeeping exceeds its P2I_BOOK bytes");
+static_assert(MBOX_DEPTH >= 4, "the weight producer's lead needs 4 mailbox rows");
+
+// k-block of round j after which Z' block i of round j - 1 is issued (nqp blocks spread
+// over the nk k-blocks; all after the last one when there are too few k-blocks)
+__device__ __forceinline__ int p2i_zpos(int i, int nqp, int nk) {
+  return nk >= nqp + 1 ? ((i + 1) * nk) / (nqp + 1) - 1 : nk - 1;
+}
+
 template <int NPROD>
-__global__ void __launch_bounds__(P2S_THREADS, 1)
-    k_p2s_tc(const TcInst* __restrict__ insts, const int64_t* __restrict__ ustart, int n_inst,
+__global__ void __launch_bounds__(P2I_THREADS, 1)
+    k_p2i_tc(const TcInst* __restrict__ insts, const int64_t* __restrict__ ustart, int n_inst,
              int G, int* status) {
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = align1024(smem_raw);
-  uint8_t* stage = smem + P2S_SLOTS * SLOT;  // this CTA's weight tile
+  uint8_t* wring = smem + P2I_SLOTS * SLOT;     // the peers' weight tiles
+  uint8_t* stage = wring + P2I_WSLOTS * SLOT;   // this CTA's weight tile
   uint64_t* full = (uint64_t*)(stage + SLOT);
-  uint64_t* empty = full + P2S_SLOTS;
-  uint64_t* sfull = empty + P2S_SLOTS;
+  uint64_t* empty = full + P2I_SLOTS;
+  uint64_t* wrfull = empty + P2I_SLOTS;     // weight ring: a peer's tile has landed
+  uint64_t* wrempty = wrfull + P2I_WSLOTS;  // weight ring: its products are done
+  uint64_t* sfull = wrempty + P2I_WSLOTS;
   uint64_t* sempty = sfull + 2;
   uint64_t* zfull = sempty + 2;
   uint64_t* zempty = zfull + 1;
@@ -1159,14 +1180,19 @@ __global__ void __launch_bounds__(P2S_THREADS, 1)
   uint32_t* mbox = (uint32_t*)(drain + 1);  // [MBOX_DEPTH][P2C_MAX_G]
   uint32_t* tptr = mbox + MBOX_DEPTH * P2C_MAX_G;
   volatile int* abort = (volatile int*)(tptr + 1);
+  volatile uint32_t* rstart = (volatile uint32_t*)(tptr + 2);  // rounds the producer began
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const uint32_t rank = cluster_rank();
   const int64_t cid = blockIdx.x / G, ncl = gridDim.x / G;
 
   if (threadIdx.x == 0) {
-    for (int k = 0; k < P2S_SLOTS; ++k) {
+    for (int k = 0; k < P2I_SLOTS; ++k) {
       mbar_init(&full[k], 1);
       mbar_init(&empty[k], 1);
+    }
+    for (int k = 0; k < P2I_WSLOTS; ++k) {
+      mbar_init(&wrfull[k], 1);
+      mbar_init(&wrempty[k], 1);
     }
     for (int b = 0; b < 2; ++b) {
       mbar_init(&sfull[b], 1);
@@ -1180,6 +1206,7 @@ __global__ void __launch_bounds__(P2S_THREADS, 1)
     mbar_init(drain, 1);
     for (int k = 0; k < MBOX_DEPTH * P2C_MAX_G; ++k) mbox[k] = 0u;  // tag 0: no use yet
     *abort = 0;
+    *rstart = 0;
     fence_mbar_init();
   }
   if (warp == 1) {
@@ -1195,15 +1222,17 @@ __global__ void __launch_bounds__(P2S_THREADS, 1)
 
   if (warp == 0) {
     if (lane == 0) {
-      uint32_t it = 0, sent[P2C_MAX_G] = {};
+      // main ring: logit operands of this CTA's block and the Y'^T tiles of its chunk, in
+      // the MMA's order (Z' blocks of round j - 1 between the k-blocks of round j)
+      uint32_t it = 0, g = 0;
       bool ok = true;
-      auto reserve = [&](bool expect_copy) -> int {
-        const int st = it % P2S_SLOTS;
-        if (!mbar_wait(&empty[st], ((it / P2S_SLOTS) & 1) ^ 1, abort)) {
+      auto reserve = [&]() -> int {
+        const int st = it % P2I_SLOTS;
+        if (!mbar_wait(&empty[st], ((it / P2I_SLOTS) & 1) ^ 1, abort)) {
           ok = false;
           return -1;
         }
-        if (expect_copy) mbar_expect_tx(&full[st], 32768);
+        mbar_expect_tx(&full[st], 32768);
         return st;
       };
       for (int64_t u = cid; ok && u < total; u += ncl) {
@@ -1219,88 +1248,66 @@ __global__ void __launch_bounds__(P2S_THREADS, 1)
         const int jb0 = split * a.iblk_per_split;
         const int nb = min(a.n_iblk, jb0 + a.iblk_per_split) - jb0;
         const int rounds = (nb + G - 1) / G;
-        // software-pipelined order: logits of round j, then the Z' fills of round j - 1
         for (int j = 0; ok && j <= rounds; ++j) {
           const int r0 = j * G, nq = j < rounds ? min(G, nb - r0) : 0;
+          const int rp = (j - 1) * G, nqp = j >= 1 ? min(G, nb - rp) : 0;
+          *rstart = ++g;  // the weight producer may announce the slots of round j - 1
+          auto z_fills = [&](int i) {
+            if (!cvalid) return;
+            const int ib = (jb0 + rp + p2c_block((int)rank, nqp, i)) * 128;
+            for (int h = 0; ok && h < 2; ++h) {
+              const int s2 = reserve();
+              if (!ok) break;
+              tma_load_2d(smem + s2 * SLOT, &I->tmYT, &full[s2], ib + h * 64, chunk * 256);
+              ++it;
+            }
+          };
+          int zi = 0;
           if ((int)rank < nq) {  // logits of this CTA's own block
             const int ib = (jb0 + r0 + (int)rank) * 128;
             for (int kb = 0; ok && kb < a.nk; ++kb) {
               if (NPROD == 3) {
-                int st = reserve(true);
+                int st = reserve();
                 if (!ok) break;
                 tma_load_2d(smem + st * SLOT, &I->tmA128, &full[st], kb * 64, stile * 128);
                 tma_load_2d(smem + st * SLOT + 16384, &I->tmAl128, &full[st], kb * 64,
                             stile * 128);
                 ++it;
-                st = reserve(true);
+                st = reserve();
                 if (!ok) break;
                 tma_load_2d(smem + st * SLOT, &I->tmY, &full[st], kb * 64, ib);
                 tma_load_2d(smem + st * SLOT + 16384, &I->tmYl, &full[st], kb * 64, ib);
                 ++it;
               } else {
-                const int st = reserve(true);
+                const int st = reserve();
                 if (!ok) break;
                 tma_load_2d(smem + st * SLOT, &I->tmA128, &full[st], kb * 64, stile * 128);
                 tma_load_2d(smem + st * SLOT + 16384, &I->tmY, &full[st], kb * 64, ib);
                 ++it;
               }
+              for (; ok && zi < nqp && p2i_zpos(zi, nqp, a.nk) == kb; ++zi) z_fills(zi);
             }
           }
-          const int rp = (j - 1) * G, nqp = j >= 1 ? min(G, nb - rp) : 0;
-          if (!cvalid) {
-            // no pixel chunk in this unit: no weight tiles and no Z' products, but the
-            // uses of the peers' tiles still count, so that later announcements carry
-            // the tags their senders expect
-            for (int kq = 0; kq < nqp; ++kq)
-              if (kq != (int)rank) ++sent[kq];
-            continue;
-          }
-          // round j - 1: a ring slot for each peer's weight tile, reserved one block ahead
-          // of the two Y'^T tiles it multiplies (W1 T0 T0 W2 T1 T1 ... in this CTA's block
-          // order, its own tile staged apart).  Every Y'^T tile then lies within
-          // P2S_SLOTS - 1 places of its weight slot, so no fill waits for a slot that is
-          // only freed by the products that need that fill.
-          auto reserve_w = [&](int kq) {
-            const int st = reserve(true);
-            if (!ok) return;
-            const uint32_t row = sent[kq] % MBOX_DEPTH;
-            const uint32_t tag = (sent[kq] + 1u) & MBOX_TAG_MASK;
-            st_release_cluster_u32(mapa(smem_u32(mbox + row * P2C_MAX_G + rank), kq),
-                                   (tag << 4) | (uint32_t)st);
-            ++sent[kq];
-            ++it;
-          };
-          if (nqp > 0 && p2c_block((int)rank, nqp, 0) != (int)rank)
-            reserve_w(p2c_block((int)rank, nqp, 0));
-          for (int i = 0; ok && i < nqp; ++i) {
-            if (i + 1 < nqp) reserve_w(p2c_block((int)rank, nqp, i + 1));  // never own
-            const int ib = (jb0 + rp + p2c_block((int)rank, nqp, i)) * 128;
-            for (int h = 0; ok && h < 2; ++h) {
-              const int s2 = reserve(true);
-              if (!ok) break;
-              tma_load_2d(smem + s2 * SLOT, &I->tmYT, &full[s2], ib + h * 64, chunk * 256);
-              ++it;
-            }
-          }
+          for (; ok && zi < nqp; ++zi) z_fills(zi);
         }
       }
       if (!ok) {
         raise_timeout(abort, status);
-        const uint32_t lo = it > P2S_SLOTS ? it - P2S_SLOTS : 0;
+        const uint32_t lo = it > P2I_SLOTS ? it - P2I_SLOTS : 0;
         int zero = 0;
         for (uint32_t k = lo; k < it; ++k)
-          mbar_wait(&full[k % P2S_SLOTS], (k / P2S_SLOTS) & 1, (volatile int*)&zero);
+          mbar_wait(&full[k % P2I_SLOTS], (k / P2I_SLOTS) & 1, (volatile int*)&zero);
       }
     }
   } else if (warp == 1) {
     if (lane == 0) {
       constexpr uint32_t idS = idesc_bf16_f32(128, 128);
       constexpr uint32_t idZ = idesc_f16_f32(128, 256);
-      uint32_t it = 0, sc = 0, uc = 0, ow = 0;
+      uint32_t it = 0, itw = 0, sc = 0, uc = 0, ow = 0;
       bool ok = true;
       auto wait_slot = [&]() -> int {
-        const int st = it % P2S_SLOTS;
-        if (!mbar_wait(&full[st], (it / P2S_SLOTS) & 1, abort)) {
+        const int st = it % P2I_SLOTS;
+        if (!mbar_wait(&full[st], (it / P2I_SLOTS) & 1, abort)) {
           ok = false;
           return -1;
         }
@@ -1323,6 +1330,60 @@ __global__ void __launch_bounds__(P2S_THREADS, 1)
         const int rounds = (nb + G - 1) / G;
         for (int j = 0; ok && j <= rounds; ++j) {
           const int r0 = j * G, nq = j < rounds ? min(G, nb - r0) : 0;
+          const int nqp = j >= 1 ? min(G, nb - (j - 1) * G) : 0;
+          // Z' block i of round j - 1: the own tile from the staging slot, the others'
+          // from the weight ring, in this CTA's block order
+          auto z_block = [&](int i) {
+            const bool own = p2c_block((int)rank, nqp, i) == (int)rank;
+            int sw = -1;
+            if (own) {
+              // the staged tile of this round is written (tiles without a chunk are
+              // still consumed, so that the staging slot is released in order)
+              if (!mbar_wait(wfull, ow & 1, abort)) {
+                ok = false;
+                return;
+              }
+            } else if (cvalid) {
+              sw = itw % P2I_WSLOTS;
+              if (!mbar_wait(&wrfull[sw], (itw / P2I_WSLOTS) & 1, abort)) {
+                ok = false;
+                return;
+              }
+              ++itw;
+            }
+            tc_fence_after();
+            if (cvalid) {
+              if (first_z && !mbar_wait(zempty, (uc & 1) ^ 1, abort)) {
+                ok = false;
+                return;
+              }
+              tc_fence_after();
+              const uint32_t dZ = tbase + 256u;
+              const uint8_t* wt = own ? stage : wring + sw * SLOT;
+              for (int h = 0; ok && h < 2; ++h) {
+                const int stT = wait_slot();
+                if (!ok) break;
+                tc_fence_after();
+                const uint64_t dP = desc_sw128(wt + h * 16384);
+                const uint64_t dT = desc_sw128(smem + stT * SLOT);
+#pragma unroll
+                for (int k4 = 0; k4 < 4; ++k4)
+                  mma_bf16(dZ, desc_advance(dP, k4), desc_advance(dT, k4), idZ,
+                           (!first_z || h > 0 || k4 > 0) ? 1u : 0u);
+                mma_commit(&empty[stT]);
+                ++it;
+              }
+              if (!ok) return;
+              first_z = false;
+            }
+            if (own) {
+              mma_commit(wfree);
+              ++ow;
+            } else if (cvalid) {
+              mma_commit(&wrempty[sw]);
+            }
+          };
+          int zi = 0;
           if ((int)rank < nq) {
             const int b = sc & 1;
             if (!mbar_wait(&sempty[b], ((sc >> 1) & 1) ^ 1, abort)) {
@@ -1358,65 +1419,15 @@ __global__ void __launch_bounds__(P2S_THREADS, 1)
               mma_commit(&empty[stA]);
               if (NPROD == 3) mma_commit(&empty[stY]);
               ++it;
+              if (kb == a.nk - 1) {
+                mma_commit(&sfull[b]);  // the logits of round j are complete
+                ++sc;
+              }
+              for (; ok && zi < nqp && p2i_zpos(zi, nqp, a.nk) == kb; ++zi) z_block(zi);
             }
             if (!ok) break;
-            mma_commit(&sfull[b]);
-            ++sc;
           }
-          const int nqp = j >= 1 ? min(G, nb - (j - 1) * G) : 0;
-          // same order as the producer: the own tile from the staging slot, the others'
-          // ring slots taken one block ahead
-          int stPs[P2C_MAX_G];
-          if (cvalid && nqp > 0 && p2c_block((int)rank, nqp, 0) != (int)rank) {
-            stPs[0] = wait_slot();
-            ++it;
-          }
-          for (int i = 0; ok && i < nqp; ++i) {
-            if (cvalid && i + 1 < nqp) {
-              stPs[i + 1] = wait_slot();
-              ++it;
-              if (!ok) break;
-            }
-            const bool own = p2c_block((int)rank, nqp, i) == (int)rank;
-            if (own) {
-              // the staged tile of this round is written (tiles without a chunk are
-              // still consumed, so that the staging slot is released in order)
-              if (!mbar_wait(wfull, ow & 1, abort)) {
-                ok = false;
-                break;
-              }
-              tc_fence_after();
-            }
-            if (cvalid) {
-              if (first_z && !mbar_wait(zempty, (uc & 1) ^ 1, abort)) {
-                ok = false;
-                break;
-              }
-              tc_fence_after();
-              const uint32_t dZ = tbase + 256u;
-              const uint8_t* wt = own ? stage : smem + stPs[i] * SLOT;
-              for (int h = 0; ok && h < 2; ++h) {
-                const int stT = wait_slot();
-                if (!ok) break;
-                tc_fence_after();
-                const uint64_t dP = desc_sw128(wt + h * 16384);
-                const uint64_t dT = desc_sw128(smem + stT * SLOT);
-#pragma unroll
-                for (int k4 = 0; k4 < 4; ++k4)
-                  mma_bf16(dZ, desc_advance(dP, k4), desc_advance(dT, k4), idZ,
-                           (!first_z || h > 0 || k4 > 0) ? 1u : 0u);
-                mma_commit(&empty[stT]);
-                ++it;
-              }
-              first_z = false;
-            }
-            if (own) {
-              mma_commit(wfree);
-              ++ow;
-            } else if (cvalid) {
-              mma_commit(&empty[stPs[i]]);
-            }
-          }
+          for (; ok && zi < nqp; ++zi) z_block(zi);
         }
         if (!ok) break;
         if (cvalid) {
@@ -1435,7 +1446,7 @@ __global__ void __launch_bounds__(P2S_THREADS, 1)
     const int q = warp & 3;
     const int row = q * 32 + lane;
     const uint32_t lane_addr = tbase + ((uint32_t)(q * 32) << 16);
-    float2* wobs = (float2*)(stage + SLOT + P2S_BOOK) + q * 32;  // this warp's staging
+    float2* wobs = (float2*)(stage + SLOT + P2I_BOOK) + q * 32;  // this warp's staging
     uint32_t sc = 0, m = 0, uc = 0;
     bool ok = true;
     for (int64_t u = cid; ok && u < total; u += ncl) {
@@ -1554,10 +1565,10 @@ __global__ void __launch_bounds__(P2S_THREADS, 1)
       }
     }
     if (!ok) raise_timeout(abort, status);
-  } else if (lane == 0) {
-    // sender: each staged tile goes to every peer that owns a pixel chunk, into the ring
-    // slot that peer announced for this use of the tile, in the order the announcements
-    // arrive
+  } else if (warp == 6 && lane == 0) {
+    // sender: each staged tile goes to every peer that owns a pixel chunk, into the
+    // weight-ring slot that peer announced for this use of the tile, in the order the
+    // announcements arrive
     uint32_t m = 0;
     bool ok = true;
     for (int64_t u = cid; ok && u < total; u += ncl) {
@@ -1590,8 +1601,8 @@ __global__ void __launch_bounds__(P2S_THREADS, 1)
             const uint32_t v = ld_acquire_cluster_u32(mrow + k);
             if ((v >> 4) == expect) {
               const uint32_t slot = v & 15u;
-              bulk_copy_to_peer(mapa(smem_u32(smem + slot * SLOT), k), stage, 32768,
-                                mapa(smem_u32(&full[slot]), k));
+              bulk_copy_to_peer(mapa(smem_u32(wring + slot * SLOT), k), stage, 32768,
+                                mapa(smem_u32(&wrfull[slot]), k));
               pending &= ~(1u << k);
             }
           }
@@ -1612,6 +1623,66 @@ __global__ void __launch_bounds__(P2S_THREADS, 1)
     }
     bulk_wait0();  // no copy is still landing in a peer when the cluster leaves
     if (!ok) raise_timeout(abort, status);
+  } else if (warp == 7 && lane == 0) {
+    // weight producer: a weight-ring slot for each peer's tile of round j - 1, announced
+    // in that peer's mailbox once the main producer has begun round j (so that it runs at
+    // most about a round ahead, also through units where this CTA owns no pixel chunk)
+    uint32_t itw = 0, g = 0, sent[P2C_MAX_G] = {};
+    bool ok = true;
+    for (int64_t u = cid; ok && u < total; u += ncl) {
+      const int ki = find_inst(ustart, n_inst, u);
+      const TcP2Args& a = insts[ki].p2;
+      const int64_t lu = u - ustart[ki];
+      const int ncg = (a.n_chunks + G - 1) / G;
+      const int per_split = a.n_stiles * ncg;
+      const int split = (int)(lu / per_split), rem = (int)(lu % per_split);
+      const int chunk = (rem % ncg) * G + (int)rank;
+      const bool cvalid = chunk < a.n_chunks;
+      const int jb0 = split * a.iblk_per_split;
+      const int nb = min(a.n_iblk, jb0 + a.iblk_per_split) - jb0;
+      const int rounds = (nb + G - 1) / G;
+      ++g;  // round 0 of the unit multiplies no weight tiles
+      for (int j = 1; ok && j <= rounds; ++j) {
+        ++g;
+        const uint64_t t0 = globaltimer();
+        while (*rstart < g) {
+          if (*abort || globaltimer() - t0 > kWaitTimeoutNs) {
+            ok = false;
+            break;
+          }
+          __nanosleep(64);
+        }
+        if (!ok) break;
+        const int nqp = min(G, nb - (j - 1) * G);
+        for (int i = 0; ok && i < nqp; ++i) {
+          const int kq = p2c_block((int)rank, nqp, i);
+          if (kq == (int)rank) continue;
+          if (!cvalid) {  // not taken, but counted: later tags stay in step
+            ++sent[kq];
+            continue;
+          }
+          const int sw = itw % P2I_WSLOTS;
+          if (!mbar_wait(&wrempty[sw], ((itw / P2I_WSLOTS) & 1) ^ 1, abort)) {
+            ok = false;
+            break;
+          }
+          mbar_expect_tx(&wrfull[sw], 32768);
+          const uint32_t row = sent[kq] % MBOX_DEPTH;
+          const uint32_t tag = (sent[kq] + 1u) & MBOX_TAG_MASK;
+          st_release_cluster_u32(mapa(smem_u32(mbox + row * P2C_MAX_G + rank), kq),
+                                 (tag << 4) | (uint32_t)sw);
+          ++sent[kq];
+          ++itw;
+        }
+      }
+    }
+    if (!ok) {
+      raise_timeout(abort, status);
+      const uint32_t lo = itw > P2I_WSLOTS ? itw - P2I_WSLOTS : 0;
+      int zero = 0;
+      for (uint32_t q = lo; q < itw; ++q)
+        mbar_wait(&wrfull[q % P2I_WSLOTS], (q / P2I_WSLOTS) & 1, (volatile int*)&zero);
+    }
   }
   __syncthreads();
   if (warp == 1) {
@@ -1624,8 +1695,9 @@ __global__ void __launch_bounds__(P2S_THREADS, 1)
 // ring + staging slot + bookkeeping (22 mbarriers, 8 x 16 mailbox, TMEM address, abort
 // flag: 696 of the 768 bytes) + per-warp staging of one 32-observation chunk's
 // (ybar, lse2) (4 x 256 bytes)
-constexpr size_t P2S_SMEM = 1024 + (P2S_SLOTS + 1) * SLOT + P2S_BOOK + 1024;
-static_assert(P2S_SMEM <= 232448, "exceeds the shared memory of one CTA");
+// main ring + weight ring + staging slot + bookkeeping + per-warp (ybar, lse2) staging
+constexpr size_t P2I_SMEM = 1024 + (P2I_SLOTS + P2I_WSLOTS + 1) * SLOT + P2I_BOOK + 1024;
+static_assert(P2I_SMEM <= 232448, "exceeds the shared memory of one CTA");
 
 constexpr size_t P1_SMEM = 1024 + P1_SLOTS * SLOT + 256 + 1024;
 constexpr size_t P2_SMEM = 1024 + P2_SLOTS * SLOT + 2 * SLOT + 256 + 1024;
@@ -1746,28 +1818,31 @@ cudaError_t set_smem(K kernel, size_t bytes) {
 }
 
 // the clustered pass-2 kernels: their shared memory, and clusters above the portable
-// size for the staged form
+// size for the interleaved form
 template <int NPROD>
 cudaError_t set_p2c_attrs() {
   cudaError_t e = set_smem(k_p2c_tc<NPROD>, P2R_SMEM);
-  if (e == cudaSuccess) e = set_smem(k_p2s_tc<NPROD>, P2S_SMEM);
+  if (e == cudaSuccess) e = set_smem(k_p2i_tc<NPROD>, P2I_SMEM);
   if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(k_p2s_tc<NPROD>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+    e = cudaFuncSetAttribute(k_p2i_tc<NPROD>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
   return e;
 }
 
-// The launch shape of the cluster form used for clusters of G: the ring form up to
-// P2R_MAX_G, the staged form above.
+// The cluster form for clusters of G: the ring form up to P2R_MAX_G, the interleaved
+// form above.
+bool p2_ring_form(int G) { return G <= P2R_MAX_G; }
+
+// The launch shape of that form.
 template <int NPROD>
 void p2c_form(int G, const void** fn, int* threads, size_t* smem) {
-  if (G <= P2R_MAX_G) {
+  if (p2_ring_form(G)) {
     *fn = (const void*)k_p2c_tc<NPROD>;
     *threads = TC_THREADS;
     *smem = P2R_SMEM;
   } else {
-    *fn = (const void*)k_p2s_tc<NPROD>;
-    *threads = P2S_THREADS;
-    *smem = P2S_SMEM;
+    *fn = (const void*)k_p2i_tc<NPROD>;
+    *threads = P2I_THREADS;
+    *smem = P2I_SMEM;
   }
 }
 
@@ -2024,9 +2099,9 @@ cudaError_t launch_cluster_p2(int G, const TcInst* d_insts, const int64_t* d_ust
   at[0].val.clusterDim.z = 1;
   cfg.attrs = at;
   cfg.numAttrs = 1;
-  if (G <= P2R_MAX_G)
+  if (p2_ring_form(G))
     return cudaLaunchKernelEx(&cfg, k_p2c_tc<NPROD>, d_insts, d_ustart, n, G, status);
-  return cudaLaunchKernelEx(&cfg, k_p2s_tc<NPROD>, d_insts, d_ustart, n, G, status);
+  return cudaLaunchKernelEx(&cfg, k_p2i_tc<NPROD>, d_insts, d_ustart, n, G, status);
 }
 
 template <int NPROD>
@@ -2069,14 +2144,14 @@ template int max_clusters_p2<3>(int, int);
 // of G chunks, and G trades that recompute against the cost of a round and how many
 // clusters of G co-reside (GPC packing).  A cluster round takes about a * NPROD * l2 (the
 // logits of the CTA's own block) + b * G (one weight tile handed over per member), with
-// a = 2.93 ns and b = 4.3 us (ring form, G <= 4) or 4.0 us (staged form), fitted to
-// measured pass-2 times of both forms (L = 72..128, K = 2, G = 3..16); the busiest
+// a = 2.93 ns and b = 4.3 us (ring form, G <= 4) or 3.3 us (interleaved form), fitted
+// to measured pass-2 times (L = 72..128, K = 2, G = 3..16); the busiest
 // cluster runs groups * ceil(n_iblk / G) / clusters(G) rounds per shift tile.
 int choose_p2_cluster(int chunks, int l2, int64_t n_iblk, int prec, int num_sms) {
   if (chunks <= 1) return 1;
   if (chunks <= P2R_MAX_G) return chunks;
   const int nprod = prec == SRMRA_BF16X3 ? 3 : 1;
-  constexpr double a_us = 2.93e-3, b_ring_us = 4.3, b_staged_us = 4.0;
+  constexpr double a_us = 2.93e-3, b_ring_us = 4.3, b_inter_us = 3.3;
   int best = P2R_MAX_G;
   double best_cost = 0.0;
   for (int G = 2; G <= P2C_MAX_G && G <= chunks; ++G) {
@@ -2084,7 +2159,7 @@ int choose_p2_cluster(int chunks, int l2, int64_t n_iblk, int prec, int num_sms)
     if (ncl < 1) continue;
     const double groups = (double)((chunks + G - 1) / G);
     const double rounds = groups * (double)((n_iblk + G - 1) / G) / (double)ncl;
-    const double b_us = G <= P2R_MAX_G ? b_ring_us : b_staged_us;
+    const double b_us = G <= P2R_MAX_G ? b_ring_us : b_inter_us;
     const double cost = rounds * (a_us * nprod * l2 + b_us * G);
     if (best_cost == 0.0 || cost < best_cost) {
       best = G;

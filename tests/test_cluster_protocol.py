@@ -1,12 +1,15 @@
 """Host-side models of the synchronisation of the clustered tensor-core pass 2, in its
 two forms.
 
-Staged form (clusters of 5 to 16).  Each CTA of a cluster of G runs four roles:
-- a producer that reserves slots of a 6-deep shared-memory ring, for TMA tiles and for
-  the weight tiles the other CTAs send it, and announces each weight slot in the
-  sender's mailbox (an 8-row table of tagged entries, one row per use of a tile);
-- an MMA issuer that consumes the ring in the same order, and its own weight tile from a
-  staging slot;
+Interleaved form (clusters of 5 to 16).  Each CTA of a cluster of G runs five roles:
+- a producer that fills a 4-slot main ring with the logit operands of its own block and
+  the Y'^T tiles of its chunk, in the MMA's order: the Z' blocks of round j - 1 between
+  the logit k-blocks of round j;
+- a weight producer that reserves slots of a 2-slot weight ring for the peers' tiles and
+  announces each in the tile owner's mailbox (an 8-row table of tagged entries, one row
+  per use of a tile), once the main producer has begun the round;
+- an MMA issuer that consumes both rings in the same orders, and its own weight tile from
+  a staging slot;
 - an epilogue that turns the logits of its own observation block into the staged
   weight tile, once the previous tile has been consumed and copied;
 - a sender that copies the staged tile into each chunk-owning peer's announced slot as
@@ -14,11 +17,11 @@ Staged form (clusters of 5 to 16).  Each CTA of a cluster of G runs four roles:
 
 A CTA takes the blocks of a round in its own order: its own block first, then the next
 ranks cyclically.  The model runs the roles as coroutines under random schedules, with
-the kernel's order, and reports a deadlock when no role can move, or a mailbox race when
-a sender finds a row already overwritten by a later use.  It checks the kernel's order,
-and that the model catches a weight slot reserved two blocks ahead (a deadlock in a
-6-slot ring), a mailbox too shallow to hold the announcements in flight, and skipped
-uses left uncounted.
+the kernel's orders, and reports a deadlock when no role can move, or a mailbox race when
+a sender finds a row already overwritten by a later use.  It checks the kernel's orders,
+with chunk ownership fixed and changing from unit to unit, and that the model catches a
+weight producer that is not held to the main producer's round, a mailbox too shallow
+for the announcements in flight, and skipped uses left uncounted.
 
 Ring form (clusters up to 4).  Every weight tile, the owner's included, goes through a
 7-slot ring; each producer reserves a slot for every tile of the round in block order
@@ -30,7 +33,7 @@ import random
 
 import pytest
 
-SLOTS, RING_SLOTS, MBOX = 6, 7, 8
+MAIN_SLOTS, W_SLOTS, RING_SLOTS, MBOX = 4, 2, 7, 8
 
 
 class MailboxRace(Exception):
@@ -42,80 +45,112 @@ def block_order(r, n):
     return [(r % n + i) % n for i in range(n)] if n else []
 
 
-def run_staged(G, units, seed=0, nk=8, cvalid=None, mbox=MBOX, lookahead=1, count_skipped=True):
-    """units: observation blocks per work unit (every CTA of the cluster walks the same
-    units).  cvalid: which CTAs own a pixel chunk, one pattern for all units or a list of
-    patterns cycled over the units (ownership changes with the unit's chunk group).
-    lookahead: how many blocks ahead a weight slot is reserved (the kernel: 1).
-    count_skipped: a CTA without a chunk still counts the uses of the peers' tiles it
-    does not take (the kernel does).  Returns True when every role finishes, False on a
-    deadlock."""
+def zpos(i, nqp, nk):
+    """k-block of round j after which Z' block i of round j - 1 is issued."""
+    return ((i + 1) * nk) // (nqp + 1) - 1 if nk >= nqp + 1 else nk - 1
+
+
+def run_interleaved(G, units, seed=0, nk=8, cvalid=None, mslots=MAIN_SLOTS, wslots=W_SLOTS,
+                    mbox=MBOX, count_skipped=True, gate=True):
+    """The interleaved form (clusters of 5 to 16).  units: observation blocks per work unit
+    (every CTA of the cluster walks the same units).  cvalid: which CTAs own a pixel chunk,
+    one pattern for all units or a list of patterns cycled over the units.  gate: the
+    weight producer announces the slots of round j - 1 only once the main producer has
+    begun round j (the kernel does).  count_skipped: a CTA without a chunk still counts
+    the uses of the peers' tiles it does not take (the kernel does).  Returns True when
+    every role finishes, False on a deadlock."""
     rnd = random.Random(seed)
-    st = [dict(free=[0] * SLOTS, full=[0] * SLOTS, sfull=[0, 0], sempty=[0, 0], zfull=0,
-               zempty=0, wfull=0, wfree=0, cdone=0, mbox=[[(0, 0)] * G for _ in range(mbox)])
-          for _ in range(G)]
+    st = [dict(free_m=[0] * mslots, full_m=[0] * mslots, free_w=[0] * wslots, full_w=[0] * wslots,
+               sfull=[0, 0], sempty=[0, 0], zfull=0, zempty=0, wfull=0, wfree=0, cdone=0,
+               rstart=0,
+               mbox=[[(0, 0)] * G for _ in range(mbox)]) for _ in range(G)]
     pats = [[True] * G] if cvalid is None else (
         cvalid if isinstance(cvalid[0], (list, tuple)) else [cvalid])
 
-    def valid_in(u):  # ownership pattern of unit u
+    def valid_in(u):
         return pats[u % len(pats)]
 
     def own_rounds(r, nb):
         return [r0 for r0 in range(0, nb, G) if r < min(G, nb - r0)]
 
+    def schedule(r, nb, j):
+        """The main-ring sequence of round j: ('L', kb) logit k-blocks, ('Z', i) Z blocks."""
+        rounds = -(-nb // G)
+        nq = min(G, nb - j * G) if j < rounds else 0
+        nqp = min(G, nb - (j - 1) * G) if j >= 1 else 0
+        seq = []
+        done = 0
+        if r < nq:
+            for kb in range(nk):
+                seq.append(('L', kb))
+                while done < nqp and zpos(done, nqp, nk) == kb:
+                    seq.append(('Z', done))
+                    done += 1
+        while done < nqp:
+            seq.append(('Z', done))
+            done += 1
+        return seq, nq, nqp
+
     def producer(r):
         it = 0
-        sent = [0] * G
 
-        def reserve():
+        def fill():
             nonlocal it
-            s, need = it % SLOTS, it // SLOTS
-            yield lambda: st[r]["free"][s] >= need
+            s, need = it % mslots, it // mslots
+            yield lambda: st[r]["free_m"][s] >= need
             it += 1
-            return s
-
-        def reserve_w(kq):  # a slot for CTA kq's weight tile, announced in its mailbox
-            s = yield from reserve()
-            row = sent[kq] % mbox
-            st[kq]["mbox"][row] = (st[kq]["mbox"][row][:r] + [(sent[kq] + 1, s)]
-                                   + st[kq]["mbox"][row][r + 1:])
-            sent[kq] += 1
-
-        def tile():  # a TMA tile: it lands at once
-            s = yield from reserve()
-            st[r]["full"][s] += 1
+            st[r]["full_m"][s] += 1
 
         for u, nb in enumerate(units):
             valid = valid_in(u)
             rounds = -(-nb // G)
             for j in range(rounds + 1):
-                nq = min(G, nb - j * G) if j < rounds else 0
-                if r < nq:
-                    for _ in range(2 * nk):  # logits: (A hi+lo, Y hi+lo) per k-block
-                        yield from tile()
-                ks = block_order(r, min(G, nb - (j - 1) * G) if j >= 1 else 0)
-                if not valid[r]:
-                    if count_skipped:
-                        for kq in ks:
-                            if kq != r:
-                                sent[kq] += 1
-                    continue
-                for i in range(min(lookahead, len(ks))):
-                    if ks[i] != r:
-                        yield from reserve_w(ks[i])
-                for i in range(len(ks)):
-                    if i + lookahead < len(ks) and ks[i + lookahead] != r:
-                        yield from reserve_w(ks[i + lookahead])
-                    yield from tile()
-                    yield from tile()
+                seq, nq, nqp = schedule(r, nb, j)
+                st[r]["rstart"] += 1  # round (u, j) started
+                for kind, _ in seq:
+                    if kind == 'L':
+                        yield from fill()
+                        yield from fill()
+                    elif valid[r]:
+                        yield from fill()
+                        yield from fill()
+
+    def wprod(r):
+        itw = 0
+        sent = [0] * G
+        g = 0  # rounds (u, j) passed, in the producer's count
+        for u, nb in enumerate(units):
+            valid = valid_in(u)
+            rounds = -(-nb // G)
+            g += 1  # round j = 0 of the unit carries no Z' blocks
+            for j in range(1, rounds + 1):
+                g += 1
+                if gate:
+                    yield lambda g=g: st[r]["rstart"] >= g
+                nqp = min(G, nb - (j - 1) * G)
+                ks = block_order(r, nqp)
+                for kq in ks:
+                    if kq == r:
+                        continue
+                    if not valid[r]:
+                        if count_skipped:
+                            sent[kq] += 1
+                        continue
+                    s, need = itw % wslots, itw // wslots
+                    yield lambda s=s, need=need: st[r]["free_w"][s] >= need
+                    itw += 1
+                    row = sent[kq] % mbox
+                    st[kq]["mbox"][row] = (st[kq]["mbox"][row][:r] + [(sent[kq] + 1, s)]
+                                           + st[kq]["mbox"][row][r + 1:])
+                    sent[kq] += 1
 
     def mma(r):
-        it = sc = uc = ow = 0
+        it = itw = sc = uc = ow = 0
 
-        def wait_slot():
+        def take_m():
             nonlocal it
-            s, need = it % SLOTS, it // SLOTS + 1
-            yield lambda: st[r]["full"][s] >= need
+            s, need = it % mslots, it // mslots + 1
+            yield lambda: st[r]["full_m"][s] >= need
             it += 1
             return s
 
@@ -124,37 +159,40 @@ def run_staged(G, units, seed=0, nk=8, cvalid=None, mbox=MBOX, lookahead=1, coun
             rounds = -(-nb // G)
             first = True
             for j in range(rounds + 1):
-                nq = min(G, nb - j * G) if j < rounds else 0
+                seq, nq, nqp = schedule(r, nb, j)
+                ks = block_order(r, nqp)
                 if r < nq:
                     b, need = sc & 1, sc >> 1
                     yield lambda b=b, need=need: st[r]["sempty"][b] >= need
-                    for _ in range(2 * nk):
-                        s = yield from wait_slot()
-                        st[r]["free"][s] += 1
-                    st[r]["sfull"][b] += 1
-                    sc += 1
-                ks = block_order(r, min(G, nb - (j - 1) * G) if j >= 1 else 0)
-                stP = {}
-                for i in range(min(lookahead, len(ks))):
-                    if valid[r] and ks[i] != r:
-                        stP[i] = yield from wait_slot()
-                for i, kq in enumerate(ks):
-                    if valid[r] and i + lookahead < len(ks) and ks[i + lookahead] != r:
-                        stP[i + lookahead] = yield from wait_slot()
+                for kind, idx in seq:
+                    if kind == 'L':
+                        for _ in range(2):
+                            s = yield from take_m()
+                            st[r]["free_m"][s] += 1
+                        if idx == nk - 1:
+                            st[r]["sfull"][sc & 1] += 1
+                            sc += 1
+                        continue
+                    kq = ks[idx]
+                    sw = None
                     if kq == r:
                         yield lambda o=ow: st[r]["wfull"] >= o + 1
+                    elif valid[r]:
+                        sw, need = itw % wslots, itw // wslots + 1
+                        yield lambda sw=sw, need=need: st[r]["full_w"][sw] >= need
+                        itw += 1
                     if valid[r]:
                         if first:
                             yield lambda u=uc: st[r]["zempty"] >= u
                         for _ in range(2):
-                            t = yield from wait_slot()
-                            st[r]["free"][t] += 1
+                            s = yield from take_m()
+                            st[r]["free_m"][s] += 1
                         first = False
                     if kq == r:
                         st[r]["wfree"] += 1
                         ow += 1
                     elif valid[r]:
-                        st[r]["free"][stP[i]] += 1
+                        st[r]["free_w"][sw] += 1
             if valid[r]:
                 st[r]["zfull"] += 1
                 uc += 1
@@ -166,10 +204,10 @@ def run_staged(G, units, seed=0, nk=8, cvalid=None, mbox=MBOX, lookahead=1, coun
             for _ in own_rounds(r, nb):
                 b, need = sc & 1, (sc >> 1) + 1
                 yield lambda b=b, need=need: st[r]["sfull"][b] >= need
-                st[r]["sempty"][b] += 1  # weights computed; logits released
+                st[r]["sempty"][b] += 1
                 sc += 1
                 yield lambda m=m: st[r]["wfree"] >= m and st[r]["cdone"] >= m
-                st[r]["wfull"] += 1  # the tile is staged
+                st[r]["wfull"] += 1
                 m += 1
             if valid[r]:
                 yield lambda u=uc: st[r]["zfull"] >= u + 1
@@ -197,14 +235,14 @@ def run_staged(G, units, seed=0, nk=8, cvalid=None, mbox=MBOX, lookahead=1, coun
                 while pending:
                     yield lambda: bool(announced())
                     for k, s in announced():
-                        st[k]["full"][s] += 1  # the copy lands in the peer's slot
+                        st[k]["full_w"][s] += 1
                         pending.discard(k)
                 st[r]["cdone"] += 1
                 m += 1
 
     roles = []
     for r in range(G):
-        for f in (producer, mma, epilogue, sender):
+        for f in (producer, wprod, mma, epilogue, sender):
             g = f(r)
             roles.append([g, next(g, None)])
     while True:
@@ -216,6 +254,7 @@ def run_staged(G, units, seed=0, nk=8, cvalid=None, mbox=MBOX, lookahead=1, coun
             return False
         ro = rnd.choice(ready)
         ro[1] = next(ro[0], None)
+
 
 
 def run_ring(G, units, order, seed=0, nk=16, cvalid=None, mbox=MBOX):
@@ -392,36 +431,47 @@ def test_block_order():
 
 
 @pytest.mark.parametrize("G", [5, 6, 7, 8, 9, 12, 13, 16])
-def test_staged_form_order_never_deadlocks(G):
+def test_interleaved_form_order_never_deadlocks(G):
     for units in UNITS:
         for cvalid in cvalid_patterns(G):
-            for seed in range(3):
-                assert run_staged(G, units, seed=seed, cvalid=cvalid, nk=8), (units, cvalid)
+            for seed in range(2):
+                assert run_interleaved(G, units, seed=seed, cvalid=cvalid, nk=8), \
+                    (units, cvalid)
 
 
-def test_staged_model_catches_a_shallow_mailbox():
-    """With a single mailbox row, a producer's announcement for the next use of a tile
-    overwrites the row before the sender has read it."""
+def test_interleaved_form_with_few_k_blocks():
+    """Fewer k-blocks than Z' blocks per round: all Z' blocks after the last k-block."""
+    for G in (5, 9):
+        for units in ([12] * 3, [7, 1, 9]):
+            assert run_interleaved(G, units, nk=2, cvalid=cvalid_patterns(G)[4])
+
+
+def test_interleaved_model_catches_an_ungated_weight_producer():
+    """Without the gate, the weight producer runs through a unit where its CTA owns no
+    chunk (counting, not taking, the peers' tiles) and announces a later use into a
+    mailbox row the peer's sender has not read yet."""
     with pytest.raises(MailboxRace):
-        for seed in range(4):
-            run_staged(2, [24] * 4, seed=seed, nk=1, mbox=1)
+        for seed in range(2):
+            run_interleaved(2, [13] * 3, seed=seed, cvalid=[[True, True], [True, False]],
+                            gate=False)
 
 
-def test_staged_model_catches_uncounted_skipped_uses():
-    """A CTA without a pixel chunk takes none of the peers' tiles; if it did not count
-    those uses, its later announcements would carry stale tags and the senders would
+def test_interleaved_model_catches_a_shallow_mailbox():
+    """With 3 mailbox rows a weight producer's announcement can overwrite a row whose
+    use the sender has not reached (the kernel has 8)."""
+    with pytest.raises(MailboxRace):
+        for seed in range(2):
+            run_interleaved(2, [1] * 10, seed=seed, nk=4, mbox=3,
+                            cvalid=[[True, False], [True, True], [True, False]])
+
+
+def test_interleaved_model_catches_uncounted_skipped_uses():
+    """Uncounted skipped uses leave later announcements with stale tags: the senders
     wait for them forever."""
     G = 4
     half = [True, True, False, False]
-    assert not run_staged(G, [8, 8, 8], cvalid=[[True] * G, half], count_skipped=False)
-    assert run_staged(G, [8, 8, 8], cvalid=[[True] * G, half])
-
-
-def test_staged_model_catches_a_weight_slot_two_blocks_ahead():
-    """Reserving weight slots two blocks ahead puts a Y'^T tile 7 places after its weight
-    slot, which a 6-slot ring cannot hold: the fill waits for the slot that only its own
-    products free."""
-    assert not any(run_staged(4, [24] * 2, seed=s, lookahead=2) for s in range(3))
+    assert not run_interleaved(G, [8, 8, 8], cvalid=[[True] * G, half], count_skipped=False)
+    assert run_interleaved(G, [8, 8, 8], cvalid=[[True] * G, half])
 
 
 @pytest.mark.parametrize("G", [2, 3, 4])
