@@ -7,6 +7,14 @@ shift pairs per second, N * L^2 * steps / device time.  Prints one JSON line.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl srmra|reference]
                     [--workload NAME] [--prec fp32|bf16|bf16x3|fft32]
+    python bench.py --study precision [--study-iters 40]   (per-iteration errors)
+
+The default workload is the largest single-GPU one: L = 96, K = 3 (l = 32), N = 5e4,
+sigma = 0.2, timed in the float32 form.  Beside the headline the line carries, for the
+same workload, the tensor-core forms (bf16x3, bf16) with their speedup over float32
+and their error against the FP64 oracle after one iteration from a common state; the
+same for sigma = 1.0; the projected-EM workload L = 64, K = 2, N = 1e4; 64 uneven
+problems in grouped launches; and a short serving trace.
 
 Under torchrun (N > 1) every rank runs an independent replica of the workload (its own
 seeded instance): the method has no data exchange between independent problems, so
@@ -28,7 +36,10 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "E+M obs x shift pairs/s"
-DEFAULT_WORKLOAD = "proj_em_L64_K2_N1e4"
+DEFAULT_WORKLOAD = "precision_L96_K3_N5e4_s0.2"
+# the second noise level of the precision workload, reported beside the first
+COMPANION = {"precision_L96_K3_N5e4_s0.2": "precision_L96_K3_N5e4_s1.0"}
+SECONDARY = "proj_em_L64_K2_N1e4"
 
 
 def parse():
@@ -50,7 +61,15 @@ def parse():
     ap.add_argument("--rates", default=None,
                     help="serve: comma-separated arrival rates per second (a sweep)")
     ap.add_argument("--no-mixed", action="store_true",
-                    help="skip the bf16x3-vs-fp32 comparison block")
+                    help="skip the blocks beside the headline (other forms, workloads)")
+    ap.add_argument("--no-extra", action="store_true",
+                    help="keep the other forms of the workload, skip the other workloads")
+    ap.add_argument("--oracle-threads", type=int, default=0,
+                    help="threads of the FFT oracle error checks (0 = all host cores)")
+    ap.add_argument("--study", default=None, choices=[None, "precision"],
+                    help="precision: per-iteration one-step errors of every form against "
+                         "the FP64 oracle over a projected run")
+    ap.add_argument("--study-iters", type=int, default=40)
     return ap.parse_args()
 
 
@@ -76,10 +95,12 @@ def fp32_peak_tflops(sm_mhz: float) -> float:
 KERNEL_SOURCE = {"fp32": "k_simt.cu", "bf16": "k_tc.cu", "bf16x3": "k_tc.cu", "fft32": "k_fft.cu"}
 
 
-def traffic_from_profiles(kernel: str, workload: str, prec: str):
-    """DRAM bytes per launch recorded from an ncu capture in profiles/traffic.txt, or
-    None.  Lines: `traffic <kernel> <workload> <bytes_per_launch> <source sha1 prefix>`;
-    a line counts only while the kernel's source file still has that hash."""
+def profile_record(field: str, kernel: str, workload: str, prec: str):
+    """A per-launch figure recorded from an ncu capture in profiles/traffic.txt, or None.
+    Lines: `<field> <kernel> <workload> <value> <source sha1 prefix>`, field `traffic`
+    (DRAM bytes per launch) or `tensor` (sm__pipe_tensor_cycles_active, fraction of
+    elapsed cycles); a line counts only while the kernel's source file still has that
+    hash."""
     import hashlib
     path = os.path.join(ROOT, "profiles", "traffic.txt")
     src = os.path.join(ROOT, "paper_2204_04754_gb300", "csrc", KERNEL_SOURCE[prec])
@@ -90,7 +111,7 @@ def traffic_from_profiles(kernel: str, workload: str, prec: str):
     with open(path) as f:
         for line in f:
             parts = line.split()
-            if len(parts) == 5 and parts[0] == "traffic" and parts[1] == kernel \
+            if len(parts) == 5 and parts[0] == field and parts[1] == kernel \
                     and parts[2] == workload and digest.startswith(parts[4]):
                 return float(parts[3])
     return None
@@ -150,10 +171,14 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+def gpu_index(local: int) -> int:
+    vis = os.environ.get("CUDA_VISIBLE_DEVICES", "").split(",")[0]
+    return int(vis) if vis.isdigit() else local
+
+
 def cpu_oracle_rate(problem, budget_s: float, n_sub: int | None = None):
     """Time the FP64 oracle (as it stands) on a bounded sample of the workload: one EM
     iteration over the first n_sub observations, repeated for ~budget_s seconds."""
-    import numpy as np
     from oracle import srmra_oracle as O
     p = problem
     if n_sub is None:
@@ -171,7 +196,6 @@ def cpu_oracle_rate(problem, budget_s: float, n_sub: int | None = None):
         if el >= budget_s or reps >= 50:
             break
     pairs = n_sub * p.L * p.L * reps
-    _ = np
     return {"value": pairs / el, "unit": "pairs/s", "cores": os.cpu_count(), "kind": "oracle",
             "sample": f"{reps} dense FP64 oracle EM iteration(s) over the first {n_sub} of "
                       f"{p.N} observations (all {p.L * p.L} shifts), {el:.1f} s",
@@ -248,40 +272,212 @@ def time_steps(run_step, steps, stream, torch, flush):
     return [a.elapsed_time(b) for a, b in evs]
 
 
-def mixed_block(p, w, steps, warmup, srmra, torch, stream, flush, fp32_value, form="bf16x3"):
-    """The same workload in another form (split-bf16 tensor cores, or the polyphase FFT):
-    pairs/s and speedup over the fp32 form; and the error at which that speedup holds:
-    one EM iteration of each form from the same state (the fp32 run's state after the
-    warm-up), compared."""
-    import numpy as np
-    s3 = srmra.Solver(p.L, p.K, p.sigma, p.y, prec=form, x0=p.x0, rho1=p.rho1_0,
-                      rho2=p.rho2_0, stream=stream.cuda_stream)
-    s3.solve(warmup, w["F"], sigma_bm1=1.0, loglik=False)
-    ms = time_steps(lambda: s3.solve(1, w["F"], sigma_bm1=0.0, loglik=False), steps,
-                    stream, torch, flush)
-    s1 = srmra.Solver(p.L, p.K, p.sigma, p.y, prec="fp32", x0=p.x0, rho1=p.rho1_0,
-                      rho2=p.rho2_0, stream=stream.cuda_stream)
-    s1.solve(warmup, w["F"], sigma_bm1=1.0, loglik=False)
-    st = s1.state()
-    s3.set_state(*st)
-    s1.em_iter(1, loglik=False)
-    s3.em_iter(1, loglik=False)
-    (x1, r11, r21, _, _), (x3, r13, r23, _, _) = s1.state(), s3.state()
-    s1.close()
-    s3.close()
-    value = p.N * p.L * p.L * steps / (sum(ms) / 1e3)
-    rel = lambda a, b: float(np.linalg.norm(a.astype(np.float64) - b) / np.linalg.norm(b))
-    note = {"bf16x3": "per-iteration parity with the FP64 oracle (<= 1e-4) is tested in "
-                      "tests/test_gpu_tc.py",
-            "fft32": "exact reformulation (polyphase correlation by l x l FFTs) in float32; "
-                     "per-iteration parity with the FP64 oracle (<= 1e-5) is tested in "
-                     "tests/test_gpu_fft.py"}[form]
-    return {"precision": form, "value": value, "unit": "pairs/s",
-            "ms_per_step": sum(ms) / steps, "speedup_vs_fp32": value / fp32_value,
-            "one_step_rel_diff_vs_fp32": {"x": rel(x3, x1), "rho1": rel(r13, r11),
-                                          "rho2": rel(r23, r21)},
-            "note": note}
+# ------------------------------------------------------------------- work accounting
 
+def padded(p):
+    """Padded sizes the kernels execute over: (Npad, Spad, ldk, pixel chunks)."""
+    l2 = p.l * p.l
+    return (-(-p.N // 128) * 128, -(-(p.L * p.L) // 256) * 256, -(-l2 // 64) * 64,
+            -(-l2 // 256))
+
+
+def kernel_names(prec: str, plan: dict, l: int):
+    """The pass-1 and pass-2 kernels as they are launched."""
+    if prec == "fp32":
+        return "k_p1_f32", "k_p2_f32"
+    if prec == "fft32":
+        return f"k_fft_p1<{l}>", f"k_fft_p2<{l}>"
+    n = 3 if prec == "bf16x3" else 1
+    p2 = {"per_chunk": "k_p2_tc", "ring": "k_p2c_tc", "interleaved": "k_p2i_tc"}[plan["p2_form"]]
+    return f"k_p1_tc<{n}>", f"{p2}<{n}>"
+
+
+def tc_executed_flops(p, prec: str, plan: dict):
+    """Tensor-core flops the two passes issue per launch (padding included): pass 1 NPROD
+    MMAs per logit tile; pass 2 the same logits once per chunk group plus the fp16 M-step
+    product Z' = W^T Y' over every 256-pixel chunk."""
+    nprod = 3 if prec == "bf16x3" else 1
+    Npad, Spad, ldk, nch = padded(p)
+    p1 = nprod * 2.0 * Npad * Spad * ldk
+    p2 = nprod * 2.0 * Spad * Npad * ldk * plan["p2_chunk_groups"] + 2.0 * Spad * Npad * nch * 256
+    return p1, p2
+
+
+def roofline_of(p, prec: str, plan: dict, workload: str, phase_ms: dict, phase_n: dict):
+    """Roofline of the dominant pass: algorithmic flops (Sec. 2 E- and M-step: 2 l^2 per
+    pair for the logits of pass 1; 4 l^2 for pass 2, the logit recompute plus the M-step
+    sum) over its average CUDA-event launch time, against the FP32 FFMA peak (float32 and
+    FFT forms) or the sustained bf16 tensor peak (tensor-core forms).  Tensor-core forms
+    add the executed tensor flops (padding and recompute included) of each pass and of
+    the two passes together, time-weighted."""
+    peaks, src = load_peaks()
+    dom = max(("pass1", "pass2"), key=lambda k: phase_ms[k])
+    l2 = p.l * p.l
+    pairs = p.N * p.L * p.L
+    if prec == "fft32":
+        lg = math.log2(l2)
+        per_pair = {"pass1": 5 * lg + 6, "pass2": 10 * lg + 14}[dom]
+    else:
+        per_pair = {"pass1": 2 * l2, "pass2": 4 * l2}[dom]
+    t_ms = {k: phase_ms[k] / max(1, phase_n[k]) for k in ("pass1", "pass2")}
+    k1, k2 = kernel_names(prec, plan, p.l)
+    kern = {"pass1": k1, "pass2": k2}[dom]
+    achieved = per_pair * pairs / (t_ms[dom] / 1e3) / 1e12
+    if prec in ("fp32", "fft32"):
+        sm_max = float(peaks.get("sm_max_mhz", 2070.0))
+        peak = fp32_peak_tflops(sm_max)
+        bound = "alu"
+        note = (f"FP32 FFMA peak derived: {NUM_SMS} SMs x {FP32_LANES_PER_SM} lanes x 2 "
+                f"flops x {sm_max:.0f} MHz (max SM clock, {src} peaks file)")
+    else:
+        peak = float(peaks["bf16_tflops_sustained"])
+        bound = "tensor"
+        note = f"dense bf16, sustained, of {src}"
+    traffic = profile_record("traffic", kern, workload, prec)
+    roof = {"bound": bound, "kernel": kern, "achieved": achieved, "peak": peak,
+            "unit": "TFLOP/s", "frac": achieved / peak, "traffic": traffic,
+            "algorithmic_flops_per_launch": per_pair * pairs, "avg_launch_ms": t_ms[dom],
+            "peak_source": note}
+    if traffic:
+        hbm = float(peaks["hbm_gbs"])
+        roof["dram_gbs"] = traffic / (t_ms[dom] / 1e3) / 1e9
+        roof["dram_frac_of_hbm_peak"] = roof["dram_gbs"] / hbm
+    if bound == "tensor":
+        e1, e2 = tc_executed_flops(p, prec, plan)
+        ex = {"pass1": e1, "pass2": e2}
+        roof["executed_flops_per_launch"] = ex[dom]
+        roof["executed_tflops"] = ex[dom] / (t_ms[dom] / 1e3) / 1e12
+        roof["executed_frac"] = roof["executed_tflops"] / peak
+        both = t_ms["pass1"] + t_ms["pass2"]
+        roof["passes"] = {
+            "pass1": {"kernel": k1, "ms": t_ms["pass1"],
+                      "executed_frac": e1 / (t_ms["pass1"] / 1e3) / 1e12 / peak,
+                      "algorithmic_frac": 2 * l2 * pairs / (t_ms["pass1"] / 1e3) / 1e12 / peak},
+            "pass2": {"kernel": k2, "ms": t_ms["pass2"],
+                      "executed_frac": e2 / (t_ms["pass2"] / 1e3) / 1e12 / peak,
+                      "algorithmic_frac": 4 * l2 * pairs / (t_ms["pass2"] / 1e3) / 1e12 / peak},
+            "both_time_weighted": {"ms": both,
+                                   "executed_frac": (e1 + e2) / (both / 1e3) / 1e12 / peak,
+                                   "algorithmic_frac": 4 * l2 * pairs / (both / 1e3) / 1e12 / peak}}
+        tp = profile_record("tensor", kern, workload, prec)
+        if tp is not None:
+            roof["ncu_tensor_pipe_active"] = tp
+        roof["algorithmic_frac_of_burst_peak"] = achieved / float(peaks["bf16_tflops"])
+    return roof
+
+
+# ------------------------------------------------------------------- one form, timed
+
+class FormRun:
+    """One precision form of a workload on the GPU: a context created from device-
+    resident observations, warmed up (Algorithm 2's sigma_BM schedule started at 1), then
+    `steps` projected-EM iterations timed with CUDA events (L2 flushed before each)."""
+
+    def __init__(self, p, w, workload, prec, steps, warmup, srmra, torch, stream, flush,
+                 clocks=False, local=0):
+        self.p, self.prec = p, prec
+        y = torch.from_numpy(p.y).cuda()
+        self.s = srmra.Solver(p.L, p.K, p.sigma, y, prec=prec, x0=p.x0, rho1=p.rho1_0,
+                              rho2=p.rho2_0, stream=stream.cuda_stream)
+        del y
+        F = w["F"]
+        self.s.solve(warmup, F, sigma_bm1=1.0, loglik=False)
+        self.s.profile(True)
+        self.s.profile_read()
+        torch.cuda.synchronize()
+        l0 = self.s.launches
+        cs = ClockSampler(gpu_index(local)) if clocks else None
+        if cs:
+            cs.start()
+        self.step_ms = time_steps(lambda: self.s.solve(1, F, sigma_bm1=0.0, loglik=False),
+                                  steps, stream, torch, flush)
+        self.clocks = cs.stop() if cs else None
+        self.launches = self.s.launches - l0
+        ms, n = self.s.profile_read()
+        self.s.profile(False)
+        from paper_2204_04754_gb300.srmra import PHASES
+        self.phase_ms = {k: float(ms[i]) for i, k in enumerate(PHASES)}
+        self.phase_n = {k: int(n[i]) for i, k in enumerate(PHASES)}
+        self.steps = steps
+        self.total_ms = float(sum(self.step_ms))
+        self.value = p.N * p.L * p.L * steps / (self.total_ms / 1e3)
+        self.plan = self.s.plan()
+        self.roof = roofline_of(p, prec, self.plan, workload, self.phase_ms, self.phase_n)
+
+    def summary(self, fp32_value=None):
+        d = {"precision": self.prec, "value": self.value, "unit": "pairs/s",
+             "ms_per_step": self.total_ms / self.steps,
+             "phases_ms_per_step": {k: v / self.steps for k, v in self.phase_ms.items()},
+             "plan": self.plan, "roofline": self.roof, "gpu_launches": self.launches}
+        if fp32_value:
+            d["speedup_vs_fp32"] = self.value / fp32_value
+        return d
+
+    def close(self):
+        self.s.close()
+
+
+def rel(a, b):
+    import numpy as np
+    a = np.asarray(a, np.float64)
+    b = np.asarray(b, np.float64)
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+def errors_vs_oracle(p, runs, threads):
+    """One EM iteration of every form from one common state (the first run's current
+    estimate), each compared with the FP64 FFT oracle's iteration from the same state:
+    relative 2-norm errors of x, rho1, rho2, |dLL| / |LL|, and the largest |d lse_i| /
+    |lse_i| (and the same over ||y_i||^2 / (2 sigma^2) + |lse_i| + 1, the scale of the
+    terms that cancel in lse_i)."""
+    import numpy as np
+    from oracle import fft_oracle as FO
+    x, r1, r2, sbm, t = runs[0].s.state()
+    t0 = time.perf_counter()
+    xo, r1o, r2o, llo, aux = FO.em_iter_fft(p.y, x, r1, r2, p.sigma, p.K, workers=threads)
+    oracle_s = time.perf_counter() - t0
+    yscale = (p.y.astype(np.float64) ** 2).sum(axis=(1, 2)) / (2 * p.sigma ** 2)
+    out = {}
+    for r in runs:
+        r.s.set_state(x, r1, r2, sbm, t)
+        ll = r.s.em_iter(1)[0]
+        lse, _ = r.s.estep()
+        xg, r1g, r2g, _, _ = r.s.state()
+        out[r.prec] = {
+            "x": rel(xg, xo), "rho1": rel(r1g, r1o), "rho2": rel(r2g, r2o),
+            "LL": abs(ll - llo) / abs(llo),
+            "lse_max_rel": float(np.max(np.abs(lse - aux["lse"]) / np.abs(aux["lse"]))),
+            "lse_max_scaled": float(np.max(np.abs(lse - aux["lse"]) /
+                                           (1.0 + np.abs(aux["lse"]) + yscale)))}
+    return out, {"oracle": "FP64 polyphase-FFT oracle (pinned to the dense definition), all "
+                           f"{p.N} observations, {threads} threads, {oracle_s:.1f} s",
+                 "state": f"the float32 run's estimate after its timed iterations (t = {t})"}
+
+
+def workload_block(name, steps, warmup, srmra, torch, stream, flush, threads, local=0,
+                   forms=("fp32", "bf16x3", "bf16"), clocks=False):
+    """Every form of one workload: timed runs, and errors against the oracle."""
+    from paper_2204_04754_gb300 import synth
+    w = synth.WORKLOADS[name]
+    p = synth.workload_problem(name)
+    runs = [FormRun(p, w, name, f, steps, warmup, srmra, torch, stream, flush,
+                    clocks=(clocks and f == forms[0]), local=local) for f in forms]
+    err, how = errors_vs_oracle(p, runs, threads)
+    base = runs[0].value
+    block = {"workload": name, "L_high": p.L, "K": p.K, "N": p.N, "sigma": p.sigma,
+             "forms": {}, "error_vs_oracle": how}
+    for r in runs:
+        d = r.summary(None if r.prec == forms[0] else base)
+        d["error_vs_oracle"] = err[r.prec]
+        if r.prec != "fp32":
+            worst = max(err[r.prec][k] for k in ("x", "rho1", "rho2", "LL"))
+            d["rel_err_max"] = worst
+            d["within_1e-4"] = bool(worst <= 1e-4)
+        block["forms"][r.prec] = d
+    return p, w, runs, block
+
+
+# ------------------------------------------------------------------- other blocks
 
 def online_block(p, w, steps, warmup, srmra, torch, stream, flush, fp32_value, n_shards=10):
     """Online (mini-batch) EM on the same workload: the observations split into n_shards
@@ -347,36 +543,48 @@ def mom_block(p, steps, warmup, srmra, torch, stream, flush, sm_max):
                     "tests/test_gpu_mom.py"}
 
 
-def run_batched(args, rank, world, local):
-    """64 uneven problems advanced together: grouped launches in a CUDA graph."""
-    import numpy as np
-    import torch
-    from paper_2204_04754_gb300 import srmra, synth
-    torch.cuda.set_device(local)
-    w = synth.WORKLOADS[args.workload]
-    prec = args.prec or w["prec"]
-    specs = synth.batched_instances(w["count"], seed=synth.seed_for(4) + 1000 * rank)
-    stream = torch.cuda.current_stream()
+def secondary_block(steps, warmup, srmra, torch, stream, flush, threads):
+    """The projected-EM workload L = 64, K = 2, N = 1e4, sigma = 0.3 (F = 1): the float32,
+    bf16x3 and polyphase-FFT forms with errors against the oracle, online EM and
+    projected MoM on the same observations."""
+    p, w, runs, block = workload_block(SECONDARY, steps, warmup, srmra, torch, stream, flush,
+                                       threads, forms=("fp32", "bf16x3", "fft32"))
+    fp32_value = runs[0].value
+    for r in runs:
+        r.close()
+    block["online"] = online_block(p, w, steps, warmup, srmra, torch, stream, flush,
+                                   fp32_value)
+    block["mom"] = mom_block(p, steps, warmup, srmra, torch, stream, flush,
+                             float(load_peaks()[0].get("sm_max_mhz", 2070.0)))
+    return block
+
+
+def batched_block(steps, warmup, rank, prec, srmra, synth, torch, stream, flush, count=64,
+                  clocks=None):
+    """`count` uneven problems (L in {32,48,64,96}, K in {2,4}, N ~ U[1e3, 2e4], sigma ~
+    U[0.1, 1]) advanced together: grouped persistent launches replayed as a CUDA graph,
+    decomposition and tile shape picked by the autotuner."""
+    specs = synth.batched_instances(count, seed=synth.seed_for(4) + 1000 * rank)
+    t0 = time.perf_counter()
     probs = [synth.make_problem(sp["L"], sp["K"], sp["N"], sp["sigma"], sp["seed"])
              for sp in specs]
+    gen_s = time.perf_counter() - t0
     solvers = [srmra.Solver(p.L, p.K, p.sigma, p.y, prec=prec, x0=p.x0, rho1=p.rho1_0,
                             rho2=p.rho2_0, stream=stream.cuda_stream) for p in probs]
     t0 = time.perf_counter()
     batch = srmra.Batch(solvers, autotune=True)
     tune_s = time.perf_counter() - t0
-    batch.solve(args.warmup, w["F"], sigma_bm1=1.0)
-    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    batch.solve(warmup, 1, sigma_bm1=1.0)
     l0 = sum(s.launches for s in solvers)
-    clocks = ClockSampler(local)
-    clocks.start()
-    ms = time_steps(lambda: batch.solve(1, w["F"], sigma_bm1=0.0), args.steps, stream, torch,
-                    flush)
-    clk = clocks.stop()
+    if clocks:
+        clocks.start()
+    ms = time_steps(lambda: batch.solve(1, 1, sigma_bm1=0.0), steps, stream, torch, flush)
+    clk = clocks.stop() if clocks else None
     launches = sum(s.launches for s in solvers) - l0
     # per-pass device times: one more iteration enqueued without the graph (events
     # recorded inside a captured graph cannot be timed)
     probe = srmra.Batch(solvers, autotune=False, graph=False)
-    probe.solve(1, w["F"], sigma_bm1=0.0)
+    probe.solve(1, 1, sigma_bm1=0.0)
     p1_ms, p2_ms = probe.pass_ms()
     probe.close()
     total_ms = float(sum(ms))
@@ -385,31 +593,52 @@ def run_batched(args, rank, world, local):
     peaks, peak_src = load_peaks()
     peak = float(peaks["bf16_tflops_sustained"])
     achieved = alg2 / (p2_ms / 1e3) / 1e12
-    out = {"metric": METRIC, "value": world * pairs * args.steps / (total_ms / 1e3),
-           "unit": "pairs/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
-           "ms_per_step": total_ms / args.steps, "higher_is_better": True, "scaling": "weak",
-           "vs_baseline": None, "dtype": prec, "data": "synthetic (64 seeded problems)",
-           "config": {"workload": args.workload, "problems": len(probs),
-                      "L_high": sorted({p.L for p in probs}), "K": sorted({p.K for p in probs}),
-                      "N_total": int(sum(p.N for p in probs)), "F": w["F"],
-                      "step": "one projected-EM iteration of all problems (grouped launches, "
-                              "CUDA graph replay)",
-                      "l2": "256 MiB buffer zeroed before every timed step",
-                      "autotuner": batch.tuning(), "autotune_seconds": tune_s,
-                      "parallelism": f"{world} independent replica(s)"},
-           "roofline": {"bound": "tensor", "kernel": f"k_p2_tc grouped ({prec})",
-                        "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                        "frac": achieved / peak, "traffic": None,
-                        "algorithmic_flops_per_launch": alg2, "avg_launch_ms": p2_ms,
-                        "peak_source": f"dense bf16, sustained, of {peak_src}"},
-           "phases_ms_last_step": {"pass1_grouped": p1_ms, "pass2_grouped": p2_ms},
-           "gpu_launches": launches, "clocks": clk}
+    d = {"value": pairs * steps / (total_ms / 1e3), "unit": "pairs/s",
+         "ms_per_step": total_ms / steps, "steps": steps, "warmup": warmup,
+         "problems": len(probs), "L_high": sorted({p.L for p in probs}),
+         "K": sorted({p.K for p in probs}), "N_total": int(sum(p.N for p in probs)),
+         "precision": prec,
+         "step": "one projected-EM iteration (F = 1) of all problems (grouped launches, "
+                 "CUDA graph replay)",
+         "autotuner": batch.tuning(), "autotune_seconds": tune_s,
+         "data_generation_s": gen_s,
+         "roofline": {"bound": "tensor", "kernel": f"grouped pass 2 ({prec})",
+                      "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                      "frac": achieved / peak, "traffic": None,
+                      "algorithmic_flops_per_launch": alg2, "avg_launch_ms": p2_ms,
+                      "peak_source": f"dense bf16, sustained, of {peak_src}"},
+         "phases_ms_last_step": {"pass1_grouped": p1_ms, "pass2_grouped": p2_ms},
+         "gpu_launches": launches, "clocks": clk}
     batch.close()
     for s_ in solvers:
         s_.close()
+    return d
+
+
+def run_batched(args, rank, world, local):
+    """The batched workload as the bench line."""
+    import torch
+    from paper_2204_04754_gb300 import srmra, synth
+    torch.cuda.set_device(local)
+    w = synth.WORKLOADS[args.workload]
+    prec = args.prec or w["prec"]
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    d = batched_block(args.steps, args.warmup, rank, prec, srmra, synth, torch, stream, flush,
+                      count=w["count"], clocks=ClockSampler(gpu_index(local)))
+    out = {"metric": METRIC, "value": world * d["value"], "unit": "pairs/s", "n_gpus": world,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": d["ms_per_step"],
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": prec,
+           "data": "synthetic (64 seeded problems)",
+           "config": {"workload": args.workload, "problems": d["problems"],
+                      "L_high": d["L_high"], "K": d["K"], "N_total": d["N_total"], "F": 1,
+                      "step": d["step"], "l2": "256 MiB buffer zeroed before every timed step",
+                      "autotuner": d["autotuner"], "autotune_seconds": d["autotune_seconds"],
+                      "parallelism": f"{world} independent replica(s)"},
+           "roofline": d["roofline"], "phases_ms_last_step": d["phases_ms_last_step"],
+           "gpu_launches": d["gpu_launches"], "clocks": d["clocks"]}
     if rank == 0:
         print(json.dumps(out), flush=True)
-    _ = np
 
 
 def serve_trace(srmra, srv, probs, arrivals, iters, F):
@@ -445,27 +674,20 @@ def serve_trace(srmra, srv, probs, arrivals, iters, F):
     return lat, makespan, steps
 
 
-def run_serve(args, rank, local):
+def serve_block(requests, rates, pool_size, slots, budget_gb, prec, srmra, synth, torch,
+                stream, iters=30, F=1, clocks=None):
     """Poisson arrivals of projected-EM solve requests (L in {64,96,128}, K in {2,4},
     N in {1e4, 5e4, 1e5}, sigma ~ U[0.2, 1], 30 projected iterations) served with
     continuous batching.  Latency = completion - planned arrival (queueing included).
-    The requests draw their data from a pool of --serve-pool distinct seeded problems
+    The requests draw their data from a pool of `pool_size` distinct seeded problems
     (request k uses pool entry k mod pool size), so that long traces fit in host memory;
-    --rates runs the same trace at several arrival rates (a sweep that shows where the
-    offered load exceeds capacity)."""
+    several rates run the same trace at each (a sweep that shows where the offered load
+    exceeds capacity)."""
     import numpy as np
-    import torch
-    from paper_2204_04754_gb300 import srmra, synth
-    if rank != 0:
-        return
-    torch.cuda.set_device(local)
-    w = synth.WORKLOADS[args.workload]
-    prec = args.prec or w["prec"]
     rng = np.random.Generator(np.random.PCG64(synth.seed_for(5)))
-    n = args.requests
-    rates = [float(r) for r in args.rates.split(",")] if args.rates else [w["rate"]]
+    n = requests
     unit_gaps = rng.exponential(1.0, size=n)  # arrivals at rate r: cumsum(unit_gaps) / r
-    pool = min(n, args.serve_pool)
+    pool = min(n, pool_size)
     specs = []
     for k in range(pool):
         L = int(rng.choice([64, 96, 128]))
@@ -478,195 +700,79 @@ def run_serve(args, rank, local):
                   for k, (L, K, N, sg) in enumerate(specs)]
     probs = [pool_probs[k % pool] for k in range(n)]
     gen_s = time.perf_counter() - t0
-    stream = torch.cuda.current_stream()
     free, total = torch.cuda.mem_get_info()
-    budget = int(min(free * 0.8, args.serve_budget_gb * 2 ** 30))
-    srv = srmra.Server(budget, max_active=args.serve_slots, prec=prec, stream=stream.cuda_stream)
+    budget = int(min(free * 0.8, budget_gb * 2 ** 30))
+    srv = srmra.Server(budget, max_active=slots, prec=prec, stream=stream.cuda_stream)
     # warm the kernels and graph machinery on a tiny request (not part of the trace)
     wp = synth.make_problem(64, 4, 2000, 0.5, seed=synth.seed_for(5, 999))
-    wid = srv.submit(wp.L, wp.K, wp.sigma, wp.y, 2, F=w["F"])
+    wid = srv.submit(wp.L, wp.K, wp.sigma, wp.y, 2, F=F)
     while srv.step()[0] > 0:
         pass
     srv.result(wid, wp.L)
-    pairs = sum(p.N * p.L * p.L * w["iters"] for p in probs)
+    pairs = sum(p.N * p.L * p.L * iters for p in probs)
     sweep = []
-    clocks = ClockSampler(local)
-    clocks.start()
+    if clocks:
+        clocks.start()
     for rate in rates:
         arrivals = np.cumsum(unit_gaps) / rate
-        lat, makespan, steps = serve_trace(srmra, srv, probs, arrivals, w["iters"], w["F"])
+        lat, makespan, steps = serve_trace(srmra, srv, probs, arrivals, iters, F)
         sweep.append({"rate_per_s": rate, "p50_ms": float(np.percentile(lat, 50)),
                       "p99_ms": float(np.percentile(lat, 99)), "max_ms": float(lat.max()),
                       "solves_per_s": n / makespan, "pairs_per_s": pairs / makespan,
                       "makespan_s": makespan, "server_steps": steps})
-    clk = clocks.stop()
+    clk = clocks.stop() if clocks else None
     srv.close()
     head = sweep[0]
-    out = {"metric": "serve p99 latency", "value": head["p99_ms"], "unit": "ms",
-           "n_gpus": 1, "steps": head["server_steps"], "warmup": 1, "higher_is_better": False,
-           "scaling": "weak", "vs_baseline": None, "dtype": prec,
-           "data": "synthetic (seeded requests)",
-           "config": {"workload": args.workload, "requests": n, "rate_per_s": head["rate_per_s"],
-                      "iters_per_request": w["iters"], "F": w["F"],
-                      "mix": "L {64,96,128} x K {2,4} x N {1e4,5e4,1e5}, sigma U[0.2,1]",
-                      "distinct_problems": pool, "slots": args.serve_slots,
-                      "budget_bytes": budget, "data_generation_s": gen_s},
-           "p50_ms": head["p50_ms"], "p99_ms": head["p99_ms"], "max_ms": head["max_ms"],
-           "solves_per_s": head["solves_per_s"], "pairs_per_s": head["pairs_per_s"],
-           "makespan_s": head["makespan_s"], "clocks": clk}
+    d = {"metric": "serve p99 latency", "unit": "ms", "precision": prec, "requests": n,
+         "rate_per_s": head["rate_per_s"], "iters_per_request": iters, "F": F,
+         "mix": "L {64,96,128} x K {2,4} x N {1e4,5e4,1e5}, sigma U[0.2,1]",
+         "distinct_problems": pool,
+         "problems": [{"L": L, "K": K, "N": N, "sigma": sg} for L, K, N, sg in specs],
+         "slots": slots, "budget_bytes": budget, "data_generation_s": gen_s,
+         "p50_ms": head["p50_ms"], "p99_ms": head["p99_ms"], "max_ms": head["max_ms"],
+         "solves_per_s": head["solves_per_s"], "pairs_per_s": head["pairs_per_s"],
+         "makespan_s": head["makespan_s"], "server_steps": head["server_steps"],
+         "clocks": clk}
     if len(sweep) > 1:
-        out["sweep"] = sweep
-    print(json.dumps(out), flush=True)
+        d["sweep"] = sweep
+    return d
 
 
-def main():
-    args = parse()
-    rank = int(os.environ.get("RANK", "0"))
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
-    if args.impl == "reference":
-        run_reference(args, rank)
-        return
-    if args.workload.startswith("batched"):
-        run_batched(args, rank, world, local)
-        return
-    if args.workload.startswith("serve"):
-        run_serve(args, rank, local)
-        return
-
-    import numpy as np
+def run_serve(args, rank, local):
+    """The serving workload as the bench line (λ = 50/s unless --rates is given)."""
     import torch
     from paper_2204_04754_gb300 import srmra, synth
-
+    if rank != 0:
+        return
     torch.cuda.set_device(local)
-    dist = None
-    if world > 1:
-        import torch.distributed as dist
-        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
-
     w = synth.WORKLOADS[args.workload]
-    prec = args.prec or "fp32"
-    p = synth.workload_problem(args.workload, instance=rank)
-    F = w["F"]
-    stream = torch.cuda.current_stream()
-    y = torch.from_numpy(p.y).cuda()
-    s = srmra.Solver(p.L, p.K, p.sigma, y, prec=prec, x0=p.x0, rho1=p.rho1_0,
-                     rho2=p.rho2_0, stream=stream.cuda_stream)
-    del y
-    # warm-up (starts Algorithm 2's sigma_BM schedule at 1)
-    s.solve(args.warmup, F, sigma_bm1=1.0, loglik=False)
-    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")  # > 129 MB L2
-    s.profile(True)
-    s.profile_read()
-    torch.cuda.synchronize()
-    if dist:
-        dist.barrier()
-    launches0 = s.launches
-    clocks = ClockSampler(int(os.environ.get("CUDA_VISIBLE_DEVICES", str(local)).split(",")[0])
-                          if os.environ.get("CUDA_VISIBLE_DEVICES", "").split(",")[0].isdigit()
-                          else local)
-    clocks.start()
-    evs = []
-    for _ in range(args.steps):
-        flush.zero_()
-        a = torch.cuda.Event(enable_timing=True)
-        b = torch.cuda.Event(enable_timing=True)
-        a.record(stream)
-        s.solve(1, F, sigma_bm1=0.0, loglik=False)
-        b.record(stream)
-        evs.append((a, b))
-    torch.cuda.synchronize()
-    clk = clocks.stop()
-    launches = s.launches - launches0
-    step_ms = [a.elapsed_time(b) for a, b in evs]
-    total_ms = float(sum(step_ms))
-    phase_ms, phase_n = s.profile_read()
-    s.profile(False)
-    if dist:
-        total_ms = reduce_max(total_ms, dist, "cuda")
-        dist.barrier()
-
-    pairs_per_step = p.N * p.L * p.L
-    value = job_throughput(pairs_per_step, args.steps, world, total_ms)
-
-    # roofline of the dominant kernel (phase), from the live CUDA events
-    peaks, peak_src = load_peaks()
-    dom = max(("pass1", "pass2"), key=lambda k: phase_ms[k])
-    if prec == "fft32":
-        # per (observation, phase): one inverse l x l FFT (pass 1), plus the forward FFT
-        # of the weight map and the products (pass 2), 5 n log2 n flops per complex
-        # n-point FFT; spread over the l^2 lags (pairs) of the phase
-        lg = math.log2(p.l * p.l)
-        per_pair_flops = {"pass1": 5 * lg + 6, "pass2": 10 * lg + 14}[dom]
-    else:
-        per_pair_flops = {"pass1": 2 * p.l * p.l, "pass2": 4 * p.l * p.l}[dom]
-    avg_launch_s = phase_ms[dom] / max(1, phase_n[dom]) / 1e3
-    achieved = per_pair_flops * pairs_per_step / avg_launch_s / 1e12
-    if prec in ("fp32", "fft32"):
-        sm_max = float(peaks.get("sm_max_mhz", 2070.0))
-        peak = fp32_peak_tflops(sm_max)
-        bound = "alu"
-        peak_note = (f"FP32 FFMA peak derived: {NUM_SMS} SMs x {FP32_LANES_PER_SM} lanes x 2 "
-                     f"flops x {sm_max:.0f} MHz (max SM clock, {peak_src} peaks file)")
-    else:
-        peak = float(peaks["bf16_tflops_sustained"])
-        bound = "tensor"
-        peak_note = f"dense bf16, sustained, of {peak_src}"
-    kern = {"pass1": f"k_p1_{prec}", "pass2": f"k_p2_{prec}"}[dom]
-    traffic = traffic_from_profiles(kern, args.workload, prec)
-    roof = {"bound": bound, "kernel": kern, "achieved": achieved, "peak": peak,
-            "unit": "TFLOP/s", "frac": achieved / peak, "traffic": traffic,
-            "algorithmic_flops_per_launch": per_pair_flops * pairs_per_step,
-            "avg_launch_ms": avg_launch_s * 1e3, "peak_source": peak_note}
-    if traffic:
-        # the same kernel's DRAM bandwidth: recorded bytes per launch over the live launch
-        # time, against the measured HBM copy bandwidth
-        hbm = float(peaks["hbm_gbs"])
-        roof["dram_gbs"] = traffic / avg_launch_s / 1e9
-        roof["dram_frac_of_hbm_peak"] = roof["dram_gbs"] / hbm
-
-    out = {"metric": METRIC, "value": value, "unit": "pairs/s", "n_gpus": world,
-           "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
-           "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-           "dtype": {"fp32": "f32", "bf16": "bf16", "bf16x3": "bf16x3", "fft32": "f32"}[prec],
-           "data": "synthetic (seeded blob image, mixture shift distributions, Gaussian noise)",
-           "config": {"workload": args.workload, "L_high": p.L, "K": p.K, "L_low": p.l,
-                      "N": p.N, "sigma": p.sigma, "F": F, "precision": prec,
-                      "step": "one projected-EM iteration (E-step, M-step, DCT projection)",
-                      "l2": "256 MiB buffer zeroed before every timed step",
-                      "parallelism": f"{world} independent replica(s)"},
-           "roofline": roof, "gpu_launches": launches,
-           "phases_ms_per_step": {k: v / args.steps for k, v in phase_ms.items()},
-           "clocks": clk}
-
-    if rank == 0 and not args.no_e2e:
-        out["e2e"] = e2e_run(p, prec, w, srmra, torch)
-    if rank == 0 and prec == "fp32" and not args.no_mixed:
-        out["bf16x3"] = mixed_block(p, w, args.steps, args.warmup, srmra, torch, stream, flush,
-                                    value)
-        if p.l in (8, 16, 32):
-            out["fft32"] = mixed_block(p, w, args.steps, args.warmup, srmra, torch, stream,
-                                       flush, value, form="fft32")
-        out["online"] = online_block(p, w, args.steps, args.warmup, srmra, torch, stream,
-                                     flush, value)
-        out["mom"] = mom_block(p, args.steps, args.warmup, srmra, torch, stream, flush,
-                               float(load_peaks()[0].get("sm_max_mhz", 2070.0)))
-    if rank == 0 and world == 1 and not args.no_cpu:
-        cb = cpu_oracle_rate(p, args.cpu_seconds)
-        cb.pop("n_sub", None)
-        out["cpu_baseline"] = cb
-    s.close()
-    if rank == 0:
-        print(json.dumps(out), flush=True)
-    if dist:
-        dist.destroy_process_group()
+    prec = args.prec or w["prec"]
+    rates = [float(r) for r in args.rates.split(",")] if args.rates else [w["rate"]]
+    d = serve_block(args.requests, rates, args.serve_pool, args.serve_slots,
+                    args.serve_budget_gb, prec, srmra, synth, torch,
+                    torch.cuda.current_stream(), iters=w["iters"], F=w["F"],
+                    clocks=ClockSampler(gpu_index(local)))
+    out = {"metric": "serve p99 latency", "value": d["p99_ms"], "unit": "ms",
+           "n_gpus": 1, "steps": d["server_steps"], "warmup": 1, "higher_is_better": False,
+           "scaling": "weak", "vs_baseline": None, "dtype": prec,
+           "data": "synthetic (seeded requests)",
+           "config": {"workload": args.workload, "requests": d["requests"],
+                      "rate_per_s": d["rate_per_s"], "iters_per_request": d["iters_per_request"],
+                      "F": d["F"], "mix": d["mix"], "distinct_problems": d["distinct_problems"],
+                      "slots": d["slots"], "budget_bytes": d["budget_bytes"],
+                      "data_generation_s": d["data_generation_s"]},
+           "p50_ms": d["p50_ms"], "p99_ms": d["p99_ms"], "max_ms": d["max_ms"],
+           "solves_per_s": d["solves_per_s"], "pairs_per_s": d["pairs_per_s"],
+           "makespan_s": d["makespan_s"], "clocks": d["clocks"]}
+    if "sweep" in d:
+        out["sweep"] = d["sweep"]
+    print(json.dumps(out), flush=True)
 
 
 def e2e_run(p, prec, w, srmra, torch):
     """End to end through the public API with pinned host buffers: create (uploads y),
     a full solve of the workload's iteration count with the log-likelihood read back
     every iteration, read the final state, destroy."""
-    import numpy as np
     iters = int(w["iters"])
     yh = torch.from_numpy(p.y).pin_memory()
 
@@ -683,11 +789,171 @@ def e2e_run(p, prec, w, srmra, torch):
     el, ll = once()
     h2d = p.y.nbytes + p.x0.nbytes + 16 * p.L
     d2h = 8 * iters + 4 * p.L * p.L + 16 * p.L
-    _ = np
     return {"value": p.N * p.L * p.L * iters / el, "unit": "pairs/s",
             "h2d_bytes_per_step": h2d / iters, "d2h_bytes_per_step": d2h / iters,
             "step": f"one solve of {iters} iterations per upload; per-step bytes are "
                     f"per-iteration averages", "seconds": el}
+
+
+# ------------------------------------------------------------------- precision study
+
+def run_study(args, local):
+    """Per-iteration one-step errors over a projected run of the precision workload, both
+    noise levels: every form runs Algorithm 2 (F = 1, sigma_BM_1 = 1) from the workload's
+    initial guess; before each of its iterations the FP64 oracle takes the form's own
+    current state, runs the same iteration and projection (Eq. decaying_function
+    schedule), and the form's result is compared with it.  Prints one JSON line per
+    noise level, with the maxima over the iterations and the smallest threshold margin
+    of the denoiser seen by the oracle."""
+    import numpy as np
+    import torch
+    from oracle import fft_oracle as FO
+    from oracle import srmra_oracle as O
+    from paper_2204_04754_gb300 import srmra, synth
+    torch.cuda.set_device(local)
+    threads = args.oracle_threads or os.cpu_count()
+    names = [args.workload] + ([COMPANION[args.workload]] if args.workload in COMPANION else [])
+    decay = 2.0 ** -0.1
+    for name in names:
+        p = synth.workload_problem(name)
+        res = {}
+        t_start = time.perf_counter()
+        for prec in ("fp32", "bf16x3", "bf16"):
+            s = srmra.Solver(p.L, p.K, p.sigma, p.y, prec=prec, x0=p.x0, rho1=p.rho1_0,
+                             rho2=p.rho2_0)
+            per = []
+            sbm = 1.0
+            margin = math.inf
+            for it in range(args.study_iters):
+                x, r1, r2, _, _ = s.state()
+                ll = s.solve(1, 1, sigma_bm1=sbm, decay=decay)[0]
+                xg, r1g, r2g, _, _ = s.state()
+                xo, r1o, r2o, llo, _ = FO.em_iter_fft(p.y, x, r1, r2, p.sigma, p.K,
+                                                      workers=threads)
+                xo, mg = O.dct_denoise(xo, sbm)
+                margin = min(margin, mg)
+                per.append({"x": rel(xg, xo), "rho1": rel(r1g, r1o), "rho2": rel(r2g, r2o),
+                            "LL": abs(ll - llo) / abs(llo), "margin": mg})
+                sbm *= decay
+            s.close()
+            res[prec] = {"max": {k: max(q[k] for q in per) for k in ("x", "rho1", "rho2", "LL")},
+                         "last": per[-1], "min_threshold_margin": margin,
+                         "per_iteration": per}
+        print(json.dumps({"study": "precision", "workload": name, "iters": args.study_iters,
+                          "mode": "one-step (oracle restarted from each form's state)",
+                          "seconds": time.perf_counter() - t_start, "forms": res}), flush=True)
+
+
+# ------------------------------------------------------------------- main
+
+def main():
+    args = parse()
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        run_reference(args, rank)
+        return
+    if args.study:
+        if rank == 0:
+            run_study(args, local)
+        return
+    if args.workload.startswith("batched"):
+        run_batched(args, rank, world, local)
+        return
+    if args.workload.startswith("serve"):
+        run_serve(args, rank, local)
+        return
+
+    import torch
+    from paper_2204_04754_gb300 import srmra, synth
+
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    w = synth.WORKLOADS[args.workload]
+    prec = args.prec or "fp32"
+    p = synth.workload_problem(args.workload, instance=rank)
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")  # > 129 MB L2
+    threads = args.oracle_threads or os.cpu_count()
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    head = FormRun(p, w, args.workload, prec, args.steps, args.warmup, srmra, torch, stream,
+                   flush, clocks=True, local=local)
+    total_ms = head.total_ms
+    if dist:
+        total_ms = reduce_max(total_ms, dist, "cuda")
+        dist.barrier()
+    value = job_throughput(p.N * p.L * p.L, args.steps, world, total_ms)
+
+    out = {"metric": METRIC, "value": value, "unit": "pairs/s", "n_gpus": world,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+           "dtype": {"fp32": "f32", "bf16": "bf16", "bf16x3": "bf16x3", "fft32": "f32"}[prec],
+           "data": "synthetic (seeded blob image, mixture shift distributions, Gaussian noise)",
+           "config": {"workload": args.workload, "L_high": p.L, "K": p.K, "L_low": p.l,
+                      "N": p.N, "sigma": p.sigma, "F": w["F"], "precision": prec,
+                      "step": "one projected-EM iteration (E-step, M-step, DCT projection)",
+                      "l2": "256 MiB buffer zeroed before every timed step",
+                      "parallelism": f"{world} independent replica(s)"},
+           "roofline": head.roof, "gpu_launches": head.launches,
+           "phases_ms_per_step": {k: v / args.steps for k, v in head.phase_ms.items()},
+           "plan": head.plan, "clocks": head.clocks}
+
+    if rank == 0 and not args.no_e2e:
+        out["e2e"] = e2e_run(p, prec, w, srmra, torch)
+    if rank == 0 and prec == "fp32" and not args.no_mixed:
+        # the tensor-core forms of the same workload, and the errors of every form
+        # against the FP64 oracle after one iteration from a common state
+        forms = ("bf16x3", "bf16") if p.l * p.l >= 64 else ("bf16x3",)
+        runs = [head] + [FormRun(p, w, args.workload, f, args.steps, args.warmup, srmra,
+                                 torch, stream, flush) for f in forms]
+        err, how = errors_vs_oracle(p, runs, threads)
+        out["error_vs_oracle"] = dict(err["fp32"], how=how)
+        out["forms"] = {}
+        for r in runs[1:]:
+            d = r.summary(value)
+            d["error_vs_oracle"] = err[r.prec]
+            worst = max(err[r.prec][k] for k in ("x", "rho1", "rho2", "LL"))
+            d["rel_err_max"] = worst
+            d["within_1e-4"] = bool(worst <= 1e-4)
+            out["forms"][r.prec] = d
+            r.close()
+        if "bf16x3" in out["forms"]:
+            out["roofline"]["bf16x3"] = out["forms"]["bf16x3"]["roofline"]
+            out["bf16x3_speedup_vs_fp32"] = out["forms"]["bf16x3"]["speedup_vs_fp32"]
+    head.close()
+    if rank == 0 and prec == "fp32" and not args.no_mixed and not args.no_extra:
+        if args.workload in COMPANION:
+            _, _, runs2, blk = workload_block(COMPANION[args.workload], args.steps,
+                                              args.warmup, srmra, torch, stream, flush,
+                                              threads, local=local)
+            for r in runs2:
+                r.close()
+            out[COMPANION[args.workload]] = blk
+        if args.workload != SECONDARY:
+            out[SECONDARY] = secondary_block(args.steps, args.warmup, srmra, torch, stream,
+                                             flush, threads)
+        del flush
+        torch.cuda.empty_cache()
+        flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+        out["batched_64"] = batched_block(min(args.steps, 5), args.warmup, rank, "bf16x3",
+                                          srmra, synth, torch, stream, flush)
+        out["serve"] = serve_block(16, [2.0], 6, args.serve_slots, args.serve_budget_gb,
+                                   "bf16x3", srmra, synth, torch, stream)
+    if rank == 0 and world == 1 and not args.no_cpu:
+        cb = cpu_oracle_rate(p, args.cpu_seconds)
+        cb.pop("n_sub", None)
+        out["cpu_baseline"] = cb
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    if dist:
+        dist.destroy_process_group()
 
 
 if __name__ == "__main__":

@@ -215,6 +215,38 @@ srmra_status srmra_mstep_stats(srmra_ctx* ctx, const double* stats, int32_t stat
 /* srmra_launch_count -- number of CUDA kernels this context has launched so far. */
 srmra_status srmra_launch_count(const srmra_ctx* ctx, int64_t* count);
 
+/* srmra_set_wait_limit -- limit, in nanoseconds, of the bounded device-side waits of
+ * this context's tensor-core kernels (mbarrier, mailbox and flag waits; default 2e9).
+ * A wait that runs out makes its kernel stop the pipeline, drain its own asynchronous
+ * copies and MMAs, release TMEM and set the device status word: the next entry point
+ * that reads the status (one returning host values, or any call with
+ * SRMRA_FLAG_CHECK_NUMERIC) returns SRMRA_ETIMEOUT, and the GPU keeps answering.
+ * limit_ns must lie in [1e3, 6e10].
+ * test_hook exists to test that failure path (0 in normal use): 1 makes the epilogue
+ * of the first CTA of pass 1 wait on a barrier that nothing completes; 2 does the same
+ * in pass 2 (in a cluster form the first cluster's rank 0, so that its peers' waits for
+ * its weight tile run out as well).  The wait runs out after limit_ns and the iteration
+ * reports SRMRA_ETIMEOUT; x and rho are then undefined until srmra_set_state.
+ * A batch copies the setting when it is created; a grouped launch uses its first
+ * problem's.  The float32 and FFT forms have no such waits (the setting is kept,
+ * unused).  Errors: SRMRA_EINVAL. */
+srmra_status srmra_set_wait_limit(srmra_ctx* ctx, int64_t limit_ns, int32_t test_hook);
+
+/* Pass-2 kernel forms reported by srmra_get_plan (entry 4). */
+#define SRMRA_P2_PER_CHUNK 0   /* tensor cores, weights recomputed per 256-pixel chunk */
+#define SRMRA_P2_RING 1        /* tensor cores, ring cluster form (clusters of 2-4) */
+#define SRMRA_P2_INTERLEAVED 2 /* tensor cores, interleaved cluster form (clusters of 5-16) */
+#define SRMRA_P2_FP32 3        /* float32 persistent clusters */
+#define SRMRA_P2_FFT 4         /* polyphase-FFT form */
+
+/* srmra_get_plan -- the work decomposition the context's kernels use (no computation;
+ * the executed-work counts of a profile are derived from it).  out (host, n int32
+ * entries, n <= 6 are filled): [0] pass-1 shift groups per observation tile, [1] pass-1
+ * shift tiles per group, [2] pass-2 cluster size G (CTAs sharing each weight tile; 1 =
+ * none), [3] pass-2 chunk groups (each recomputes the logits of a shift tile), [4] the
+ * pass-2 form (SRMRA_P2_*), [5] pass-2 observation splits.  Errors: SRMRA_EINVAL. */
+srmra_status srmra_get_plan(const srmra_ctx* ctx, int32_t* out, int32_t n);
+
 /* ---- Batches: many independent problems advanced together (one GPU). ----
  * A batch groups contexts of the same precision form and CUDA stream.  Each EM
  * iteration (Sec. 2) of a batch runs ONE grouped persistent launch of pass 1 and ONE of
@@ -461,7 +493,10 @@ const char* srmra_mom_last_error(const srmra_mom* m);
  * message (srmra_noalloc_last_error); roughly N * l^2 <= 7.5e6 fits.  The library calls
  * no cudaMalloc, cudaFree or allocating routine here.  The first call on a device looks
  * up the array's device address (cudaGetSymbolAddress) with that device current; make
- * that first call before any stream capture.  Every call on a device shares the array
+ * that first call before any stream capture.  The address is cached per device and
+ * looked up again when the device's context has changed (a device reset reloads the
+ * library's module; call again before capturing after a reset).  Every call on a
+ * device shares the array
  * and leaves its contents behind: calls whose work overlaps on the GPU (other streams,
  * other threads) race on it and must be serialised by the caller. */
 srmra_status srmra_loglik_noalloc(const float* y_dev, int64_t N, int32_t L, int32_t K,

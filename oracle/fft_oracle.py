@@ -46,25 +46,11 @@ def shift_of(K: int, L: int) -> np.ndarray:
     return (t * K - r) % L
 
 
-def em_iter_fft(Y, x, rho1, rho2, sigma, K, chunk: int | None = None):
-    """One EM iteration. Returns (x_{t+1}, rho1_{t+1}, rho2_{t+1}, LL(theta_t), aux)
-    with aux = dict(lse, c (joint, L x L), b (L x L), A (L x L))."""
-    x = np.asarray(x, np.float64)
-    L = x.shape[0]
-    l = L // K
+def _estep_sums(Y, Xf, nu, lp, inv2s2, K, l, chunk):
+    """The sums over the observations Y (n x l x l, float64) that the M-step reads:
+    G[r] = sum_i conj(FFT2(w_{i,r,.})) * FFT2(y_i), c[r, t] = sum_i w^{i,(r,t)}, and
+    lse_i (Eqs. weights_EM and likelihood_EM, Sec. 2)."""
     N = Y.shape[0]
-    Y = np.asarray(Y, np.float64).reshape(N, l, l)
-    if chunk is None:
-        chunk = max(1, (1 << 26) // (L * L * 16))
-    xr = polyphase(x, K)                                   # (K,K,l,l)
-    Xf = np.fft.fft2(xr)
-    nu = (xr * xr).sum(axis=(2, 3))                        # ||x_r||^2, (K,K)
-    S = shift_of(K, L)                                     # (K, l)
-    with np.errstate(divide="ignore"):
-        lr1 = np.log(np.asarray(rho1, np.float64))[S]      # (K, l) over (r1, t1)
-        lr2 = np.log(np.asarray(rho2, np.float64))[S]      # (K, l) over (r2, t2)
-    lp = lr1[:, None, :, None] + lr2[None, :, None, :]     # (K,K,l,l)
-    inv2s2 = 1.0 / (2.0 * sigma * sigma)
     G = np.zeros((K, K, l, l), dtype=np.complex128)
     c = np.zeros((K, K, l, l))
     lse = np.empty(N)
@@ -83,6 +69,48 @@ def em_iter_fft(Y, x, rho1, rho2, sigma, K, chunk: int | None = None):
         lse[a:a + n] = lse_c
         c += W.sum(axis=0)
         G += (np.conj(np.fft.fft2(W)) * Yf[:, None, None]).sum(axis=0)
+    return G, c, lse
+
+
+def em_iter_fft(Y, x, rho1, rho2, sigma, K, chunk: int | None = None, workers: int = 1):
+    """One EM iteration. Returns (x_{t+1}, rho1_{t+1}, rho2_{t+1}, LL(theta_t), aux)
+    with aux = dict(lse, c (joint, L x L), b (L x L), A (L x L)).
+
+    workers > 1 splits the observations into that many contiguous ranges whose sums
+    over i (a plain regrouping of the sums in Eqs. x_EM and rho_EM) are formed by
+    threads and added in range order, so that large problems check in seconds."""
+    x = np.asarray(x, np.float64)
+    L = x.shape[0]
+    l = L // K
+    N = Y.shape[0]
+    Y = np.asarray(Y, np.float64).reshape(N, l, l)
+    if chunk is None:
+        chunk = max(1, (1 << 26) // (L * L * 16))
+    xr = polyphase(x, K)                                   # (K,K,l,l)
+    Xf = np.fft.fft2(xr)
+    nu = (xr * xr).sum(axis=(2, 3))                        # ||x_r||^2, (K,K)
+    S = shift_of(K, L)                                     # (K, l)
+    with np.errstate(divide="ignore"):
+        lr1 = np.log(np.asarray(rho1, np.float64))[S]      # (K, l) over (r1, t1)
+        lr2 = np.log(np.asarray(rho2, np.float64))[S]      # (K, l) over (r2, t2)
+    lp = lr1[:, None, :, None] + lr2[None, :, None, :]     # (K,K,l,l)
+    inv2s2 = 1.0 / (2.0 * sigma * sigma)
+    workers = max(1, min(int(workers), N))
+    if workers == 1:
+        G, c, lse = _estep_sums(Y, Xf, nu, lp, inv2s2, K, l, chunk)
+    else:
+        from concurrent.futures import ThreadPoolExecutor
+        cuts = [N * k // workers for k in range(workers + 1)]
+        with ThreadPoolExecutor(workers) as ex:
+            parts = list(ex.map(lambda k: _estep_sums(Y[cuts[k]:cuts[k + 1]], Xf, nu, lp,
+                                                      inv2s2, K, l, chunk),
+                                range(workers)))
+        G = parts[0][0].copy()
+        c = parts[0][1].copy()
+        for Gp, cp_, _ in parts[1:]:
+            G += Gp
+            c += cp_
+        lse = np.concatenate([q[2] for q in parts])
     b_r = np.fft.ifft2(G).real                             # (K,K,l,l)
     A_r = c.sum(axis=(2, 3))                               # (K,K)
     xr_new = np.where(A_r[:, :, None, None] > 0,

@@ -640,6 +640,31 @@ srmra_status srmra_launch_count(const srmra_ctx* c, int64_t* count) {
   return SRMRA_OK;
 }
 
+srmra_status srmra_set_wait_limit(srmra_ctx* c, int64_t limit_ns, int32_t test_hook) {
+  if (!c) return fail(nullptr, SRMRA_EINVAL, "ctx is NULL");
+  if (limit_ns < 1000 || limit_ns > 60000000000ll)
+    return fail(c, SRMRA_EINVAL, "need 1e3 <= limit_ns <= 6e10");
+  if (test_hook < 0 || test_hook > 2) return fail(c, SRMRA_EINVAL, "test_hook must be 0, 1 or 2");
+  c->wait_ns = (uint64_t)limit_ns;
+  c->test_hook = test_hook;
+  if (is_tc_prec(c->prec)) CK(c, tc_upload_inst(c));
+  return SRMRA_OK;
+}
+
+srmra_status srmra_get_plan(const srmra_ctx* c, int32_t* out, int32_t n) {
+  if (!c || !out || n < 0) return fail(nullptr, SRMRA_EINVAL, "ctx or out is NULL");
+  const Plan& p = c->plan;
+  int form = SRMRA_P2_FP32;
+  if (is_tc_prec(c->prec))
+    form = p.p2_gc <= 1 ? SRMRA_P2_PER_CHUNK : (p.p2_gc <= 4 ? SRMRA_P2_RING : SRMRA_P2_INTERLEAVED);
+  else if (c->prec == SRMRA_FFT32)
+    form = SRMRA_P2_FFT;
+  const int32_t v[6] = {p.p1_groups, p.p1_tiles_per_group, p.p2_gc, p.p2_chunk_groups, form,
+                        p.p2_nsplit};
+  for (int k = 0; k < n && k < 6; ++k) out[k] = v[k];
+  return SRMRA_OK;
+}
+
 srmra_status srmra_profile(srmra_ctx* c, int32_t enable) {
   if (!c) return fail(nullptr, SRMRA_EINVAL, "ctx is NULL");
   c->profiling = enable != 0;

@@ -11,9 +11,26 @@
 // with nu'_r = ||x'_r||^2 (exact algebra; it shrinks the operands of the contraction).
 #include <math.h>
 
+#include <mutex>
+#include <set>
+#include <utility>
+
 #include "srmra_internal.cuh"
 
 namespace srmra {
+
+cudaError_t once_per_device(int key, cudaError_t (*set)()) {
+  static std::mutex mu;
+  static std::set<std::pair<int, int>> done;
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  std::lock_guard<std::mutex> lock(mu);
+  if (done.count({dev, key})) return cudaSuccess;
+  e = set();
+  if (e == cudaSuccess) done.insert({dev, key});
+  return e;
+}
 
 namespace {
 

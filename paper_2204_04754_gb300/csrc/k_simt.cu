@@ -581,11 +581,9 @@ int p2_clusters(int gc, int num_sms) {
 }
 
 cudaError_t launch_pass2_f32(srmra_ctx* c) {
-  static bool attr_done = false;
-  if (!attr_done) {
-    cudaError_t e = simt_set_attributes();
+  {
+    cudaError_t e = once_per_device(ATTR_SIMT_P2, simt_set_attributes);
     if (e != cudaSuccess) return e;
-    attr_done = true;
   }
   const Geom& g = c->g;
   const Plan& p = c->plan;

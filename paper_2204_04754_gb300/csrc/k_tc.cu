@@ -25,6 +25,9 @@
 #include <cudaTypedefs.h>
 
 #include <algorithm>
+#include <map>
+#include <mutex>
+#include <utility>
 
 #include "ptx_sm103.cuh"
 #include "srmra_internal.cuh"
@@ -56,6 +59,8 @@ struct TcP1Args {
   float* pm;
   float* ps;
   int* status;
+  uint64_t wait_ns;  // limit of every bounded wait of the launch (instance 0's is used)
+  int hook;          // test hook (srmra_set_wait_limit): 1 = a wait in pass 1 that never ends
 };
 
 struct TcP2Args {
@@ -76,6 +81,8 @@ struct TcP2Args {
   float* cp;
   float* zbp;
   int* status;
+  uint64_t wait_ns;  // limit of every bounded wait of the launch (instance 0's is used)
+  int hook;          // test hook (srmra_set_wait_limit): 2 = a wait in pass 2 that never ends
 };
 
 // One problem instance of a (possibly grouped) launch: the tensor maps of its operands
@@ -122,9 +129,12 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
   uint64_t* tfull = empty + P1_SLOTS;
   uint64_t* tempty = tfull + 2;
   uint64_t* drain = tempty + 2;
-  uint32_t* tptr = (uint32_t*)(drain + 1);
+  uint64_t* never = drain + 1;  // nothing arrives on it (test hook)
+  uint32_t* tptr = (uint32_t*)(never + 1);
   volatile int* abort = (volatile int*)(tptr + 1);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const uint64_t wlim = insts[0].p1.wait_ns;
+  const int hook = insts[0].p1.hook;
 
   if (threadIdx.x == 0) {
     for (int k = 0; k < P1_SLOTS; ++k) {
@@ -136,6 +146,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
       mbar_init(&tempty[b], 128);
     }
     mbar_init(drain, 1);
+    mbar_init(never, 1);
     *abort = 0;
     fence_mbar_init();
   }
@@ -165,7 +176,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             for (int sl = 0; sl < SPK; ++sl) {
               const int st = it % P1_SLOTS;
               const uint32_t ph = (it / P1_SLOTS) & 1;
-              if (!mbar_wait(&empty[st], ph ^ 1, abort)) {
+              if (!mbar_wait(&empty[st], ph ^ 1, abort, wlim)) {
                 ok = false;
                 break;
               }
@@ -181,9 +192,11 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
               ++it;
             }
       }
-      if (!ok) {
-        raise_timeout(abort, status);
-        // let the loads already issued land before the CTA exits
+      if (!ok) raise_timeout(abort, status);
+      {
+        // the fills already issued land before the CTA exits, also when another role
+        // gave up and stopped consuming them (in a normal run they are all consumed and
+        // these waits return at once)
         const uint32_t lo = it > P1_SLOTS ? it - P1_SLOTS : 0;
         int zero = 0;
         for (uint32_t k = lo; k < it; ++k)
@@ -205,7 +218,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         for (int tile = tb; ok && tile < te; ++tile) {
           const int b = tcount & 1;
           const uint32_t tph = (tcount >> 1) & 1;
-          if (!mbar_wait(&tempty[b], tph ^ 1, abort)) {
+          if (!mbar_wait(&tempty[b], tph ^ 1, abort, wlim)) {
             ok = false;
             break;
           }
@@ -215,7 +228,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             int st[SPK];
             for (int sl = 0; sl < SPK; ++sl) {
               st[sl] = (it + sl) % P1_SLOTS;
-              if (!mbar_wait(&full[st[sl]], ((it + sl) / P1_SLOTS) & 1, abort)) ok = false;
+              if (!mbar_wait(&full[st[sl]], ((it + sl) / P1_SLOTS) & 1, abort, wlim)) ok = false;
             }
             if (!ok) break;
             tc_fence_after();
@@ -240,12 +253,12 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
           ++tcount;
         }
       }
-      if (!ok) {
-        raise_timeout(abort, status);
-        mma_commit(drain);  // all issued MMAs complete before TMEM is released
-        int zero = 0;
-        mbar_wait(drain, 0, (volatile int*)&zero);
-      }
+      if (!ok) raise_timeout(abort, status);
+      // every issued MMA completes before TMEM is released, also when another role
+      // gave up and left accumulators unread
+      mma_commit(drain);
+      int zero = 0;
+      mbar_wait(drain, 0, (volatile int*)&zero);
     }
   } else {
     const int q = warp & 3;  // TMEM lane quadrant of this warp
@@ -272,7 +285,12 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
       for (int tile = tb; tile < te; ++tile) {
         const int b = tcount & 1;
         const uint32_t tph = (tcount >> 1) & 1;
-        ok = __all_sync(0xffffffffu, mbar_wait(&tfull[b], tph, abort));
+        // test hook: the first CTA's epilogue first waits on a barrier that nothing
+        // completes, so that the wait runs out after the limit and the launch reports a
+        // timeout through the ordinary abort path
+        const bool held = hook == 1 && blockIdx.x == 0 && tcount == 0;
+        ok = __all_sync(0xffffffffu, (!held || mbar_wait(never, 0, abort, wlim)) &&
+                                         mbar_wait(&tfull[b], tph, abort, wlim));
         if (!ok) break;
         tc_fence_after();
 #pragma unroll 1
@@ -339,11 +357,15 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
   uint64_t* zfull = pempty + 2;
   uint64_t* zempty = zfull + 1;
   uint64_t* drain = zempty + 1;
-  uint32_t* tptr = (uint32_t*)(drain + 1);
+  uint64_t* never = drain + 1;  // nothing arrives on it (test hook)
+  uint32_t* tptr = (uint32_t*)(never + 1);
   volatile int* abort = (volatile int*)(tptr + 1);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const uint64_t wlim = insts[0].p2.wait_ns;
+  const int hook = insts[0].p2.hook;
 
   if (threadIdx.x == 0) {
+    mbar_init(never, 1);
     for (int k = 0; k < P2_SLOTS; ++k) {
       mbar_init(&full[k], 1);
       mbar_init(&empty[k], 1);
@@ -376,7 +398,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
       bool ok = true;
       auto next_slot = [&](uint32_t bytes) -> uint8_t* {
         const int st = it % P2_SLOTS;
-        if (!mbar_wait(&empty[st], ((it / P2_SLOTS) & 1) ^ 1, abort)) {
+        if (!mbar_wait(&empty[st], ((it / P2_SLOTS) & 1) ^ 1, abort, wlim)) {
           ok = false;
           return nullptr;
         }
@@ -428,8 +450,11 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
           }
         }
       }
-      if (!ok) {
-        raise_timeout(abort, status);
+      if (!ok) raise_timeout(abort, status);
+      {
+        // the fills already issued land before the CTA exits, also when another role
+        // gave up and stopped consuming them (in a normal run they are all consumed and
+        // these waits return at once)
         const uint32_t lo = it > P2_SLOTS ? it - P2_SLOTS : 0;
         int zero = 0;
         for (uint32_t k = lo; k < it; ++k)
@@ -444,7 +469,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
       bool ok = true;
       auto wait_slot = [&]() -> uint8_t* {
         const int st = it % P2_SLOTS;
-        if (!mbar_wait(&full[st], (it / P2_SLOTS) & 1, abort)) {
+        if (!mbar_wait(&full[st], (it / P2_SLOTS) & 1, abort, wlim)) {
           ok = false;
           return nullptr;
         }
@@ -462,7 +487,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         for (int j = 0; ok && j <= nb; ++j) {
           if (j < nb) {  // logits S_j into TMEM buffer sc & 1
             const int b = sc & 1;
-            if (!mbar_wait(&sempty[b], ((sc >> 1) & 1) ^ 1, abort)) {
+            if (!mbar_wait(&sempty[b], ((sc >> 1) & 1) ^ 1, abort, wlim)) {
               ok = false;
               break;
             }
@@ -503,11 +528,11 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
           if (j >= 1) {  // Z' += W_{j-1} . Y'^T
             const int jj = j - 1;
             const int pb = pz & 1;
-            if (jj == 0 && !mbar_wait(zempty, (uc & 1) ^ 1, abort)) {
+            if (jj == 0 && !mbar_wait(zempty, (uc & 1) ^ 1, abort, wlim)) {
               ok = false;
               break;
             }
-            if (!mbar_wait(&pfull[pb], (pz >> 1) & 1, abort)) {
+            if (!mbar_wait(&pfull[pb], (pz >> 1) & 1, abort, wlim)) {
               ok = false;
               break;
             }
@@ -535,12 +560,12 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         mma_commit(zfull);
         ++uc;
       }
-      if (!ok) {
-        raise_timeout(abort, status);
-        mma_commit(drain);
-        int zero = 0;
-        mbar_wait(drain, 0, (volatile int*)&zero);
-      }
+      if (!ok) raise_timeout(abort, status);
+      // every issued MMA completes before TMEM is released, also when another role
+      // gave up and left accumulators unread
+      mma_commit(drain);
+      int zero = 0;
+      mbar_wait(drain, 0, (volatile int*)&zero);
     }
   } else {
     const int q = warp & 3;
@@ -570,8 +595,11 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         // use; lse2 = +inf past N gives weight 0
         float ny = a.ybar[ib + lane];
         float nl = (ib + lane < a.N) ? a.lse2[ib + lane] : INFINITY;
-        ok = __all_sync(0xffffffffu, mbar_wait(&sfull[b], (sc >> 1) & 1, abort));
-        if (ok) ok = __all_sync(0xffffffffu, mbar_wait(&pempty[pb], ((pz >> 1) & 1) ^ 1, abort));
+        // test hook: see pass 1
+        const bool held = hook == 2 && blockIdx.x == 0 && sc == 0;
+        ok = __all_sync(0xffffffffu, (!held || mbar_wait(never, 0, abort, wlim)) &&
+                                         mbar_wait(&sfull[b], (sc >> 1) & 1, abort, wlim));
+        if (ok) ok = __all_sync(0xffffffffu, mbar_wait(&pempty[pb], ((pz >> 1) & 1) ^ 1, abort, wlim));
         if (!ok) break;
         tc_fence_after();
         uint8_t* prow = pbuf + pb * SLOT + row * 128;
@@ -623,7 +651,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         ++pz;
       }
       if (!ok) break;
-      ok = __all_sync(0xffffffffu, mbar_wait(zfull, uc & 1, abort));
+      ok = __all_sync(0xffffffffu, mbar_wait(zfull, uc & 1, abort, wlim));
       if (!ok) break;
       tc_fence_after();
       float* zrow = a.Zp + ((int64_t)split * a.Spad + s) * a.ldy;
@@ -693,10 +721,11 @@ constexpr int MBOX_DEPTH = 8;
 // ---- ring form
 constexpr int P2R_SLOTS = 7;
 static_assert(MBOX_DEPTH > P2R_SLOTS, "a mailbox row could be reused before it is read");
-// barriers: full, empty (ring), sfull, sempty, zfull, zempty, mfull (rows), drain, wready;
+// barriers: full, empty (ring), sfull, sempty, zfull, zempty, mfull (rows), drain, wready,
+// never;
 // then the mailbox, the TMEM address and the abort flag, in P2R_BOOK bytes after the ring
 constexpr int P2R_BOOK = 512;
-static_assert((2 * P2R_SLOTS + 2 + 2 + 1 + 1 + MBOX_DEPTH + 1 + 1) * 8 +
+static_assert((2 * P2R_SLOTS + 2 + 2 + 1 + 1 + MBOX_DEPTH + 1 + 1 + 1) * 8 +
                       MBOX_DEPTH * P2R_MAX_G * 4 + 4 + 4 <= P2R_BOOK,
               "ring-form bookkeeping exceeds its P2R_BOOK bytes");
 
@@ -715,10 +744,13 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
   uint64_t* mfull = zempty + 1;  // [MBOX_DEPTH]: one barrier per mailbox row
   uint64_t* drain = mfull + MBOX_DEPTH;
   uint64_t* wready = drain + 1;  // the 128 epilogue threads have written the weight tile
-  uint32_t* mbox = (uint32_t*)(wready + 1);  // [MBOX_DEPTH][P2R_MAX_G] reserved slots
+  uint64_t* never = wready + 1;  // nothing arrives on it (test hook)
+  uint32_t* mbox = (uint32_t*)(never + 1);  // [MBOX_DEPTH][P2R_MAX_G] reserved slots
   uint32_t* tptr = mbox + MBOX_DEPTH * P2R_MAX_G;
   volatile int* abort = (volatile int*)(tptr + 1);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const uint64_t wlim = insts[0].p2.wait_ns;
+  const int hook = insts[0].p2.hook;
   const uint32_t rank = cluster_rank();
   const int64_t cid = blockIdx.x / G, ncl = gridDim.x / G;
 
@@ -736,6 +768,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     for (int k = 0; k < MBOX_DEPTH; ++k) mbar_init(&mfull[k], G);
     mbar_init(drain, 1);
     mbar_init(wready, 128);
+    mbar_init(never, 1);
     *abort = 0;
     fence_mbar_init();
   }
@@ -756,7 +789,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
       bool ok = true;
       auto reserve = [&](bool expect_copy) -> int {
         const int st = it % P2R_SLOTS;
-        if (!mbar_wait(&empty[st], ((it / P2R_SLOTS) & 1) ^ 1, abort)) {
+        if (!mbar_wait(&empty[st], ((it / P2R_SLOTS) & 1) ^ 1, abort, wlim)) {
           ok = false;
           return -1;
         }
@@ -835,8 +868,11 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
           }
         }
       }
-      if (!ok) {
-        raise_timeout(abort, status);
+      if (!ok) raise_timeout(abort, status);
+      {
+        // the fills already issued land before the CTA exits, also when another role
+        // gave up and stopped consuming them (in a normal run they are all consumed and
+        // these waits return at once)
         const uint32_t lo = it > P2R_SLOTS ? it - P2R_SLOTS : 0;
         int zero = 0;
         for (uint32_t k = lo; k < it; ++k)
@@ -851,7 +887,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
       bool ok = true;
       auto wait_slot = [&]() -> int {
         const int st = it % P2R_SLOTS;
-        if (!mbar_wait(&full[st], (it / P2R_SLOTS) & 1, abort)) {
+        if (!mbar_wait(&full[st], (it / P2R_SLOTS) & 1, abort, wlim)) {
           ok = false;
           return -1;
         }
@@ -876,7 +912,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
           const int r0 = j * G, nq = j < rounds ? min(G, nb - r0) : 0;
           if ((int)rank < nq) {
             const int b = sc & 1;
-            if (!mbar_wait(&sempty[b], ((sc >> 1) & 1) ^ 1, abort)) {
+            if (!mbar_wait(&sempty[b], ((sc >> 1) & 1) ^ 1, abort, wlim)) {
               ok = false;
               break;
             }
@@ -929,7 +965,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             }
             const int stP = stPs[kq];
             if (cvalid) {
-              if (first_z && !mbar_wait(zempty, (uc & 1) ^ 1, abort)) {
+              if (first_z && !mbar_wait(zempty, (uc & 1) ^ 1, abort, wlim)) {
                 ok = false;
                 break;
               }
@@ -959,12 +995,12 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
           ++uc;
         }
       }
-      if (!ok) {
-        raise_timeout(abort, status);
-        mma_commit(drain);
-        int zero = 0;
-        mbar_wait(drain, 0, (volatile int*)&zero);
-      }
+      if (!ok) raise_timeout(abort, status);
+      // every issued MMA completes before TMEM is released, also when another role
+      // gave up and left accumulators unread
+      mma_commit(drain);
+      int zero = 0;
+      mbar_wait(drain, 0, (volatile int*)&zero);
     }
   } else {
     const int q = warp & 3;
@@ -999,7 +1035,11 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         // use; lse2 = +inf past N gives weight 0
         float ny = a.ybar[ib + lane];
         float nl = (ib + lane < a.N) ? a.lse2[ib + lane] : INFINITY;
-        ok = __all_sync(0xffffffffu, mbar_wait(&sfull[b], (sc >> 1) & 1, abort));
+        // test hook: see pass 1 (the first cluster's rank 0 never builds its first tile,
+        // so its peers' waits for that tile run out as well)
+        const bool held = hook == 2 && blockIdx.x == 0 && sc == 0;
+        ok = __all_sync(0xffffffffu, (!held || mbar_wait(never, 0, abort, wlim)) &&
+                                         mbar_wait(&sfull[b], (sc >> 1) & 1, abort, wlim));
         if (!ok) break;
         tc_fence_after();
         // the weights of this row, as fp16 pairs in the order of the tile's columns; they
@@ -1040,7 +1080,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         tc_fence_before();
         mbar_arrive(&sempty[b]);  // the logits are no longer needed
         ok = __all_sync(0xffffffffu,
-                        mbar_wait_cluster(&mfull[mr % MBOX_DEPTH], (mr / MBOX_DEPTH) & 1, abort));
+                        mbar_wait_cluster(&mfull[mr % MBOX_DEPTH], (mr / MBOX_DEPTH) & 1, abort, wlim));
         if (!ok) break;
         const uint32_t* mrow = mbox + (mr % MBOX_DEPTH) * P2R_MAX_G;
         const int own = (int)mrow[rank];
@@ -1056,7 +1096,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         mbar_arrive(wready);
         bool sent_ok = true;
         if (row == 0) {  // all 128 rows written: send the tile to the other CTAs
-          sent_ok = mbar_wait(wready, mr & 1, abort);
+          sent_ok = mbar_wait(wready, mr & 1, abort, wlim);
           if (sent_ok) {
             const uint8_t* src = smem + own * SLOT;
             for (int j = 0; j < G; ++j) {
@@ -1077,7 +1117,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
       }
       if (!ok) break;
       if (cvalid) {
-        ok = __all_sync(0xffffffffu, mbar_wait(zfull, uc & 1, abort));
+        ok = __all_sync(0xffffffffu, mbar_wait(zfull, uc & 1, abort, wlim));
         if (!ok) break;
         tc_fence_after();
         float* zrow = a.Zp + ((int64_t)split * a.Spad + s) * a.ldy;
@@ -1107,6 +1147,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
       }
     }
     if (!ok) raise_timeout(abort, status);
+    if (row == 0) bulk_wait0();  // the tiles sent to the peers have landed
   }
   __syncthreads();
   if (warp == 1) {
@@ -1143,10 +1184,10 @@ constexpr int P2I_SLOTS = 4;
 constexpr int P2I_WSLOTS = 2;
 constexpr int P2I_THREADS = 256;  // producer, MMA, 4 epilogue warps, sender, weight producer
 // barriers: full, empty (main ring), wrfull, wrempty (weight ring), sfull, sempty, zfull,
-// zempty, wfull, wfree, cdone, drain; then the mailbox, the TMEM address, the abort flag
+// zempty, wfull, wfree, cdone, drain, never; then the mailbox, the TMEM address, the abort flag
 // and the round counter, in P2I_BOOK bytes
 constexpr int P2I_BOOK = 768;
-static_assert((2 * P2I_SLOTS + 2 * P2I_WSLOTS + 2 + 2 + 1 + 1 + 1 + 1 + 1 + 1) * 8 +
+static_assert((2 * P2I_SLOTS + 2 * P2I_WSLOTS + 2 + 2 + 1 + 1 + 1 + 1 + 1 + 1 + 1) * 8 +
                       MBOX_DEPTH * P2C_MAX_G * 4 + 4 + 4 + 4 <= P2I_BOOK,
               "interleaved-form bookkeeping exceeds its P2I_BOOK bytes");
 static_assert(MBOX_DEPTH >= 4, "the weight producer's lead needs 4 mailbox rows");
@@ -1177,11 +1218,14 @@ __global__ void __launch_bounds__(P2I_THREADS, 1)
   uint64_t* wfree = wfull + 1;   // the MMAs that read the staged tile have completed
   uint64_t* cdone = wfree + 1;   // the copies of the staged tile have read it
   uint64_t* drain = cdone + 1;
-  uint32_t* mbox = (uint32_t*)(drain + 1);  // [MBOX_DEPTH][P2C_MAX_G]
+  uint64_t* never = drain + 1;  // nothing arrives on it (test hook)
+  uint32_t* mbox = (uint32_t*)(never + 1);  // [MBOX_DEPTH][P2C_MAX_G]
   uint32_t* tptr = mbox + MBOX_DEPTH * P2C_MAX_G;
   volatile int* abort = (volatile int*)(tptr + 1);
   volatile uint32_t* rstart = (volatile uint32_t*)(tptr + 2);  // rounds the producer began
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const uint64_t wlim = insts[0].p2.wait_ns;
+  const int hook = insts[0].p2.hook;
   const uint32_t rank = cluster_rank();
   const int64_t cid = blockIdx.x / G, ncl = gridDim.x / G;
 
@@ -1204,6 +1248,7 @@ __global__ void __launch_bounds__(P2I_THREADS, 1)
     mbar_init(wfree, 1);
     mbar_init(cdone, 1);
     mbar_init(drain, 1);
+    mbar_init(never, 1);
     for (int k = 0; k < MBOX_DEPTH * P2C_MAX_G; ++k) mbox[k] = 0u;  // tag 0: no use yet
     *abort = 0;
     *rstart = 0;
@@ -1228,7 +1273,7 @@ __global__ void __launch_bounds__(P2I_THREADS, 1)
       bool ok = true;
       auto reserve = [&]() -> int {
         const int st = it % P2I_SLOTS;
-        if (!mbar_wait(&empty[st], ((it / P2I_SLOTS) & 1) ^ 1, abort)) {
+        if (!mbar_wait(&empty[st], ((it / P2I_SLOTS) & 1) ^ 1, abort, wlim)) {
           ok = false;
           return -1;
         }
@@ -1291,8 +1336,11 @@ __global__ void __launch_bounds__(P2I_THREADS, 1)
           for (; ok && zi < nqp; ++zi) z_fills(zi);
         }
       }
-      if (!ok) {
-        raise_timeout(abort, status);
+      if (!ok) raise_timeout(abort, status);
+      {
+        // the fills already issued land before the CTA exits, also when another role
+        // gave up and stopped consuming them (in a normal run they are all consumed and
+        // these waits return at once)
         const uint32_t lo = it > P2I_SLOTS ? it - P2I_SLOTS : 0;
         int zero = 0;
         for (uint32_t k = lo; k < it; ++k)
@@ -1307,7 +1355,7 @@ __global__ void __launch_bounds__(P2I_THREADS, 1)
       bool ok = true;
       auto wait_slot = [&]() -> int {
         const int st = it % P2I_SLOTS;
-        if (!mbar_wait(&full[st], (it / P2I_SLOTS) & 1, abort)) {
+        if (!mbar_wait(&full[st], (it / P2I_SLOTS) & 1, abort, wlim)) {
           ok = false;
           return -1;
         }
@@ -1339,13 +1387,13 @@ __global__ void __launch_bounds__(P2I_THREADS, 1)
             if (own) {
               // the staged tile of this round is written (tiles without a chunk are
               // still consumed, so that the staging slot is released in order)
-              if (!mbar_wait(wfull, ow & 1, abort)) {
+              if (!mbar_wait(wfull, ow & 1, abort, wlim)) {
                 ok = false;
                 return;
               }
             } else if (cvalid) {
               sw = itw % P2I_WSLOTS;
-              if (!mbar_wait(&wrfull[sw], (itw / P2I_WSLOTS) & 1, abort)) {
+              if (!mbar_wait(&wrfull[sw], (itw / P2I_WSLOTS) & 1, abort, wlim)) {
                 ok = false;
                 return;
               }
@@ -1353,7 +1401,7 @@ __global__ void __launch_bounds__(P2I_THREADS, 1)
             }
             tc_fence_after();
             if (cvalid) {
-              if (first_z && !mbar_wait(zempty, (uc & 1) ^ 1, abort)) {
+              if (first_z && !mbar_wait(zempty, (uc & 1) ^ 1, abort, wlim)) {
                 ok = false;
                 return;
               }
@@ -1386,7 +1434,7 @@ __global__ void __launch_bounds__(P2I_THREADS, 1)
           int zi = 0;
           if ((int)rank < nq) {
             const int b = sc & 1;
-            if (!mbar_wait(&sempty[b], ((sc >> 1) & 1) ^ 1, abort)) {
+            if (!mbar_wait(&sempty[b], ((sc >> 1) & 1) ^ 1, abort, wlim)) {
               ok = false;
               break;
             }
@@ -1435,12 +1483,12 @@ __global__ void __launch_bounds__(P2I_THREADS, 1)
           ++uc;
         }
       }
-      if (!ok) {
-        raise_timeout(abort, status);
-        mma_commit(drain);
-        int zero = 0;
-        mbar_wait(drain, 0, (volatile int*)&zero);
-      }
+      if (!ok) raise_timeout(abort, status);
+      // every issued MMA completes before TMEM is released, also when another role
+      // gave up and left accumulators unread
+      mma_commit(drain);
+      int zero = 0;
+      mbar_wait(drain, 0, (volatile int*)&zero);
     }
   } else if (warp < 6) {
     const int q = warp & 3;
@@ -1475,7 +1523,11 @@ __global__ void __launch_bounds__(P2I_THREADS, 1)
         // use; lse2 = +inf past N gives weight 0
         float ny = a.ybar[ib + lane];
         float nl = (ib + lane < a.N) ? a.lse2[ib + lane] : INFINITY;
-        ok = __all_sync(0xffffffffu, mbar_wait(&sfull[b], (sc >> 1) & 1, abort));
+        // test hook: see pass 1 (the first cluster's rank 0 never builds its first tile,
+        // so its peers' waits for that tile run out as well)
+        const bool held = hook == 2 && blockIdx.x == 0 && sc == 0;
+        ok = __all_sync(0xffffffffu, (!held || mbar_wait(never, 0, abort, wlim)) &&
+                                         mbar_wait(&sfull[b], (sc >> 1) & 1, abort, wlim));
         if (!ok) break;
         tc_fence_after();
         // the weights of this row, as fp16 pairs in the order of the tile's columns; they
@@ -1517,8 +1569,8 @@ __global__ void __launch_bounds__(P2I_THREADS, 1)
         mbar_arrive(&sempty[b]);  // the logits are no longer needed
         // the staging slot is free once the MMAs and the copies of the previous tile
         // have read it
-        ok = __all_sync(0xffffffffu, mbar_wait(wfree, (m & 1) ^ 1, abort) &&
-                                         mbar_wait(cdone, (m & 1) ^ 1, abort));
+        ok = __all_sync(0xffffffffu, mbar_wait(wfree, (m & 1) ^ 1, abort, wlim) &&
+                                         mbar_wait(cdone, (m & 1) ^ 1, abort, wlim));
         if (!ok) break;
         uint8_t* prow = stage + row * 128;
 #pragma unroll
@@ -1535,7 +1587,7 @@ __global__ void __launch_bounds__(P2I_THREADS, 1)
       }
       if (!ok) break;
       if (cvalid) {
-        ok = __all_sync(0xffffffffu, mbar_wait(zfull, uc & 1, abort));
+        ok = __all_sync(0xffffffffu, mbar_wait(zfull, uc & 1, abort, wlim));
         if (!ok) break;
         tc_fence_after();
         float* zrow = a.Zp + ((int64_t)split * a.Spad + s) * a.ldy;
@@ -1586,7 +1638,7 @@ __global__ void __launch_bounds__(P2I_THREADS, 1)
         if (k != (int)rank && cgrp * G + k < a.n_chunks) peers |= 1u << k;
       for (int r0 = 0; ok && r0 < nb; r0 += G) {
         if ((int)rank >= min(G, nb - r0)) continue;
-        if (!mbar_wait(wfull, m & 1, abort)) {
+        if (!mbar_wait(wfull, m & 1, abort, wlim)) {
           ok = false;
           break;
         }
@@ -1606,7 +1658,7 @@ __global__ void __launch_bounds__(P2I_THREADS, 1)
               pending &= ~(1u << k);
             }
           }
-          if (pending && (*abort || globaltimer() - t0 > kWaitTimeoutNs)) {
+          if (pending && (*abort || globaltimer() - t0 > wlim)) {
             ok = false;
             break;
           }
@@ -1646,7 +1698,7 @@ __global__ void __launch_bounds__(P2I_THREADS, 1)
         ++g;
         const uint64_t t0 = globaltimer();
         while (*rstart < g) {
-          if (*abort || globaltimer() - t0 > kWaitTimeoutNs) {
+          if (*abort || globaltimer() - t0 > wlim) {
             ok = false;
             break;
           }
@@ -1662,7 +1714,7 @@ __global__ void __launch_bounds__(P2I_THREADS, 1)
             continue;
           }
           const int sw = itw % P2I_WSLOTS;
-          if (!mbar_wait(&wrempty[sw], ((itw / P2I_WSLOTS) & 1) ^ 1, abort)) {
+          if (!mbar_wait(&wrempty[sw], ((itw / P2I_WSLOTS) & 1) ^ 1, abort, wlim)) {
             ok = false;
             break;
           }
@@ -1826,6 +1878,15 @@ cudaError_t set_p2c_attrs() {
   if (e == cudaSuccess)
     e = cudaFuncSetAttribute(k_p2i_tc<NPROD>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
   return e;
+}
+
+template <int NPROD>
+cudaError_t set_p1_attrs() {
+  return set_smem(k_p1_tc<NPROD>, P1_SMEM);
+}
+template <int NPROD>
+cudaError_t set_p2_attrs() {
+  return set_smem(k_p2_tc<NPROD>, P2_SMEM);
 }
 
 // The cluster form for clusters of G: the ring form up to P2R_MAX_G, the interleaved
@@ -2009,6 +2070,8 @@ void fill_inst(const srmra_ctx* c, TcInst* I) {
   a.pm = c->pm;
   a.ps = c->ps;
   a.status = c->status;
+  a.wait_ns = c->wait_ns;
+  a.hook = c->test_hook;
   TcP2Args& b = I->p2;
   b.nk = a.nk;
   b.n_stiles = g.Spad / 128;
@@ -2031,14 +2094,24 @@ void fill_inst(const srmra_ctx* c, TcInst* I) {
   b.cp = c->cp;
   b.zbp = c->zbp;
   b.status = c->status;
+  b.wait_ns = c->wait_ns;
+  b.hook = c->test_hook;
 }
 
 // Co-resident clusters of G CTAs of the clustered pass-2 kernel of that size (queried
 // once per G); 0 for a cluster size above the portable limit that the GPU cannot place.
 template <int NPROD>
 int max_clusters(int G, int num_sms) {
-  static int cache[P2C_MAX_G + 1] = {};
-  if (cache[G] != 0) return cache[G] > 0 ? cache[G] : 0;
+  // per (device, G): the answer depends on the device's GPC layout
+  static std::mutex mu;
+  static std::map<std::pair<int, int>, int> cache;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) dev = -1;
+  std::lock_guard<std::mutex> lock(mu);
+  {
+    auto hit = cache.find({dev, G});
+    if (hit != cache.end()) return hit->second > 0 ? hit->second : 0;
+  }
   cudaGetLastError();
   set_p2c_attrs<NPROD>();
   const void* fn;
@@ -2060,23 +2133,21 @@ int max_clusters(int G, int num_sms) {
   if (cudaOccupancyMaxActiveClusters(&n, fn, &cfg) != cudaSuccess || n < 1) {
     cudaGetLastError();
     if (G > P2C_PORTABLE_G) {
-      cache[G] = -1;
+      cache[{dev, G}] = -1;
       return 0;
     }
     n = num_sms / G / 2 > 0 ? num_sms / G / 2 : 1;
   }
-  cache[G] = n;
+  cache[{dev, G}] = n;
   return n;
 }
 
 template <int NPROD>
 cudaError_t launch_cluster_p2(int G, const TcInst* d_insts, const int64_t* d_ustart, int n,
                               int64_t total, int* status, cudaStream_t stream, int num_sms) {
-  static bool attr = false;
-  if (!attr) {
-    cudaError_t e = set_p2c_attrs<NPROD>();
+  {
+    cudaError_t e = once_per_device(ATTR_TC_P2C + NPROD, set_p2c_attrs<NPROD>);
     if (e != cudaSuccess) return e;
-    attr = true;
   }
   if (G < 2 || G > P2C_MAX_G) return cudaErrorInvalidValue;
   int ncl = max_clusters<NPROD>(G, num_sms);
@@ -2107,23 +2178,16 @@ cudaError_t launch_cluster_p2(int G, const TcInst* d_insts, const int64_t* d_ust
 template <int NPROD>
 cudaError_t launch_group(int pass, const TcInst* d_insts, const int64_t* d_ustart, int n,
                          int64_t total, int* status, cudaStream_t stream, int num_sms) {
-  static bool attr1 = false, attr2 = false;
   cudaError_t e = cudaSuccess;
   const unsigned grid = (unsigned)(total < num_sms ? total : num_sms);
   if (grid == 0) return cudaSuccess;
   if (pass == 1) {
-    if (!attr1) {
-      e = set_smem(k_p1_tc<NPROD>, P1_SMEM);
-      if (e != cudaSuccess) return e;
-      attr1 = true;
-    }
+    e = once_per_device(ATTR_TC_P1 + NPROD, set_p1_attrs<NPROD>);
+    if (e != cudaSuccess) return e;
     k_p1_tc<NPROD><<<grid, TC_THREADS, P1_SMEM, stream>>>(d_insts, d_ustart, n, status);
   } else {
-    if (!attr2) {
-      e = set_smem(k_p2_tc<NPROD>, P2_SMEM);
-      if (e != cudaSuccess) return e;
-      attr2 = true;
-    }
+    e = once_per_device(ATTR_TC_P2 + NPROD, set_p2_attrs<NPROD>);
+    if (e != cudaSuccess) return e;
     k_p2_tc<NPROD><<<grid, TC_THREADS, P2_SMEM, stream>>>(d_insts, d_ustart, n, status);
   }
   return cudaGetLastError();

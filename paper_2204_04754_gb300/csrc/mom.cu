@@ -15,6 +15,7 @@
 // The products Y^T Y, T^T diag(rho) T and T R run through one float32 tile kernel
 // (k-major operands, 128 x 128 tiles, packed FMA, k split into partials that are summed in
 // float64 in a fixed order); every other reduction is float64 in a fixed order.
+#include <atomic>
 #include <algorithm>
 #include <cmath>
 #include <new>
@@ -612,15 +613,16 @@ cudaError_t mget(srmra_mom* m, T** p, int64_t count) {
 
 // Co-resident blocks of the product kernel on the device (SMs x blocks per SM).
 int gemm_slots(int sms) {
-  static int per_sm = 0;
-  if (per_sm == 0) {
-    int b = 0;
+  // occupancy of a kernel without opt-in shared memory: the same on every GB300
+  static std::atomic<int> per_sm{0};
+  int b = per_sm.load();
+  if (b == 0) {
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_mom_gemm, 256, 0) != cudaSuccess ||
         b < 1)
       b = 1;
-    per_sm = b;
+    per_sm.store(b);
   }
-  return per_sm * sms;
+  return b * sms;
 }
 
 // k splits of a product with `tiles` output tiles: as many as keep all blocks in one

@@ -8,6 +8,8 @@
 // float32 E-step normaliser (observation centring, template preparation, the pass-1
 // kernel and the log-sum-exp combine) with every intermediate buffer placed in one
 // fixed, file-scope device array instead of memory obtained from an allocator.
+#include <cuda.h>
+
 #include <mutex>
 
 #include "srmra_internal.cuh"
@@ -23,23 +25,63 @@ static __device__ __align__(256) unsigned char g_noalloc_scratch[kScratchBytes];
 
 std::mutex g_setup_mutex;
 void* g_scratch_ptr[kMaxDevices] = {};
+unsigned long long g_scratch_ctx[kMaxDevices] = {};  // context the address belongs to
 
-// Device address of the scratch array for the current device (looked up once per
-// device, with that device current).  Host code must not use the symbol itself: on the
-// host it names a stand-in object, not device memory.
+// Unique id of the CUDA context current on this thread (0 if none is current or the
+// driver cannot tell).  A device reset destroys the context and the module with the
+// array, and the next context may place the array elsewhere: the id tells the cached
+// address apart from a stale one.
+unsigned long long current_context_id() {
+  using GetCurrent = CUresult (*)(CUcontext*);
+  using GetId = CUresult (*)(CUcontext, unsigned long long*);
+  static GetCurrent get_current = nullptr;
+  static GetId get_id = nullptr;
+  static bool looked_up = false;
+  if (!looked_up) {  // under g_setup_mutex
+    void* a = nullptr;
+    void* b = nullptr;
+    cudaDriverEntryPointQueryResult qa, qb;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &a, 12000, cudaEnableDefault, &qa) ==
+            cudaSuccess &&
+        qa == cudaDriverEntryPointSuccess &&
+        cudaGetDriverEntryPointByVersion("cuCtxGetId", &b, 12000, cudaEnableDefault, &qb) ==
+            cudaSuccess &&
+        qb == cudaDriverEntryPointSuccess) {
+      get_current = (GetCurrent)a;
+      get_id = (GetId)b;
+    }
+    cudaGetLastError();
+    looked_up = true;
+  }
+  if (!get_current || !get_id) return 0;
+  CUcontext ctx = nullptr;
+  unsigned long long id = 0;
+  if (get_current(&ctx) != CUDA_SUCCESS || !ctx) return 0;
+  if (get_id(ctx, &id) != CUDA_SUCCESS) return 0;
+  return id;
+}
+
+// Device address of the scratch array for the current device, looked up with that
+// device current the first time (and again whenever the device's context is no longer
+// the one the address was taken in, e.g. after a device reset).  Host code must not use
+// the symbol itself: on the host it names a stand-in object, not device memory.
 cudaError_t scratch_for_current_device(void** out) {
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return e;
   if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
   std::lock_guard<std::mutex> lock(g_setup_mutex);
-  if (!g_scratch_ptr[dev]) {
-    void* p = nullptr;
-    e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-    if (e != cudaSuccess) return e;
-    g_scratch_ptr[dev] = p;
+  const unsigned long long id = current_context_id();
+  if (g_scratch_ptr[dev] && id != 0 && id == g_scratch_ctx[dev]) {
+    *out = g_scratch_ptr[dev];
+    return cudaSuccess;
   }
-  *out = g_scratch_ptr[dev];
+  void* p = nullptr;
+  e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+  if (e != cudaSuccess) return e;
+  g_scratch_ptr[dev] = p;
+  g_scratch_ctx[dev] = current_context_id();
+  *out = p;
   return cudaSuccess;
 }
 

@@ -9,9 +9,11 @@
 namespace srmra {
 namespace ptx {
 
-// Bounded waits: a wait that does not complete within this many nanoseconds (read
+// Bounded waits: a wait that does not complete within its limit (nanoseconds, read
 // from %globaltimer) gives up, so that a broken pipeline ends with an error status
-// instead of a hung GPU.
+// instead of a hung GPU.  The kernels pass the context's limit (srmra_set_wait_limit);
+// kWaitTimeoutNs is the default, and the fixed limit of the waits that only drain a
+// CTA's own asynchronous copies and MMAs before it exits.
 constexpr uint64_t kWaitTimeoutNs = 2000000000ull;
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
@@ -58,13 +60,14 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
 // Wait until the phase with the given parity has completed.  Returns false if the
 // wait gave up (timeout, or another role raised *abort).
 __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity,
-                                          volatile int* abort) {
+                                          volatile int* abort,
+                                          uint64_t limit_ns = kWaitTimeoutNs) {
   if (mbar_try_wait(bar, parity)) return true;
   const uint64_t t0 = globaltimer();
   while (true) {
     if (mbar_try_wait(bar, parity)) return true;
     if (*abort) return false;
-    if (globaltimer() - t0 > kWaitTimeoutNs) return false;
+    if (globaltimer() - t0 > limit_ns) return false;
   }
 }
 
@@ -82,13 +85,14 @@ __device__ __forceinline__ bool mbar_try_wait_cluster(uint64_t* bar, uint32_t pa
   return ok != 0;
 }
 __device__ __forceinline__ bool mbar_wait_cluster(uint64_t* bar, uint32_t parity,
-                                                  volatile int* abort) {
+                                                  volatile int* abort,
+                                                  uint64_t limit_ns = kWaitTimeoutNs) {
   if (mbar_try_wait_cluster(bar, parity)) return true;
   const uint64_t t0 = globaltimer();
   while (true) {
     if (mbar_try_wait_cluster(bar, parity)) return true;
     if (*abort) return false;
-    if (globaltimer() - t0 > kWaitTimeoutNs) return false;
+    if (globaltimer() - t0 > limit_ns) return false;
   }
 }
 

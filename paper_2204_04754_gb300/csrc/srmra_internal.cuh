@@ -33,6 +33,19 @@ constexpr int SPAD = 256;   // shift padding (multiple of every s-tile)
 inline int64_t round_up(int64_t a, int64_t b) { return (a + b - 1) / b * b; }
 inline int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }
 
+// Kernel attributes (opt-in shared memory, non-portable cluster sizes) apply to the
+// device that is current when they are set, and a process may hold contexts on several
+// devices.  once_per_device(key, set) runs `set` once for each (current device, key)
+// pair, under a mutex (contexts may be driven from several threads), and remembers only
+// a success.
+enum : int {
+  ATTR_SIMT_P2 = 0,
+  ATTR_TC_P1 = 1,     // + NPROD (1 or 3)
+  ATTR_TC_P2 = 5,     // + NPROD
+  ATTR_TC_P2C = 9,    // + NPROD
+};
+cudaError_t once_per_device(int key, cudaError_t (*set)());
+
 // Geometry of one problem, shared by all kernels.
 struct Geom {
   int L, K, l, l2;  // L_high, factor, L_low, L_low^2
@@ -150,6 +163,8 @@ struct srmra_ctx {
   int64_t launches = 0;
   int64_t device_bytes = 0;   // device memory held by this context
   bool no_cluster = false;    // force the per-chunk pass-2 kernel (SRMRA_FLAG_NO_CLUSTER)
+  uint64_t wait_ns = 2000000000ull;  // limit of the kernels' bounded waits (ns)
+  int test_hook = 0;          // srmra_set_wait_limit test hook (1: pass 1, 2: pass 2)
   int sched_F = 0;            // Algorithm 2 cadence used by batches with F < 0
   int dn_mode = 0;            // built-in denoiser: 0 hard, 1 soft threshold
   bool dn_spin = false;       // average over the 64 block-grid offsets

@@ -68,6 +68,8 @@ def lib() -> ctypes.CDLL:
                                       c_int32]),
         "srmra_get_estep": (c_int32, [c_void_p, c_void_p, c_void_p]),
         "srmra_launch_count": (c_int32, [c_void_p, P(c_int64)]),
+        "srmra_get_plan": (c_int32, [c_void_p, c_void_p, c_int32]),
+        "srmra_set_wait_limit": (c_int32, [c_void_p, c_int64, c_int32]),
         "srmra_sync": (c_int32, [c_void_p]),
         "srmra_profile": (c_int32, [c_void_p, c_int32]),
         "srmra_profile_read": (c_int32, [c_void_p, c_void_p, c_void_p]),
@@ -184,6 +186,21 @@ def srmra_launch_count(ctx: int) -> int:
     n = c_int64()
     _check(lib().srmra_launch_count(ctx, byref(n)), ctx)
     return n.value
+
+
+P2_FORMS = {0: "per_chunk", 1: "ring", 2: "interleaved", 3: "fp32", 4: "fft"}
+
+
+def srmra_set_wait_limit(ctx: int, limit_ns: int, test_hook: int = 0) -> None:
+    _check(lib().srmra_set_wait_limit(ctx, int(limit_ns), int(test_hook)), ctx)
+
+
+def srmra_get_plan(ctx: int) -> dict:
+    v = np.zeros(6, np.int32)
+    _check(lib().srmra_get_plan(ctx, v.ctypes.data, 6), ctx)
+    return {"p1_groups": int(v[0]), "p1_tiles_per_group": int(v[1]), "p2_cluster": int(v[2]),
+            "p2_chunk_groups": int(v[3]), "p2_form": P2_FORMS[int(v[4])],
+            "p2_splits": int(v[5])}
 
 
 PHASES = ["prep", "pass1", "combine", "pass2", "final", "denoise"]
@@ -357,6 +374,14 @@ class Solver:
     @property
     def launches(self) -> int:
         return srmra_launch_count(self.ctx)
+
+    def plan(self) -> dict:
+        """Work decomposition of the context's kernels (srmra_get_plan)."""
+        return srmra_get_plan(self.ctx)
+
+    def set_wait_limit(self, limit_ns: int, test_hook: int = 0):
+        """Limit of the bounded device waits, and the failure-path test hook."""
+        srmra_set_wait_limit(self.ctx, limit_ns, test_hook)
 
     def sync(self):
         srmra_sync(self.ctx)

@@ -117,6 +117,25 @@ def test_gradient_step_decreases_the_objective():
     assert f1 < f0
 
 
+def test_lambda_weight_of_the_first_moment_term():
+    """Eq. (LS_SR) weighs the first-moment residual by lambda = 1 / (L^2 (1 + sigma^2)).
+    With M2^ equal to the model's M2 and M1^ off the model's M1 by a unit vector, the
+    objective is lambda alone: 1/32 at L = 4, sigma = 1 (hand-evaluated: 16 * 2 = 32),
+    and 1/(64 * 1.25) = 0.0125 at L = 8, sigma = 0.5."""
+    for L, K, sigma, lam in [(4, 2, 1.0, 1.0 / 32.0), (8, 2, 0.5, 0.0125)]:
+        x, r1, r2 = small(L, K, seed=L)
+        m1, m2 = M.model_moments(x, r1, r2, sigma, K)
+        e = np.zeros_like(m1)
+        e[1] = 1.0
+        f = M.objective(x, r1, r2, m1 + e, m2, sigma, K)
+        assert abs(f - lam) < 1e-15, (L, sigma, f)
+        # and the second-moment term is unweighted: a unit entry of M2^ - M2 adds 1
+        E = np.zeros_like(m2)
+        E[0, 1] = 1.0
+        f2 = M.objective(x, r1, r2, m1, m2 + E, sigma, K)
+        assert abs(f2 - 1.0) < 1e-12
+
+
 def test_planted_mistakes_are_caught(monkeypatch):
     def fails(check):
         try:
@@ -126,6 +145,7 @@ def test_planted_mistakes_are_caught(monkeypatch):
         return False
 
     orig = M.gradient
+    orig_moments = M.model_moments
 
     def no_four(x, r1, r2, M1h, M2h, sigma, K):  # the x-gradient with 2 R t_s instead of 4
         f, gx, g1, g2 = orig(x, r1, r2, M1h, M2h, sigma, K)
@@ -138,3 +158,18 @@ def test_planted_mistakes_are_caught(monkeypatch):
         np.outer(r1, r2).ravel() @ O.all_templates(np.asarray(x, float), K),
         O.all_templates(np.asarray(x, float), K).T @ O.all_templates(np.asarray(x, float), K)))
     assert fails(test_model_moments_element_by_element)
+    monkeypatch.setattr(M, "model_moments", orig_moments)
+    # lambda without the square on sigma, and without the 1/L^2
+    monkeypatch.setattr(M, "mom_lambda", lambda L, sigma: 1.0 / (L * L * (1.0 + sigma)))
+    assert fails(lambda: (test_lambda_weight_of_the_first_moment_term(),
+                          _lambda_at(8, 0.5, 0.0125)))
+    monkeypatch.setattr(M, "mom_lambda", lambda L, sigma: 1.0 / (1.0 + sigma * sigma))
+    assert fails(test_lambda_weight_of_the_first_moment_term)
+
+
+def _lambda_at(L, sigma, lam):
+    x, r1, r2 = small(L, 2, seed=L)
+    m1, m2 = M.model_moments(x, r1, r2, sigma, 2)
+    e = np.zeros_like(m1)
+    e[0] = 1.0
+    assert abs(M.objective(x, r1, r2, m1 + e, m2, sigma, 2) - lam) < 1e-15

@@ -106,6 +106,23 @@ def test_estep_matches_brute_force(L, K, N, sigma):
         np.testing.assert_allclose(W.sum(axis=1), 1.0, rtol=0, atol=1e-15)
 
 
+@pytest.mark.parametrize("chunk", [None, 1, 3, 7])
+def test_chunked_loglik_matches_brute_force(chunk):
+    """The chunked Eq. (likelihood_EM) of the oracle equals the brute-force sum over
+    observations of log sum_s rho1 rho2 exp(-||y_i - P R_s x||^2 / (2 sigma^2)) (explicit
+    P and R_s matrices, naive normalisation), for any chunk size, and the E-step's LL."""
+    L, K, N, sigma = 6, 2, 8, 0.7
+    rng = np.random.default_rng(321)
+    x = rng.uniform(0, 1, (L, L))
+    Y = rng.uniform(0, 1, (N, L // K, L // K))
+    r1 = synth.uniform_simplex_draw(L, rng)
+    r2 = synth.uniform_simplex_draw(L, rng)
+    _, LLb = brute_force_estep(Y, x, r1, r2, sigma, K)
+    ll = O.loglik(Y, x, r1, r2, sigma, K, chunk=chunk)
+    assert abs(ll - LLb) <= 1e-12 * abs(LLb)
+    assert abs(ll - O.estep(Y, x, r1, r2, sigma, K)[2]) <= 1e-12 * abs(LLb)
+
+
 def test_literal_and_expanded_distances_agree():
     p = synth.make_problem(16, 2, 40, 0.3, seed=11)
     T = O.all_templates(p.x0, 2)
@@ -294,6 +311,19 @@ def test_fft_oracle_matches_dense(L, K, N, sigma):
     assert abs(a[3] - b[3]) <= 1e-12 * abs(a[3])
     for key in ("b", "A", "c", "lse"):
         assert np.linalg.norm(a[4][key] - b[4][key]) <= 1e-12 * np.linalg.norm(a[4][key])
+
+
+@pytest.mark.parametrize("workers", [2, 5])
+def test_fft_oracle_thread_split_matches_dense(workers):
+    """The observation-range split of the FFT oracle (sums over i formed per range and
+    added in order) is the same iteration as the dense definition."""
+    p = synth.make_problem(12, 3, 333, 0.4, seed=77)
+    a = O.em_iter(p.y, p.x0, p.rho1_true, p.rho2_true, 0.4, 3)
+    b = FO.em_iter_fft(p.y, p.x0, p.rho1_true, p.rho2_true, 0.4, 3, chunk=41, workers=workers)
+    for u, v in zip(a[:3], b[:3]):
+        assert np.linalg.norm(u - v) <= 1e-12 * np.linalg.norm(u)
+    assert abs(a[3] - b[3]) <= 1e-12 * abs(a[3])
+    np.testing.assert_allclose(b[4]["lse"], a[4]["lse"], rtol=1e-12)
 
 
 # ---------------------------------------------------------------- denoiser

@@ -119,3 +119,18 @@ def test_unweighted_online_update_is_caught(monkeypatch):
     monkeypatch.setattr(O, "sa_update",
                         lambda S, Sb, g: Sb if S is None else tuple(a + g * b for a, b in zip(S, Sb)))
     assert fails(T.test_online_statistics_average_to_the_full_data_ones)
+
+
+def test_loglik_chunk_overlap_is_caught(monkeypatch):
+    """A chunked log-likelihood whose chunks overlap by one observation."""
+    orig = O.loglik
+
+    def overlapping(Y, x, rho1, rho2, sigma, K, chunk=None):
+        if chunk is None or chunk >= len(Y):
+            return orig(Y, x, rho1, rho2, sigma, K, chunk=chunk)
+        total = 0.0
+        for a in range(0, len(Y), chunk):
+            total += orig(Y[max(0, a - 1):a + chunk], x, rho1, rho2, sigma, K)
+        return total
+    monkeypatch.setattr(O, "loglik", overlapping)
+    assert fails(lambda: T.test_chunked_loglik_matches_brute_force(3))
