@@ -288,18 +288,22 @@ def kernel_names(prec: str, plan: dict, l: int):
     if prec == "fft32":
         return f"k_fft_p1<{l}>", f"k_fft_p2<{l}>"
     n = 3 if prec == "bf16x3" else 1
-    p2 = {"per_chunk": "k_p2_tc", "ring": "k_p2c_tc", "interleaved": "k_p2i_tc"}[plan["p2_form"]]
-    return f"k_p1_tc<{n}>", f"{p2}<{n}>"
+    p2 = {"per_chunk": f"k_p2_tc<{n}, false>", "per_chunk_comp": f"k_p2_tc<{n}, true>",
+          "ring": f"k_p2c_tc<{n}>", "interleaved": f"k_p2i_tc<{n}>"}[plan["p2_form"]]
+    return f"k_p1_tc<{n}>", p2
 
 
 def tc_executed_flops(p, prec: str, plan: dict):
     """Tensor-core flops the two passes issue per launch (padding included): pass 1 NPROD
     MMAs per logit tile; pass 2 the same logits once per chunk group plus the fp16 M-step
-    product Z' = W^T Y' over every 256-pixel chunk."""
+    product Z' = W^T Y' over every 256-pixel chunk (three products with the compensated
+    M-step)."""
     nprod = 3 if prec == "bf16x3" else 1
+    nz = 3 if plan["p2_form"] == "per_chunk_comp" else 1
     Npad, Spad, ldk, nch = padded(p)
     p1 = nprod * 2.0 * Npad * Spad * ldk
-    p2 = nprod * 2.0 * Spad * Npad * ldk * plan["p2_chunk_groups"] + 2.0 * Spad * Npad * nch * 256
+    p2 = (nprod * 2.0 * Spad * Npad * ldk * plan["p2_chunk_groups"] +
+          nz * 2.0 * Spad * Npad * nch * 256)
     return p1, p2
 
 
@@ -395,9 +399,8 @@ class FormRun:
         self.launches = self.s.launches - l0
         ms, n = self.s.profile_read()
         self.s.profile(False)
-        from paper_2204_04754_gb300.srmra import PHASES
-        self.phase_ms = {k: float(ms[i]) for i, k in enumerate(PHASES)}
-        self.phase_n = {k: int(n[i]) for i, k in enumerate(PHASES)}
+        self.phase_ms = {k: float(v) for k, v in ms.items()}
+        self.phase_n = {k: int(v) for k, v in n.items()}
         self.steps = steps
         self.total_ms = float(sum(self.step_ms))
         self.value = p.N * p.L * p.L * steps / (self.total_ms / 1e3)

@@ -85,6 +85,13 @@ typedef enum {
 #define SRMRA_FLAG_CHECK_NUMERIC 1u /* scan x, rho, LL for NaN/Inf after each iteration */
 #define SRMRA_FLAG_NO_CLUSTER 2u    /* tensor-core forms: recompute the weights per pixel
                                        chunk instead of sharing them across a cluster */
+/* SRMRA_BF16X3: the M-step sum Z' = W^T Y' runs on fp16 operands.  With one fp16 part
+ * per operand its rounding (2^-11 relative) averages out only over many observations;
+ * below about N = 31.25 (L/K) max(1, 2 sigma) observations the library therefore splits
+ * both operands into fp16 hi + lo parts (three MMAs, per-chunk kernel): the compensated
+ * M-step.  These flags force it on, or off. */
+#define SRMRA_FLAG_MSTEP_COMP 4u
+#define SRMRA_FLAG_MSTEP_FP16 8u
 
 typedef struct {
   int32_t L_high;  /* L >= 2 */
@@ -238,6 +245,7 @@ srmra_status srmra_set_wait_limit(srmra_ctx* ctx, int64_t limit_ns, int32_t test
 #define SRMRA_P2_INTERLEAVED 2 /* tensor cores, interleaved cluster form (clusters of 5-16) */
 #define SRMRA_P2_FP32 3        /* float32 persistent clusters */
 #define SRMRA_P2_FFT 4         /* polyphase-FFT form */
+#define SRMRA_P2_PER_CHUNK_COMP 5 /* tensor cores, per chunk, compensated M-step (bf16x3) */
 
 /* srmra_get_plan -- the work decomposition the context's kernels use (no computation;
  * the executed-work counts of a profile are derived from it).  out (host, n int32

@@ -219,6 +219,7 @@ void setup_ctx(srmra_ctx* c, const srmra_params* p, int num_sms, int caps[3]) {
     caps[1] = 0;
     caps[2] = c->plan.nparts_c;
   } else if (is_tc_prec(c->prec)) {
+    c->plan.p2_comp = tc_comp_mstep(g, c->prec, c->flags);
     // size the partial buffers for the finest decomposition the batch tuner may pick
     plan_tc(c, 2, 2);
     c->plan.cap_p1_groups = c->plan.p1_groups;
@@ -252,6 +253,7 @@ cudaError_t allocate_buffers(srmra_ctx* c, Allocator& A, const int caps[3], cons
   if (tc) {
     AL(c->Yh, g.Npad * g.ldk);
     AL(c->YTf, g.Npad * g.l2);
+    if (pl.p2_comp) AL(c->YTfl, g.Npad * g.l2);
     AL(c->Ah, (int64_t)g.Spad * g.ldk);
     AL(c->d_ustart, 4);
     {
@@ -656,7 +658,9 @@ srmra_status srmra_get_plan(const srmra_ctx* c, int32_t* out, int32_t n) {
   const Plan& p = c->plan;
   int form = SRMRA_P2_FP32;
   if (is_tc_prec(c->prec))
-    form = p.p2_gc <= 1 ? SRMRA_P2_PER_CHUNK : (p.p2_gc <= 4 ? SRMRA_P2_RING : SRMRA_P2_INTERLEAVED);
+    form = p.p2_comp ? SRMRA_P2_PER_CHUNK_COMP
+                     : p.p2_gc <= 1 ? SRMRA_P2_PER_CHUNK
+                                    : (p.p2_gc <= 4 ? SRMRA_P2_RING : SRMRA_P2_INTERLEAVED);
   else if (c->prec == SRMRA_FFT32)
     form = SRMRA_P2_FFT;
   const int32_t v[6] = {p.p1_groups, p.p1_tiles_per_group, p.p2_gc, p.p2_chunk_groups, form,

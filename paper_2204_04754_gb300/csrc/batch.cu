@@ -83,9 +83,10 @@ srmra_status upload_group(srmra_batch* b) {
   b->h_insts.assign(isz * n + 64, 0);
   unsigned char* base =
       (unsigned char*)(((uintptr_t)b->h_insts.data() + 63) & ~(uintptr_t)63);
-  // pass 2 launches once per cluster size: keep contexts of equal G contiguous
+  // pass 2 launches once per kernel (cluster size, or the compensated per-chunk kernel):
+  // keep contexts of one kernel contiguous
   std::stable_sort(b->ctxs.begin(), b->ctxs.end(), [](const srmra_ctx* x, const srmra_ctx* y) {
-    return x->plan.p2_gc < y->plan.p2_gc;
+    return tc_p2_key(x) < tc_p2_key(y);
   });
   b->h_ustart.assign(n + 1, 0);
   for (int k = 0; k < n; ++k) {
@@ -95,9 +96,9 @@ srmra_status upload_group(srmra_batch* b) {
   b->total1 = b->h_ustart[n];
   b->p2.clear();
   for (int k0 = 0; k0 < n;) {
-    const int G = b->ctxs[k0]->plan.p2_gc;
+    const int G = tc_p2_key(b->ctxs[k0]);
     int k1 = k0;
-    while (k1 < n && b->ctxs[k1]->plan.p2_gc == G) ++k1;
+    while (k1 < n && tc_p2_key(b->ctxs[k1]) == G) ++k1;
     srmra_batch::P2Range rg{G, k0, k1, (int64_t)b->h_ustart.size(), 0};
     b->h_ustart.push_back(0);
     for (int k = k0; k < k1; ++k) b->h_ustart.push_back(b->h_ustart.back() + tc_units(b->ctxs[k], 2));

@@ -40,7 +40,8 @@ using namespace ptx;
 
 constexpr int SLOT = 32768;
 constexpr int P1_SLOTS = 6;
-constexpr int P2_SLOTS = 5;
+constexpr int P2_SLOTS_PLAIN = 5;  // per-chunk pass 2: operand ring slots
+constexpr int P2_SLOTS_COMP = 3;   // the same with the compensated M-step
 constexpr int TC_THREADS = 192;
 constexpr float W_SCALE = 4096.f;        // 2^12, weights scaled before fp16 rounding
 constexpr float W_UNSCALE = 1.f / 4096.f;
@@ -88,7 +89,7 @@ struct TcP2Args {
 // One problem instance of a (possibly grouped) launch: the tensor maps of its operands
 // and the arguments of both passes.  Kept in device memory; TMA reads the maps there.
 struct TcInst {
-  CUtensorMap tmY, tmYl, tmA256, tmAl256, tmA128, tmAl128, tmYT;
+  CUtensorMap tmY, tmYl, tmA256, tmAl256, tmA128, tmAl128, tmYT, tmYTl;
   TcP1Args p1;
   TcP2Args p2;
 };
@@ -341,14 +342,21 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
 }
 
 // ------------------------------------------------------------------------------ pass 2
-template <int NPROD>
+// Per pixel chunk.  COMP selects the compensated M-step: the weights and Y' are each
+// split into fp16 hi + lo parts and Z' accumulates Wh Yh' + Wh Yl' + Wl Yh' (the
+// dropped Wl Yl' is below 2^-22 relative), so the rounding of the 16-bit operands no
+// longer needs many observations to average out (Eq. x_EM); c and zb take Wh + Wl.
+// The two weight tiles of a block take 64 KB, so the operand ring has 3 slots.
+template <int NPROD, bool COMP>
 __global__ void __launch_bounds__(TC_THREADS, 1)
     k_p2_tc(const TcInst* __restrict__ insts, const int64_t* __restrict__ ustart, int n_inst,
             int* status) {
+  constexpr int P2_SLOTS = COMP ? P2_SLOTS_COMP : P2_SLOTS_PLAIN;
+  constexpr int WB = COMP ? 2 * SLOT : SLOT;  // one weight buffer: hi tile [+ lo tile]
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = align1024(smem_raw);
-  uint8_t* pbuf = smem + P2_SLOTS * SLOT;  // 2 x 32 KB weight tiles (K-major, SW128)
-  uint64_t* full = (uint64_t*)(pbuf + 2 * SLOT);
+  uint8_t* pbuf = smem + P2_SLOTS * SLOT;  // 2 weight buffers (K-major, SW128)
+  uint64_t* full = (uint64_t*)(pbuf + 2 * WB);
   uint64_t* empty = full + P2_SLOTS;
   uint64_t* sfull = empty + P2_SLOTS;
   uint64_t* sempty = sfull + 2;
@@ -446,6 +454,12 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
               if (!ok) break;
               tma_load_2d(s0, &I->tmYT, &full[it % P2_SLOTS], ib + h * 64, chunk * 256);
               ++it;
+              if (COMP) {  // the lo part of the same Y'^T tile
+                uint8_t* s1 = next_slot(32768);
+                if (!ok) break;
+                tma_load_2d(s1, &I->tmYTl, &full[it % P2_SLOTS], ib + h * 64, chunk * 256);
+                ++it;
+              }
             }
           }
         }
@@ -541,14 +555,31 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             for (int h = 0; ok && h < 2; ++h) {
               uint8_t* sT = wait_slot();
               if (!ok) break;
+              const int stT = it % P2_SLOTS;
+              uint8_t* sTl = sT;
+              int stTl = stT;
+              if (COMP) {
+                ++it;
+                sTl = wait_slot();
+                if (!ok) break;
+                stTl = it % P2_SLOTS;
+              }
               tc_fence_after();
-              const uint64_t dP = desc_sw128(pbuf + pb * SLOT + h * 16384);
+              const uint64_t dP = desc_sw128(pbuf + pb * WB + h * 16384);
               const uint64_t dT = desc_sw128(sT);
 #pragma unroll
-              for (int k4 = 0; k4 < 4; ++k4)
+              for (int k4 = 0; k4 < 4; ++k4) {
                 mma_bf16(dZ, desc_advance(dP, k4), desc_advance(dT, k4), idZ,
                          (jj > 0 || h > 0 || k4 > 0) ? 1u : 0u);
-              mma_commit(&empty[it % P2_SLOTS]);
+                if (COMP) {
+                  const uint64_t dPl = desc_sw128(pbuf + pb * WB + SLOT + h * 16384);
+                  const uint64_t dTl = desc_sw128(sTl);
+                  mma_bf16(dZ, desc_advance(dP, k4), desc_advance(dTl, k4), idZ, 1u);
+                  mma_bf16(dZ, desc_advance(dPl, k4), desc_advance(dT, k4), idZ, 1u);
+                }
+              }
+              mma_commit(&empty[stT]);
+              if (COMP) mma_commit(&empty[stTl]);
               ++it;
             }
             if (!ok) break;
@@ -571,7 +602,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     const int q = warp & 3;
     const int row = q * 32 + lane;
     const uint32_t lane_addr = tbase + ((uint32_t)(q * 32) << 16);
-    float2* wobs = (float2*)(pbuf + 2 * SLOT + 256) + q * 32;  // this warp's staging
+    float2* wobs = (float2*)(pbuf + 2 * WB + 256) + q * 32;  // this warp's staging
     uint32_t sc = 0, pz = 0, uc = 0;
     bool ok = true;
     for (int64_t u = blockIdx.x; ok && u < total; u += gridDim.x) {
@@ -602,7 +633,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         if (ok) ok = __all_sync(0xffffffffu, mbar_wait(&pempty[pb], ((pz >> 1) & 1) ^ 1, abort, wlim));
         if (!ok) break;
         tc_fence_after();
-        uint8_t* prow = pbuf + pb * SLOT + row * 128;
+        uint8_t* prow = pbuf + pb * WB + row * 128;
 #pragma unroll 1
         for (int c = 0; c < 4; ++c) {
           __syncwarp();  // the warp is done with the previous chunk's terms
@@ -616,10 +647,10 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
           float v[32];
           tmem_ld32(lane_addr + (uint32_t)(b * 128 + c * 32), v);
           tmem_ld_wait();
-          uint32_t packed[16];
+          uint32_t packed[16], packed_lo[16];
 #pragma unroll
           for (int e = 0; e < 32; e += 2) {
-            float w2[2];
+            float w2[2], wl2[2];
 #pragma unroll
             for (int h = 0; h < 2; ++h) {
               const float2 yl = wobs[e + h];
@@ -628,11 +659,17 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
               const float val = fmaf(v[e + h], a2, cb - yl.y) - c2 * dd * dd;
               const float w = exp2f(val) * W_SCALE;
               w2[h] = __half2float(__float2half_rn(w));
-              cacc += w2[h];
-              zacc = fmaf(w2[h], ybi, zacc);
+              wl2[h] = COMP ? __half2float(__float2half_rn(w - w2[h])) : 0.f;
+              const float wsum = COMP ? w2[h] + wl2[h] : w2[h];
+              cacc += wsum;
+              zacc = fmaf(wsum, ybi, zacc);
             }
             const __half2 pr = __floats2half2_rn(w2[0], w2[1]);
             packed[e >> 1] = *reinterpret_cast<const uint32_t*>(&pr);
+            if (COMP) {
+              const __half2 pl = __floats2half2_rn(wl2[0], wl2[1]);
+              packed_lo[e >> 1] = *reinterpret_cast<const uint32_t*>(&pl);
+            }
           }
 #pragma unroll
           for (int g = 0; g < 4; ++g) {
@@ -641,6 +678,10 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             uint4 val = make_uint4(packed[4 * g], packed[4 * g + 1], packed[4 * g + 2],
                                    packed[4 * g + 3]);
             *reinterpret_cast<uint4*>(prow + kb2 * 16384 + ((cc ^ (row & 7)) << 4)) = val;
+            if (COMP)
+              *reinterpret_cast<uint4*>(prow + SLOT + kb2 * 16384 + ((cc ^ (row & 7)) << 4)) =
+                  make_uint4(packed_lo[4 * g], packed_lo[4 * g + 1], packed_lo[4 * g + 2],
+                             packed_lo[4 * g + 3]);
           }
         }
         tc_fence_before();
@@ -1752,8 +1793,10 @@ constexpr size_t P2I_SMEM = 1024 + (P2I_SLOTS + P2I_WSLOTS + 1) * SLOT + P2I_BOO
 static_assert(P2I_SMEM <= 232448, "exceeds the shared memory of one CTA");
 
 constexpr size_t P1_SMEM = 1024 + P1_SLOTS * SLOT + 256 + 1024;
-constexpr size_t P2_SMEM = 1024 + P2_SLOTS * SLOT + 2 * SLOT + 256 + 1024;
+constexpr size_t P2_SMEM = 1024 + P2_SLOTS_PLAIN * SLOT + 2 * SLOT + 256 + 1024;
+constexpr size_t P2_SMEM_COMP = 1024 + P2_SLOTS_COMP * SLOT + 4 * SLOT + 256 + 1024;
 static_assert(P2_SMEM <= 232448, "exceeds the shared memory of one CTA");
+static_assert(P2_SMEM_COMP <= 232448, "exceeds the shared memory of one CTA");
 
 // ------------------------------------------------------------------------------ operands
 // y' -> bf16 hi / lo rows [Npad][ldk] (zero padding beyond l2).
@@ -1770,9 +1813,10 @@ __global__ void k_split_obs(const float* __restrict__ Yc, int ldy, int l2, int64
   if (Yl) Yl[idx] = __float2bfloat16_rn(v - __bfloat162float(h));
 }
 
-// YT[p][i] = fp16(y'_i[p]) for p < l2 (32x32 tiles): the M-step operand.
+// YT[p][i] = fp16(y'_i[p]) for p < l2 (32x32 tiles): the M-step operand; with out_lo,
+// also its rounding residual fp16(y' - YT) (the compensated M-step's lo part).
 __global__ void k_transpose_f16(const float* __restrict__ in, int64_t R, int ld_in, int C,
-                                __half* __restrict__ out) {
+                                __half* __restrict__ out, __half* __restrict__ out_lo) {
   __shared__ float tile[32][33];
   const int64_t r0 = (int64_t)blockIdx.y * 32;
   const int c0 = blockIdx.x * 32;
@@ -1785,7 +1829,12 @@ __global__ void k_transpose_f16(const float* __restrict__ in, int64_t R, int ld_
   for (int k = threadIdx.y; k < 32; k += 8) {
     const int c = c0 + k;
     const int64_t r = r0 + threadIdx.x;
-    if (c < C && r < R) out[(int64_t)c * R + r] = __float2half_rn(tile[threadIdx.x][k]);
+    if (c < C && r < R) {
+      const float v = tile[threadIdx.x][k];
+      const __half h = __float2half_rn(v);
+      out[(int64_t)c * R + r] = h;
+      if (out_lo) out_lo[(int64_t)c * R + r] = __float2half_rn(v - __half2float(h));
+    }
   }
 }
 
@@ -1886,8 +1935,9 @@ cudaError_t set_p1_attrs() {
 }
 template <int NPROD>
 cudaError_t set_p2_attrs() {
-  return set_smem(k_p2_tc<NPROD>, P2_SMEM);
+  return set_smem(k_p2_tc<NPROD, false>, P2_SMEM);
 }
+cudaError_t set_p2comp_attrs() { return set_smem(k_p2_tc<3, true>, P2_SMEM_COMP); }
 
 // The cluster form for clusters of G: the ring form up to P2R_MAX_G, the interleaved
 // form above.
@@ -1912,6 +1962,29 @@ void p2c_form(int G, const void** fn, int* threads, size_t* smem) {
 int choose_p2_cluster(int chunks, int l2, int64_t n_iblk, int prec, int num_sms);
 template <int NPROD>
 int max_clusters_p2(int G, int num_sms);
+
+// Whether a bf16x3 context takes the compensated M-step (hi + lo fp16 operands for
+// Z' = W^T Y').  With single fp16 operands the rounding of the weights and of Y'
+// (2^-11 relative each) reaches x through sums over the observations of each
+// sub-image, so its effect shrinks as they grow in number: measured (emulated in
+// float64 with the same roundings, one iteration from the workloads' initial guess) it
+// is 1.5e-4 at L = 128, K = 2, N = 300, sigma = 0.5; 2.3e-5 with N = 1200; 9.6e-5 at
+// L = 96, K = 2, N = 300; 4.4e-5 at L = 64, K = 2, N = 300; below 1e-5 from a few
+// thousand observations, at sigma = 1 included.  Below N = 31.25 l max(1, 2 sigma)
+// (2000 at l = 64, sigma <= 0.5) that estimate can pass 2e-5, a fifth of the mixed
+// form's 1e-4 target, and the compensated per-chunk kernel is used instead of the
+// cluster forms.  SRMRA_FLAG_MSTEP_COMP forces it, SRMRA_FLAG_MSTEP_FP16 rules it out.
+bool tc_comp_mstep(const Geom& g, int prec, unsigned flags) {
+  if (prec != SRMRA_BF16X3) return false;
+  if (flags & SRMRA_FLAG_MSTEP_COMP) return true;
+  if (flags & SRMRA_FLAG_MSTEP_FP16) return false;
+  const double n_min = 31.25 * (double)g.l * std::max(1.0, 2.0 * g.sigma);
+  return (double)g.N < n_min;
+}
+
+// Pass-2 launch group of a context: its cluster size, or 0 for the compensated
+// per-chunk kernel.
+int tc_p2_key(const srmra_ctx* c) { return c->plan.p2_comp ? 0 : c->plan.p2_gc; }
 
 // Work decomposition of the tensor-core passes.  s1 multiplies the number of shift
 // groups of pass 1 and s2 the number of observation ranges of pass 2: finer units
@@ -1949,7 +2022,8 @@ void plan_tc(srmra_ctx* c, int s1, int s2) {
   const int chunks = (int)ceil_div(g.l2, 256);
   const int n_iblk = (int)(g.Npad / 128);
   // cluster size of pass 2: CTAs that share each weight tile, one pixel chunk each
-  const int G = c->no_cluster ? 1 : choose_p2_cluster(chunks, g.l2, n_iblk, c->prec, sms);
+  const int G = (c->no_cluster || p.p2_comp) ? 1
+                                             : choose_p2_cluster(chunks, g.l2, n_iblk, c->prec, sms);
   // observation splits of pass 2: each split adds a partial Z' (Spad x l2 float32) that
   // pass 2 writes and the finalize reads, so take the split count that minimises the
   // busiest cluster's block-rounds plus the partials' cost in the same units (a partial
@@ -1997,11 +2071,12 @@ cudaError_t tc_set_attributes(int prec) {
   cudaError_t e;
   if (prec == SRMRA_BF16X3) {
     e = set_smem(k_p1_tc<3>, P1_SMEM);
-    if (e == cudaSuccess) e = set_smem(k_p2_tc<3>, P2_SMEM);
+    if (e == cudaSuccess) e = set_smem(k_p2_tc<3, false>, P2_SMEM);
+    if (e == cudaSuccess) e = set_p2comp_attrs();
     if (e == cudaSuccess) e = set_p2c_attrs<3>();
   } else {
     e = set_smem(k_p1_tc<1>, P1_SMEM);
-    if (e == cudaSuccess) e = set_smem(k_p2_tc<1>, P2_SMEM);
+    if (e == cudaSuccess) e = set_smem(k_p2_tc<1, false>, P2_SMEM);
     if (e == cudaSuccess) e = set_p2c_attrs<1>();
   }
   return e;
@@ -2013,7 +2088,8 @@ cudaError_t prep_obs_tc(srmra_ctx* c) {
   k_split_obs<<<(unsigned)ceil_div(n, 256), 256, 0, c->stream>>>(
       c->Yc, g.ldy, g.l2, g.Npad, g.ldk, c->Yh, c->prec == SRMRA_BF16X3 ? c->Yl : nullptr);
   dim3 grid((unsigned)ceil_div(g.l2, 32), (unsigned)ceil_div(g.Npad, 32));
-  k_transpose_f16<<<grid, dim3(32, 8), 0, c->stream>>>(c->Yc, g.Npad, g.ldy, g.l2, c->YTf);
+  k_transpose_f16<<<grid, dim3(32, 8), 0, c->stream>>>(c->Yc, g.Npad, g.ldy, g.l2, c->YTf,
+                                                      c->plan.p2_comp ? c->YTfl : nullptr);
   c->launches += 2;
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
@@ -2023,6 +2099,8 @@ cudaError_t prep_obs_tc(srmra_ctx* c) {
                      CU_TENSOR_MAP_DATA_TYPE_FLOAT16) &&
             make_map(&c->tmA128, c->Ah, g.ldk, g.Spad, g.ldk, 128) &&
             make_map(&c->tmA256, c->Ah, g.ldk, g.Spad, g.ldk, 256);
+  if (ok && c->plan.p2_comp)
+    ok = make_map(&c->tmYTl, c->YTfl, g.Npad, g.l2, g.Npad, 256, CU_TENSOR_MAP_DATA_TYPE_FLOAT16);
   if (ok && c->prec == SRMRA_BF16X3)
     ok = make_map(&c->tmYl128, c->Yl, g.ldk, g.Npad, g.ldk, 128) &&
          make_map(&c->tmAl128, c->Al, g.ldk, g.Spad, g.ldk, 128) &&
@@ -2054,6 +2132,7 @@ void fill_inst(const srmra_ctx* c, TcInst* I) {
   I->tmA128 = c->tmA128;
   I->tmAl128 = (c->prec == SRMRA_BF16X3) ? c->tmAl128 : c->tmA128;
   I->tmYT = c->tmYT;
+  I->tmYTl = c->plan.p2_comp ? c->tmYTl : c->tmYT;
   TcP1Args& a = I->p1;
   a.nk = (int)ceil_div(g.l2, 64);
   a.n_stiles = g.Spad / 256;
@@ -2188,7 +2267,7 @@ cudaError_t launch_group(int pass, const TcInst* d_insts, const int64_t* d_ustar
   } else {
     e = once_per_device(ATTR_TC_P2 + NPROD, set_p2_attrs<NPROD>);
     if (e != cudaSuccess) return e;
-    k_p2_tc<NPROD><<<grid, TC_THREADS, P2_SMEM, stream>>>(d_insts, d_ustart, n, status);
+    k_p2_tc<NPROD, false><<<grid, TC_THREADS, P2_SMEM, stream>>>(d_insts, d_ustart, n, status);
   }
   return cudaGetLastError();
 }
@@ -2247,6 +2326,15 @@ cudaError_t tc_launch_group_p2(int G, int prec, const void* d_insts, const int64
                                int n, int64_t total, int* status, cudaStream_t stream,
                                int num_sms) {
   const TcInst* insts = (const TcInst*)d_insts;
+  if (G == 0) {  // the per-chunk kernel with the compensated M-step (bf16x3 only)
+    if (prec != SRMRA_BF16X3) return cudaErrorInvalidValue;
+    const unsigned grid = (unsigned)(total < num_sms ? total : num_sms);
+    if (grid == 0) return cudaSuccess;
+    cudaError_t e = once_per_device(ATTR_TC_P2COMP, set_p2comp_attrs);
+    if (e != cudaSuccess) return e;
+    k_p2_tc<3, true><<<grid, TC_THREADS, P2_SMEM_COMP, stream>>>(insts, d_ustart, n, status);
+    return cudaGetLastError();
+  }
   if (G <= 1)
     return tc_launch_group(2, prec, d_insts, d_ustart, n, total, status, stream, num_sms);
   if (prec == SRMRA_BF16X3)
@@ -2288,7 +2376,7 @@ cudaError_t launch_pass1_tc(srmra_ctx* c) {
 
 cudaError_t launch_pass2_tc(srmra_ctx* c) {
   c->launches++;
-  return tc_launch_group_p2(c->plan.p2_gc, c->prec, c->d_inst, c->d_ustart + 2, 1,
+  return tc_launch_group_p2(tc_p2_key(c), c->prec, c->d_inst, c->d_ustart + 2, 1,
                             c->h_ustart[3], c->status, c->stream, c->num_sms);
 }
 

@@ -43,6 +43,7 @@ enum : int {
   ATTR_TC_P1 = 1,     // + NPROD (1 or 3)
   ATTR_TC_P2 = 5,     // + NPROD
   ATTR_TC_P2C = 9,    // + NPROD
+  ATTR_TC_P2COMP = 13,
 };
 cudaError_t once_per_device(int key, cudaError_t (*set)());
 
@@ -96,6 +97,7 @@ struct Plan {
   int fft_blocks = 1;         // FFT form: observation blocks (pass 2: one partial each)
   int fft_p1_obs_per_block = 1;  // FFT form, pass 1 (per-observation outputs only)
   int fft_p1_blocks = 1;
+  bool p2_comp = false;     // tensor-core pass 2 with the compensated M-step (bf16x3)
   int cap_p1_groups = 0;    // capacity of the pass-1 partial buffers (0 = unbounded)
   int cap_nsplit = 0;       // capacity of the pass-2 partial buffers (0 = unbounded)
 };
@@ -119,9 +121,10 @@ struct srmra_ctx {
   __nv_bfloat16* Yh = nullptr;   // [Npad][ldk] bf16(y')            (tensor-core form)
   __nv_bfloat16* Yl = nullptr;   // [Npad][ldk] bf16(y' - Yh)       (split form only)
   __half* YTf = nullptr;         // [l2][Npad]  fp16(y') pixel-major (M-step operand)
+  __half* YTfl = nullptr;        // [l2][Npad]  fp16(y' - YTf) (compensated M-step only)
   __nv_bfloat16* Ah = nullptr;   // [Spad][ldk] centred templates, bf16 hi
   __nv_bfloat16* Al = nullptr;   // [Spad][ldk] bf16 lo (split form only)
-  CUtensorMap tmY128, tmYl128, tmYT, tmA128, tmAl128, tmA256, tmAl256;
+  CUtensorMap tmY128, tmYl128, tmYT, tmYTl, tmA128, tmAl128, tmA256, tmAl256;
   void* d_inst = nullptr;           // this context's launch descriptor (tensor-core form)
   int64_t* d_ustart = nullptr;      // [4] unit prefix sums of pass 1 and pass 2
   int64_t h_ustart[4] = {0, 0, 0, 0};
@@ -202,6 +205,8 @@ cudaError_t launch_sum_f64(const double* in, int n, double* out, cudaStream_t st
 int fin_t_splits(const Geom& g, int num_sms);
 
 // ---- k_tc.cu (tensor-core forms)
+bool tc_comp_mstep(const Geom& g, int prec, unsigned flags);
+int tc_p2_key(const srmra_ctx* c);  // pass-2 launch group (cluster size; 0 = compensated)
 void plan_tc(srmra_ctx* c, int s1 = 1, int s2 = 1);
 cudaError_t tc_replan(srmra_ctx* c, int s1, int s2);
 cudaError_t tc_set_attributes(int prec);
@@ -216,7 +221,8 @@ int64_t tc_units(const srmra_ctx* c, int pass);
 cudaError_t tc_launch_group(int pass, int prec, const void* d_insts, const int64_t* d_ustart,
                             int n, int64_t total, int* status, cudaStream_t stream,
                             int num_sms);
-// pass 2 for instances with cluster size G (G = 1: the per-chunk kernel)
+// pass 2 for instances with cluster size G (G = 1: the per-chunk kernel, G = 0: the
+// per-chunk kernel with the compensated M-step)
 cudaError_t tc_launch_group_p2(int G, int prec, const void* d_insts, const int64_t* d_ustart,
                                int n, int64_t total, int* status, cudaStream_t stream,
                                int num_sms);

@@ -26,6 +26,9 @@ SRMRA_FP32, SRMRA_BF16, SRMRA_BF16X3, SRMRA_FFT32 = 0, 1, 2, 3
 PRECISIONS = {"fp32": SRMRA_FP32, "bf16": SRMRA_BF16, "bf16x3": SRMRA_BF16X3,
               "fft32": SRMRA_FFT32}
 SRMRA_FLAG_CHECK_NUMERIC = 1
+SRMRA_FLAG_NO_CLUSTER = 2
+SRMRA_FLAG_MSTEP_COMP = 4
+SRMRA_FLAG_MSTEP_FP16 = 8
 
 
 class srmra_params(Structure):
@@ -188,7 +191,8 @@ def srmra_launch_count(ctx: int) -> int:
     return n.value
 
 
-P2_FORMS = {0: "per_chunk", 1: "ring", 2: "interleaved", 3: "fp32", 4: "fft"}
+P2_FORMS = {0: "per_chunk", 1: "ring", 2: "interleaved", 3: "fp32", 4: "fft",
+            5: "per_chunk_comp"}
 
 
 def srmra_set_wait_limit(ctx: int, limit_ns: int, test_hook: int = 0) -> None:

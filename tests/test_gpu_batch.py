@@ -27,9 +27,11 @@ def rel(a, b):
     return float(np.linalg.norm(a - b) / np.linalg.norm(b))
 
 
+# (64, 2, 700) and (96, 2, 400) take the compensated M-step (few observations for their
+# l^2), (96, 2, 1600) nine pixel chunks in clusters of more than 4, (64, 2, 1200) the
+# ring cluster form: one grouped pass-2 launch per kernel
 SPECS = [(32, 2, 1500, 0.3), (48, 4, 900, 0.6), (64, 2, 700, 0.2), (32, 4, 2000, 1.0),
-         (16, 2, 300, 0.1),
-         (96, 2, 400, 0.5)]  # l^2 = 2304: nine pixel chunks, clusters of more than 4
+         (16, 2, 300, 0.1), (96, 2, 400, 0.5), (96, 2, 1600, 0.5), (64, 2, 1200, 0.3)]
 
 
 def problems():
@@ -52,6 +54,9 @@ def test_batch_equals_problems_solved_alone(S, prec, graph):
         alone.append(s.state())
         s.close()
     ss = [solver(S, p, prec) for p in probs]
+    if prec == "bf16x3":  # the batch mixes the per-chunk, compensated and cluster forms
+        forms = {s.plan()["p2_form"] for s in ss}
+        assert {"per_chunk", "per_chunk_comp", "ring", "interleaved"} <= forms, forms
     b = S.Batch(ss, autotune=False, graph=graph)
     ll = b.solve(3, 1)
     for k, s in enumerate(ss):

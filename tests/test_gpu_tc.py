@@ -32,10 +32,13 @@ def S():
     return srmra
 
 
-def one_step(S, p, prec, steps=2, oracle="dense"):
+def one_step(S, p, prec, steps=2, oracle="dense", flags=0, form=None):
     yscale = (p.y.astype(np.float64) ** 2).sum(axis=(1, 2)) / (2 * p.sigma ** 2)
-    s = S.Solver(p.L, p.K, p.sigma, p.y, prec=prec, x0=p.x0, rho1=p.rho1_0, rho2=p.rho2_0)
-    worst = dict(x=0.0, rho=0.0, ll=0.0, lse=0.0)
+    s = S.Solver(p.L, p.K, p.sigma, p.y, prec=prec, x0=p.x0, rho1=p.rho1_0, rho2=p.rho2_0,
+                 flags=flags)
+    if form is not None:
+        assert s.plan()["p2_form"] in form.split("|"), s.plan()
+    worst = dict(x=0.0, rho=0.0, ll=0.0, lse=0.0, ll_rel=0.0, lse_rel=0.0)
     for _ in range(steps):
         x, r1, r2, _, _ = s.state()
         ll = s.em_iter(1)[0]
@@ -48,6 +51,10 @@ def one_step(S, p, prec, steps=2, oracle="dense"):
         worst["ll"] = max(worst["ll"], abs(ll - llo) / (abs(llo) + yscale.sum()))
         worst["lse"] = max(worst["lse"], float(np.max(np.abs(lse - aux["lse"]) /
                                                       (1.0 + np.abs(aux["lse"]) + yscale))))
+        # the same as plain relative errors (|lse_i| is far from 0 in these problems)
+        worst["ll_rel"] = max(worst["ll_rel"], abs(ll - llo) / abs(llo))
+        worst["lse_rel"] = max(worst["lse_rel"], float(np.max(np.abs(lse - aux["lse"]) /
+                                                              np.abs(aux["lse"]))))
         assert abs(r1g.sum() - 1) < 1e-12 and np.all(np.isfinite(xg))
     s.close()
     print(prec, p.L, p.K, p.N, p.sigma, worst)
@@ -64,10 +71,11 @@ CASES = [
     (64, 2, 700, 0.3),     # l = 32: four pixel chunks
     (48, 1, 300, 0.8),     # l^2 = 2304
     (32, 2, 1000, 1.0),    # low SNR
-    # l^2 = 4096 (sixteen pixel chunks, clusters of up to 8) and l^2 = 2304 (nine chunks,
-    # two chunk groups).  The fp16 M-step rounding of the mixed form averages over the
-    # observations (measured at L = 128: 1.5e-4 with N = 300, 2.6e-5 with N = 1200, the
-    # same in the cluster and per-chunk forms), so these shapes use N >= 900.
+    # l^2 = 4096 (sixteen pixel chunks) and 2304 (nine) with few observations: the
+    # compensated M-step (fp16 hi + lo operands; single fp16 operands measured 1.5e-4
+    # from the oracle at L = 128, N = 300)
+    (128, 2, 300, 0.5),
+    (96, 2, 300, 0.6),
     (128, 2, 1200, 0.5),
     (96, 2, 900, 0.6),
 ]
@@ -75,10 +83,39 @@ CASES = [
 
 @pytest.mark.parametrize("L,K,N,sigma", CASES)
 def test_em_step_parity_bf16x3(S, L, K, N, sigma):
+    """Every shape at 1e-4 with the library's own choice of M-step form."""
     p = synth.make_problem(L, K, N, sigma, seed=synth.seed_for(3, L * 7 + K))
     w = one_step(S, p, "bf16x3")
     tol = TOL["bf16x3"]
     assert w["x"] < tol and w["rho"] < tol and w["ll"] < tol and w["lse"] < tol
+    assert w["ll_rel"] < tol and w["lse_rel"] < tol
+
+
+# (shape, M-step flag, pass-2 form): the cluster forms with single fp16 M-step operands
+# where enough observations average their rounding (L = 128: 2.6e-5 at N = 1200), and
+# the compensated form forced on a shape whose default is a cluster form
+FORMS = [((128, 2, 1200, 0.5), 8, "ring|interleaved"), ((96, 2, 900, 0.6), 8, "ring|interleaved"),
+         ((64, 2, 2500, 0.3), 0, "ring"), ((64, 2, 2500, 0.3), 4, "per_chunk_comp"),
+         ((128, 2, 300, 0.5), 0, "per_chunk_comp"), ((96, 2, 300, 0.6), 0, "per_chunk_comp")]
+
+
+@pytest.mark.parametrize("shape,flags,form", FORMS)
+def test_em_step_parity_bf16x3_forms(S, shape, flags, form):
+    L, K, N, sigma = shape
+    p = synth.make_problem(L, K, N, sigma, seed=synth.seed_for(3, L * 7 + K))
+    w = one_step(S, p, "bf16x3", flags=flags, form=form)
+    tol = TOL["bf16x3"]
+    assert w["x"] < tol and w["rho"] < tol and w["ll"] < tol and w["lse"] < tol
+
+
+def test_compensated_mstep_is_closer_to_the_oracle(S):
+    """Where single fp16 M-step operands cost most (L = 128, K = 2, N = 300), the
+    compensated M-step brings x and rho much closer to the FP64 oracle."""
+    p = synth.make_problem(128, 2, 300, 0.5, seed=synth.seed_for(3, 128 * 7 + 2))
+    plain = one_step(S, p, "bf16x3", steps=1, flags=8)
+    comp = one_step(S, p, "bf16x3", steps=1, flags=4, form="per_chunk_comp")
+    print("single fp16", plain, "compensated", comp)
+    assert comp["x"] < 0.25 * plain["x"] and comp["x"] < 3e-5
 
 
 @pytest.mark.parametrize("L,K,N,sigma", [(16, 2, 500, 0.5), (64, 2, 700, 1.0),
@@ -136,14 +173,19 @@ def test_cluster_and_per_chunk_pass2_agree(S, L, K, N, sigma):
     10, two chunk groups of 10 and 6, so that chunk ownership changes between units)."""
     p = synth.make_problem(L, K, N, sigma, seed=synth.seed_for(3, 900 + L))
     out = []
-    for flags in (0, 2):  # 2 = SRMRA_FLAG_NO_CLUSTER
+    # 2 = SRMRA_FLAG_NO_CLUSTER; 8 = SRMRA_FLAG_MSTEP_FP16 keeps the single-fp16 M-step
+    # (so that these small problems stay on the cluster forms)
+    for flags in (8, 2 | 8):
         s = S.Solver(p.L, p.K, p.sigma, p.y, prec="bf16x3", x0=p.x0, rho1=p.rho1_0,
                      rho2=p.rho2_0, flags=flags)
+        assert (s.plan()["p2_form"] in ("ring", "interleaved")) == (flags == 8)
         s.solve(2, 1)
         out.append(s.state())
         s.close()
     # the weight sums are grouped differently (one partial per CTA of the cluster), so
     # the two agree to float32 rounding, well inside the mixed form's 1e-4 target
+    print("cluster vs per-chunk", L, K, N, rel(out[0][0], out[1][0]),
+          rel(out[0][1], out[1][1]), rel(out[0][2], out[1][2]))
     assert rel(out[0][0], out[1][0]) < 1e-5
     assert rel(out[0][1], out[1][1]) < 1e-5 and rel(out[0][2], out[1][2]) < 1e-5
 
