@@ -70,6 +70,8 @@ def parse():
                     help="precision: per-iteration one-step errors of every form against "
                          "the FP64 oracle over a projected run")
     ap.add_argument("--study-iters", type=int, default=40)
+    ap.add_argument("--study-forms", default="fp32,bf16x3,bf16",
+                    help="forms of the study (bf16x3-comp: the compensated M-step forced)")
     return ap.parse_args()
 
 
@@ -821,9 +823,12 @@ def run_study(args, local):
         p = synth.workload_problem(name)
         res = {}
         t_start = time.perf_counter()
-        for prec in ("fp32", "bf16x3", "bf16"):
+        for form in args.study_forms.split(","):
+            prec = form.split("-")[0]
+            flags = {"comp": srmra.SRMRA_FLAG_MSTEP_COMP,
+                     "fp16": srmra.SRMRA_FLAG_MSTEP_FP16}.get(form.partition("-")[2], 0)
             s = srmra.Solver(p.L, p.K, p.sigma, p.y, prec=prec, x0=p.x0, rho1=p.rho1_0,
-                             rho2=p.rho2_0)
+                             rho2=p.rho2_0, flags=flags)
             per = []
             sbm = 1.0
             margin = math.inf
@@ -839,7 +844,7 @@ def run_study(args, local):
                             "LL": abs(ll - llo) / abs(llo), "margin": mg})
                 sbm *= decay
             s.close()
-            res[prec] = {"max": {k: max(q[k] for q in per) for k in ("x", "rho1", "rho2", "LL")},
+            res[form] = {"max": {k: max(q[k] for q in per) for k in ("x", "rho1", "rho2", "LL")},
                          "last": per[-1], "min_threshold_margin": margin,
                          "per_iteration": per}
         print(json.dumps({"study": "precision", "workload": name, "iters": args.study_iters,

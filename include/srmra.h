@@ -92,6 +92,9 @@ typedef enum {
  * M-step.  These flags force it on, or off. */
 #define SRMRA_FLAG_MSTEP_COMP 4u
 #define SRMRA_FLAG_MSTEP_FP16 8u
+/* Tensor-core forms: pass 1 uses 128-shift tiles (four TMEM accumulators) instead of
+ * 256-shift tiles (two); a batch's autotuner also chooses between them. */
+#define SRMRA_FLAG_P1_TILE128 16u
 
 typedef struct {
   int32_t L_high;  /* L >= 2 */
@@ -211,8 +214,11 @@ srmra_status srmra_stats_length(const srmra_ctx* ctx, int64_t* len);
 srmra_status srmra_estep_stats(srmra_ctx* ctx, double* stats, int32_t stats_is_device);
 
 /* srmra_mstep_stats -- the M-step (Eqs. x_EM, rho_EM) from a statistics vector (for
- * example the sum over shards): theta_t -> theta_{t+1} in this context, t += 1.  No
- * projection (call srmra_project).  stats: host, or device memory read in the context's
+ * example the sum over shards): theta_t -> theta_{t+1} in this context, t += 1.  Then
+ * Algorithm 2 on the context's own schedule (srmra_set_schedule; none by default): if
+ * its F > 0 and t is a multiple of F, the built-in denoiser x <- D(x, sigma_BM) and
+ * sigma_BM <- decay sigma_BM (Eq. decaying_function), so that every rank of a sharded
+ * solve projects identically.  stats: host, or device memory read in the context's
  * stream order (the caller orders any producer, e.g. a collective on another stream,
  * before this call).  loglik_out (host, may be NULL): the LL entry of the vector;
  * given, the call synchronises and checks the status word (ENUMERIC). */
@@ -272,10 +278,12 @@ typedef struct srmra_batch srmra_batch; /* opaque; owned by the library */
 /* srmra_batch_create -- build a batch over ctxs[0..count-1] (distinct, same precision,
  * same stream).  The contexts stay owned by the caller and must outlive the batch; a
  * context may belong to several batches but batches that share a context must not run
- * concurrently.  With SRMRA_BATCH_AUTOTUNE the work decomposition of the grouped
- * launches (shift groups of pass 1 x {1,2}, observation ranges of pass 2 x {1,2},
- * problem order {as given, most expensive unit first}) is timed on the device and the
- * fastest is kept (the problems' estimates are not changed by the timing runs).
+ * concurrently.  With SRMRA_BATCH_AUTOTUNE the tile shape and work decomposition of the
+ * grouped launches (pass-1 tiles of 256 or 128 shifts x shift groups of pass 1 x {1,2}
+ * x observation ranges of pass 2 x {1,2} x problem order {as given, most expensive unit
+ * first}) are timed on the device and the fastest is kept (the problems' estimates are
+ * not changed by the timing runs; the contexts keep the chosen plan).  Without it the
+ * contexts must share one pass-1 tile width (SRMRA_FLAG_P1_TILE128).
  * Errors: EINVAL, ENOMEM, ECUDA.  Message: srmra_batch_last_error(NULL). */
 srmra_status srmra_batch_create(srmra_ctx** ctxs, int32_t count, uint32_t flags,
                                 srmra_batch** out);
@@ -292,9 +300,10 @@ srmra_status srmra_batch_solve(srmra_batch* b, int32_t iters, int32_t F, double 
 /* (srmra_batch_solve with F < 0 uses every problem's own schedule, see
  * srmra_set_schedule, instead of one F and decay for all.) */
 
-/* srmra_set_schedule -- the Algorithm 2 schedule a batch uses for this problem when it
- * is solved with F < 0: projection every F iterations (F = 0: none), current sigma_BM,
- * and the decay factor applied after each projection (Eq. decaying_function). */
+/* srmra_set_schedule -- the Algorithm 2 schedule of this problem: projection every F
+ * iterations (F = 0: none), current sigma_BM, and the decay factor applied after each
+ * projection (Eq. decaying_function).  Used by srmra_mstep_stats and by a batch solved
+ * with F < 0.  EINVAL if F < 0, sigma_bm < 0, decay <= 0, or F > 0 with L % 8 != 0. */
 srmra_status srmra_set_schedule(srmra_ctx* ctx, int32_t F, double sigma_bm, double decay);
 
 /* srmra_estimate_device_bytes -- device memory srmra_create would allocate for these
@@ -308,6 +317,11 @@ srmra_status srmra_device_bytes(const srmra_ctx* ctx, int64_t* bytes);
  * 0 = as given, 1 = most expensive first) and its timed milliseconds per pass pair. */
 srmra_status srmra_batch_tuning(const srmra_batch* b, int32_t* p1_scale, int32_t* p2_scale,
                                 int32_t* order, double* ms);
+
+/* srmra_batch_tiles -- the tile shape the batch's grouped pass-1 launch uses: its shift
+ * width (256 or 128; chosen by the autotuner with SRMRA_BATCH_AUTOTUNE, else the
+ * contexts' own).  Errors: SRMRA_EINVAL. */
+srmra_status srmra_batch_tiles(const srmra_batch* b, int32_t* p1_shift_tile);
 
 /* srmra_batch_pass_ms -- device time (CUDA events) of the grouped pass-1 and pass-2
  * launches of the batch's most recent iteration.  Synchronises the stream. */

@@ -220,6 +220,7 @@ void setup_ctx(srmra_ctx* c, const srmra_params* p, int num_sms, int caps[3]) {
     caps[2] = c->plan.nparts_c;
   } else if (is_tc_prec(c->prec)) {
     c->plan.p2_comp = tc_comp_mstep(g, c->prec, c->flags);
+    if (c->flags & SRMRA_FLAG_P1_TILE128) c->plan.p1_bn = 128;
     // size the partial buffers for the finest decomposition the batch tuner may pick
     plan_tc(c, 2, 2);
     c->plan.cap_p1_groups = c->plan.p1_groups;
@@ -482,6 +483,14 @@ srmra_status srmra_mstep_stats(srmra_ctx* c, const double* stats, int32_t stats_
                c->status, c->stream);
   CK(c, cudaGetLastError());
   c->t += 1;
+  // Algorithm 2 on the context's own schedule (srmra_set_schedule): the projection after
+  // every F-th M-step, then sigma_BM <- decay sigma_BM (Eq. decaying_function)
+  if (c->sched_F > 0 && c->t % c->sched_F == 0) {
+    PhaseTimer tm(c, SRMRA_PHASE_DENOISE);
+    launch_dct_denoise(c, c->sigma_bm, c->dn_thr);
+    c->sigma_bm *= c->sched_decay;
+    CK(c, cudaGetLastError());
+  }
   if (loglik_out) {
     CK(c, cudaMemcpyAsync(loglik_out, c->ll_hist, sizeof(double), cudaMemcpyDeviceToHost,
                           c->stream));

@@ -39,7 +39,7 @@ struct srmra_batch {
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
   cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};  // around the grouped passes
-  int tuned_s1 = 1, tuned_s2 = 1, tuned_order = 0;
+  int tuned_s1 = 1, tuned_s2 = 1, tuned_order = 0, tuned_bn = 256;
   double tuned_ms = 0.0;
   std::string err;
 };
@@ -124,7 +124,8 @@ cudaError_t launch_pass(srmra_batch* b, int pass) {
   if (is_tc(b->prec)) {
     for (auto* c : b->ctxs) c->launches++;
     if (pass == 1)
-      return tc_launch_group(1, b->prec, b->d_insts, b->d_ustart, n, b->total1, b->d_status,
+      return tc_launch_group(1, b->prec, b->ctxs[0]->plan.p1_bn, b->d_insts, b->d_ustart, n,
+                             b->total1, b->d_status,
                              b->stream, b->num_sms);
     const size_t isz = tc_inst_bytes();
     for (const auto& rg : b->p2) {
@@ -233,41 +234,48 @@ srmra_status time_passes(srmra_batch* b, int reps, double* ms) {
   return SRMRA_OK;
 }
 
-srmra_status apply_decomposition(srmra_batch* b, int s1, int s2, int order) {
+srmra_status apply_decomposition(srmra_batch* b, int s1, int s2, int order, int bn) {
   b->ctxs = b->given;
   if (order == 1)
     std::stable_sort(b->ctxs.begin(), b->ctxs.end(), [](const srmra_ctx* x, const srmra_ctx* y) {
       return unit_cost(x) > unit_cost(y);
     });
-  for (auto* c : b->ctxs) BCK(b, tc_replan(c, s1, s2));
+  for (auto* c : b->ctxs) BCK(b, tc_replan(c, s1, s2, bn));
   return upload_group(b);
 }
 
+// The autotuner: times the grouped passes for every candidate (pass-1 tile width 256 or
+// 128 shifts) x (pass-1 shift groups x1, x2) x (pass-2 observation ranges x1, x2) x
+// (problem order as given, costliest units first) on the current estimates (no state
+// changes) and keeps the fastest.
 srmra_status autotune(srmra_batch* b) {
   for (auto* c : b->ctxs) launch_prep_iter(c);  // operands of the current estimates
   BCK(b, cudaGetLastError());
   double best = 1e300;
-  int bs1 = 1, bs2 = 1, bo = 0;
-  for (int order = 0; order < 2; ++order)
-    for (int s1 : {1, 2})
-      for (int s2 : {1, 2}) {
-        srmra_status st = apply_decomposition(b, s1, s2, order);
-        if (st != SRMRA_OK) return st;
-        double ms = 0.0;
-        st = time_passes(b, 2, &ms);
-        if (st != SRMRA_OK) return st;
-        if (ms < best) {
-          best = ms;
-          bs1 = s1;
-          bs2 = s2;
-          bo = order;
+  int bs1 = 1, bs2 = 1, bo = 0, bbn = 256;
+  for (int bn : {256, 128})
+    for (int order = 0; order < 2; ++order)
+      for (int s1 : {1, 2})
+        for (int s2 : {1, 2}) {
+          srmra_status st = apply_decomposition(b, s1, s2, order, bn);
+          if (st != SRMRA_OK) return st;
+          double ms = 0.0;
+          st = time_passes(b, 2, &ms);
+          if (st != SRMRA_OK) return st;
+          if (ms < best) {
+            best = ms;
+            bs1 = s1;
+            bs2 = s2;
+            bo = order;
+            bbn = bn;
+          }
         }
-      }
   b->tuned_s1 = bs1;
   b->tuned_s2 = bs2;
   b->tuned_order = bo;
+  b->tuned_bn = bbn;
   b->tuned_ms = best;
-  return apply_decomposition(b, bs1, bs2, bo);
+  return apply_decomposition(b, bs1, bs2, bo, bbn);
 }
 
 }  // namespace
@@ -288,6 +296,11 @@ srmra_status srmra_batch_create(srmra_ctx** ctxs, int32_t count, uint32_t flags,
     if (ctxs[k]->stream != ctxs[0]->stream || ctxs[k]->device != ctxs[0]->device)
       return bfail(nullptr, SRMRA_EINVAL, "all contexts of a batch need the same stream");
   }
+  if (is_tc_prec(ctxs[0]->prec) && !(flags & SRMRA_BATCH_AUTOTUNE))
+    for (int k = 1; k < count; ++k)
+      if (ctxs[k]->plan.p1_bn != ctxs[0]->plan.p1_bn)
+        return bfail(nullptr, SRMRA_EINVAL,
+                     "contexts with different pass-1 tile widths need SRMRA_BATCH_AUTOTUNE");
   auto* b = new (std::nothrow) srmra_batch();
   if (!b) return bfail(nullptr, SRMRA_ENOMEM, "host allocation failed");
   b->ctxs.assign(ctxs, ctxs + count);
@@ -296,6 +309,7 @@ srmra_status srmra_batch_create(srmra_ctx** ctxs, int32_t count, uint32_t flags,
   b->stream = ctxs[0]->stream;
   b->num_sms = ctxs[0]->num_sms;
   b->flags = flags;
+  b->tuned_bn = ctxs[0]->plan.p1_bn;
   cudaError_t e = is_tc(b->prec)                ? tc_set_attributes(b->prec)
                   : b->prec == SRMRA_FFT32 ? fft_set_attributes()
                                            : simt_set_attributes();
@@ -387,6 +401,12 @@ srmra_status srmra_batch_tuning(const srmra_batch* b, int32_t* p1_scale, int32_t
   if (p2_scale) *p2_scale = b->tuned_s2;
   if (order) *order = b->tuned_order;
   if (ms) *ms = b->tuned_ms;
+  return SRMRA_OK;
+}
+
+srmra_status srmra_batch_tiles(const srmra_batch* b, int32_t* p1_shift_tile) {
+  if (!b) return bfail(nullptr, SRMRA_EINVAL, "batch is NULL");
+  if (p1_shift_tile) *p1_shift_tile = b->tuned_bn;
   return SRMRA_OK;
 }
 

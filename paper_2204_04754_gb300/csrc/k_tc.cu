@@ -118,18 +118,25 @@ __device__ __forceinline__ void raise_timeout(volatile int* abort, int* status) 
 }
 
 // ------------------------------------------------------------------------------ pass 1
-template <int NPROD>
+// BN is the shift width of a tile: 256 (two TMEM accumulators of 256 columns) or 128
+// (four of 128, so that the MMAs can run further ahead of the epilogue; the template
+// tile of a k-block, hi and lo, then shares one ring slot).  Every instance of a
+// launch has the same BN (its p1 arguments are counted in BN-wide tiles).
+template <int NPROD, int BN>
 __global__ void __launch_bounds__(TC_THREADS, 1)
     k_p1_tc(const TcInst* __restrict__ insts, const int64_t* __restrict__ ustart, int n_inst,
             int* status) {
-  constexpr int SPK = (NPROD == 3) ? 3 : 2;  // ring slots per k-block
+  static_assert(BN == 256 || BN == 128, "pass-1 tiles are 128 or 256 shifts wide");
+  constexpr int SPK = (NPROD == 3 && BN == 256) ? 3 : 2;  // ring slots per k-block
+  constexpr int NB = 512 / BN;                             // TMEM accumulators
+  constexpr uint32_t A_BYTES = BN * 128;                   // one template part, one k-block
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = align1024(smem_raw);
   uint64_t* full = (uint64_t*)(smem + P1_SLOTS * SLOT);
   uint64_t* empty = full + P1_SLOTS;
   uint64_t* tfull = empty + P1_SLOTS;
-  uint64_t* tempty = tfull + 2;
-  uint64_t* drain = tempty + 2;
+  uint64_t* tempty = tfull + NB;
+  uint64_t* drain = tempty + NB;
   uint64_t* never = drain + 1;  // nothing arrives on it (test hook)
   uint32_t* tptr = (uint32_t*)(never + 1);
   volatile int* abort = (volatile int*)(tptr + 1);
@@ -142,7 +149,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
       mbar_init(&full[k], 1);
       mbar_init(&empty[k], 1);
     }
-    for (int b = 0; b < 2; ++b) {
+    for (int b = 0; b < NB; ++b) {
       mbar_init(&tfull[b], 1);
       mbar_init(&tempty[b], 128);
     }
@@ -186,9 +193,14 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                 mbar_expect_tx(&full[st], NPROD == 3 ? 32768 : 16384);
                 tma_load_2d(dst, &I->tmY, &full[st], kb * 64, iblk * 128);
                 if (NPROD == 3) tma_load_2d(dst + 16384, &I->tmYl, &full[st], kb * 64, iblk * 128);
-              } else {
+              } else if (BN == 256) {
                 mbar_expect_tx(&full[st], 32768);
                 tma_load_2d(dst, sl == 1 ? &I->tmA256 : &I->tmAl256, &full[st], kb * 64, tile * 256);
+              } else {  // 128-row template parts, hi then lo, in one slot
+                mbar_expect_tx(&full[st], NPROD == 3 ? 2 * A_BYTES : A_BYTES);
+                tma_load_2d(dst, &I->tmA128, &full[st], kb * 64, tile * 128);
+                if (NPROD == 3)
+                  tma_load_2d(dst + A_BYTES, &I->tmAl128, &full[st], kb * 64, tile * 128);
               }
               ++it;
             }
@@ -206,7 +218,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     }
   } else if (warp == 1) {
     if (lane == 0) {
-      constexpr uint32_t idesc = idesc_bf16_f32(128, 256);
+      constexpr uint32_t idesc = idesc_bf16_f32(128, BN);
       uint32_t it = 0, tcount = 0;
       bool ok = true;
       for (int64_t u = blockIdx.x; ok && u < total; u += gridDim.x) {
@@ -217,14 +229,14 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         const int grp = (int)(lu % a.groups);
         const int tb = grp * a.tpg, te = min(a.n_stiles, tb + a.tpg);
         for (int tile = tb; ok && tile < te; ++tile) {
-          const int b = tcount & 1;
-          const uint32_t tph = (tcount >> 1) & 1;
+          const int b = tcount % NB;
+          const uint32_t tph = (tcount / NB) & 1;
           if (!mbar_wait(&tempty[b], tph ^ 1, abort, wlim)) {
             ok = false;
             break;
           }
           tc_fence_after();
-          const uint32_t d = tbase + (uint32_t)(b * 256);
+          const uint32_t d = tbase + (uint32_t)(b * BN);
           for (int kb = 0; ok && kb < a.nk; ++kb) {
             int st[SPK];
             for (int sl = 0; sl < SPK; ++sl) {
@@ -241,7 +253,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                        (kb > 0 || k4 > 0) ? 1u : 0u);
               if (NPROD == 3) {
                 const uint64_t dYl = desc_sw128(smem + st[0] * SLOT + 16384);
-                const uint64_t dAl = desc_sw128(smem + st[SPK - 1] * SLOT);
+                const uint64_t dAl = desc_sw128(BN == 256 ? smem + st[SPK - 1] * SLOT
+                                                          : smem + st[1] * SLOT + A_BYTES);
                 mma_bf16(d, desc_advance(dY, k4), desc_advance(dAl, k4), idesc, 1u);
                 mma_bf16(d, desc_advance(dYl, k4), desc_advance(dA, k4), idesc, 1u);
               }
@@ -282,10 +295,10 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
       const float* __restrict__ colm = a.colm;
       float rm = -INFINITY, rs = 0.f;
       // (colb, colm) of the next 32-column chunk, loaded one chunk ahead of its use
-      float nb_ = colb[tb * 256 + lane], nm_ = colm[tb * 256 + lane];
+      float nb_ = colb[tb * BN + lane], nm_ = colm[tb * BN + lane];
       for (int tile = tb; tile < te; ++tile) {
-        const int b = tcount & 1;
-        const uint32_t tph = (tcount >> 1) & 1;
+        const int b = tcount % NB;
+        const uint32_t tph = (tcount / NB) & 1;
         // test hook: the first CTA's epilogue first waits on a barrier that nothing
         // completes, so that the wait runs out after the limit and the launch reports a
         // timeout through the ordinary abort path
@@ -294,18 +307,19 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                                          mbar_wait(&tfull[b], tph, abort, wlim));
         if (!ok) break;
         tc_fence_after();
+        constexpr int NCH = BN / 32;  // 32-column chunks of a tile
 #pragma unroll 1
-        for (int c = 0; c < 8; ++c) {
+        for (int c = 0; c < NCH; ++c) {
           __syncwarp();  // the warp is done with the previous chunk's terms
           wcol[lane] = make_float2(nb_, nm_);
           __syncwarp();
-          const int nx = (c < 7) ? tile * 256 + (c + 1) * 32 : (tile + 1) * 256;
-          if (c < 7 || tile + 1 < te) {
+          const int nx = (c < NCH - 1) ? tile * BN + (c + 1) * 32 : (tile + 1) * BN;
+          if (c < NCH - 1 || tile + 1 < te) {
             nb_ = colb[nx + lane];
             nm_ = colm[nx + lane];
           }
           float v[32];
-          tmem_ld32(lane_addr + (uint32_t)(b * 256 + c * 32), v);
+          tmem_ld32(lane_addr + (uint32_t)(b * BN + c * 32), v);
           tmem_ld_wait();
           float mx = -INFINITY;
 #pragma unroll
@@ -1929,9 +1943,9 @@ cudaError_t set_p2c_attrs() {
   return e;
 }
 
-template <int NPROD>
+template <int NPROD, int BN>
 cudaError_t set_p1_attrs() {
-  return set_smem(k_p1_tc<NPROD>, P1_SMEM);
+  return set_smem(k_p1_tc<NPROD, BN>, P1_SMEM);
 }
 template <int NPROD>
 cudaError_t set_p2_attrs() {
@@ -1994,7 +2008,7 @@ void plan_tc(srmra_ctx* c, int s1, int s2) {
   const Geom& g = c->g;
   Plan& p = c->plan;
   const int sms = c->num_sms;
-  const int n_st1 = g.Spad / 256;
+  const int n_st1 = g.Spad / p.p1_bn;
   const int iblk1 = (int)(g.Npad / 128);
   // pass 1 is a persistent kernel that deals its (observation block, shift group) units
   // round-robin to one CTA per SM: pick the shift-group size that minimises the rounds
@@ -2062,7 +2076,8 @@ void plan_tc(srmra_ctx* c, int s1, int s2) {
   p.ll_blocks = (int)ceil_div(g.Npad, 256);
 }
 
-cudaError_t tc_replan(srmra_ctx* c, int s1, int s2) {
+cudaError_t tc_replan(srmra_ctx* c, int s1, int s2, int p1_bn) {
+  c->plan.p1_bn = p1_bn;
   plan_tc(c, s1, s2);
   return tc_upload_inst(c);
 }
@@ -2070,12 +2085,14 @@ cudaError_t tc_replan(srmra_ctx* c, int s1, int s2) {
 cudaError_t tc_set_attributes(int prec) {
   cudaError_t e;
   if (prec == SRMRA_BF16X3) {
-    e = set_smem(k_p1_tc<3>, P1_SMEM);
+    e = set_smem(k_p1_tc<3, 256>, P1_SMEM);
+    if (e == cudaSuccess) e = set_smem(k_p1_tc<3, 128>, P1_SMEM);
     if (e == cudaSuccess) e = set_smem(k_p2_tc<3, false>, P2_SMEM);
     if (e == cudaSuccess) e = set_p2comp_attrs();
     if (e == cudaSuccess) e = set_p2c_attrs<3>();
   } else {
-    e = set_smem(k_p1_tc<1>, P1_SMEM);
+    e = set_smem(k_p1_tc<1, 256>, P1_SMEM);
+    if (e == cudaSuccess) e = set_smem(k_p1_tc<1, 128>, P1_SMEM);
     if (e == cudaSuccess) e = set_smem(k_p2_tc<1, false>, P2_SMEM);
     if (e == cudaSuccess) e = set_p2c_attrs<1>();
   }
@@ -2135,7 +2152,7 @@ void fill_inst(const srmra_ctx* c, TcInst* I) {
   I->tmYTl = c->plan.p2_comp ? c->tmYTl : c->tmYT;
   TcP1Args& a = I->p1;
   a.nk = (int)ceil_div(g.l2, 64);
-  a.n_stiles = g.Spad / 256;
+  a.n_stiles = g.Spad / p.p1_bn;
   a.groups = p.p1_groups;
   a.tpg = p.p1_tiles_per_group;
   a.n_units = (g.Npad / 128) * p.p1_groups;
@@ -2255,15 +2272,19 @@ cudaError_t launch_cluster_p2(int G, const TcInst* d_insts, const int64_t* d_ust
 }
 
 template <int NPROD>
-cudaError_t launch_group(int pass, const TcInst* d_insts, const int64_t* d_ustart, int n,
+cudaError_t launch_group(int pass, int bn, const TcInst* d_insts, const int64_t* d_ustart, int n,
                          int64_t total, int* status, cudaStream_t stream, int num_sms) {
   cudaError_t e = cudaSuccess;
   const unsigned grid = (unsigned)(total < num_sms ? total : num_sms);
   if (grid == 0) return cudaSuccess;
-  if (pass == 1) {
-    e = once_per_device(ATTR_TC_P1 + NPROD, set_p1_attrs<NPROD>);
+  if (pass == 1 && bn == 128) {
+    e = once_per_device(ATTR_TC_P1N + NPROD, set_p1_attrs<NPROD, 128>);
     if (e != cudaSuccess) return e;
-    k_p1_tc<NPROD><<<grid, TC_THREADS, P1_SMEM, stream>>>(d_insts, d_ustart, n, status);
+    k_p1_tc<NPROD, 128><<<grid, TC_THREADS, P1_SMEM, stream>>>(d_insts, d_ustart, n, status);
+  } else if (pass == 1) {
+    e = once_per_device(ATTR_TC_P1 + NPROD, set_p1_attrs<NPROD, 256>);
+    if (e != cudaSuccess) return e;
+    k_p1_tc<NPROD, 256><<<grid, TC_THREADS, P1_SMEM, stream>>>(d_insts, d_ustart, n, status);
   } else {
     e = once_per_device(ATTR_TC_P2 + NPROD, set_p2_attrs<NPROD>);
     if (e != cudaSuccess) return e;
@@ -2336,19 +2357,20 @@ cudaError_t tc_launch_group_p2(int G, int prec, const void* d_insts, const int64
     return cudaGetLastError();
   }
   if (G <= 1)
-    return tc_launch_group(2, prec, d_insts, d_ustart, n, total, status, stream, num_sms);
+    return tc_launch_group(2, prec, 256, d_insts, d_ustart, n, total, status, stream, num_sms);
   if (prec == SRMRA_BF16X3)
     return launch_cluster_p2<3>(G, insts, d_ustart, n, total, status, stream, num_sms);
   return launch_cluster_p2<1>(G, insts, d_ustart, n, total, status, stream, num_sms);
 }
 
-cudaError_t tc_launch_group(int pass, int prec, const void* d_insts, const int64_t* d_ustart,
-                            int n, int64_t total, int* status, cudaStream_t stream,
-                            int num_sms) {
+cudaError_t tc_launch_group(int pass, int prec, int p1_bn, const void* d_insts,
+                            const int64_t* d_ustart, int n, int64_t total, int* status,
+                            cudaStream_t stream, int num_sms) {
   const TcInst* insts = (const TcInst*)d_insts;
+  if (pass == 1 && p1_bn != 256 && p1_bn != 128) return cudaErrorInvalidValue;
   if (prec == SRMRA_BF16X3)
-    return launch_group<3>(pass, insts, d_ustart, n, total, status, stream, num_sms);
-  return launch_group<1>(pass, insts, d_ustart, n, total, status, stream, num_sms);
+    return launch_group<3>(pass, p1_bn, insts, d_ustart, n, total, status, stream, num_sms);
+  return launch_group<1>(pass, p1_bn, insts, d_ustart, n, total, status, stream, num_sms);
 }
 
 // The context's own descriptor (a group of one) in device memory, uploaded once.
@@ -2370,8 +2392,8 @@ cudaError_t tc_upload_inst(srmra_ctx* c) {
 
 cudaError_t launch_pass1_tc(srmra_ctx* c) {
   c->launches++;
-  return tc_launch_group(1, c->prec, c->d_inst, c->d_ustart, 1, c->h_ustart[1], c->status,
-                         c->stream, c->num_sms);
+  return tc_launch_group(1, c->prec, c->plan.p1_bn, c->d_inst, c->d_ustart, 1, c->h_ustart[1],
+                         c->status, c->stream, c->num_sms);
 }
 
 cudaError_t launch_pass2_tc(srmra_ctx* c) {

@@ -44,6 +44,7 @@ enum : int {
   ATTR_TC_P2 = 5,     // + NPROD
   ATTR_TC_P2C = 9,    // + NPROD
   ATTR_TC_P2COMP = 13,
+  ATTR_TC_P1N = 14,   // + NPROD: the 128-shift pass-1 tiles
 };
 cudaError_t once_per_device(int key, cudaError_t (*set)());
 
@@ -79,6 +80,7 @@ struct DevSched {
 };
 
 struct Plan {
+  int p1_bn = 256;          // tensor-core pass 1: shifts per tile (256 or 128)
   int p1_groups = 1;        // shift groups per observation tile in pass 1
   int p1_tiles_per_group = 1;
   int p2_gc = 1;            // cluster size (pixel chunks sharing one weight tile)
@@ -208,7 +210,7 @@ int fin_t_splits(const Geom& g, int num_sms);
 bool tc_comp_mstep(const Geom& g, int prec, unsigned flags);
 int tc_p2_key(const srmra_ctx* c);  // pass-2 launch group (cluster size; 0 = compensated)
 void plan_tc(srmra_ctx* c, int s1 = 1, int s2 = 1);
-cudaError_t tc_replan(srmra_ctx* c, int s1, int s2);
+cudaError_t tc_replan(srmra_ctx* c, int s1, int s2, int p1_bn);
 cudaError_t tc_set_attributes(int prec);
 cudaError_t prep_obs_tc(srmra_ctx* c);
 void launch_templates_tc(srmra_ctx* c);
@@ -218,9 +220,9 @@ cudaError_t tc_upload_inst(srmra_ctx* c);
 size_t tc_inst_bytes();
 void tc_fill_inst(const srmra_ctx* c, void* host_dst);
 int64_t tc_units(const srmra_ctx* c, int pass);
-cudaError_t tc_launch_group(int pass, int prec, const void* d_insts, const int64_t* d_ustart,
-                            int n, int64_t total, int* status, cudaStream_t stream,
-                            int num_sms);
+cudaError_t tc_launch_group(int pass, int prec, int p1_bn, const void* d_insts,
+                            const int64_t* d_ustart, int n, int64_t total, int* status,
+                            cudaStream_t stream, int num_sms);
 // pass 2 for instances with cluster size G (G = 1: the per-chunk kernel, G = 0: the
 // per-chunk kernel with the compensated M-step)
 cudaError_t tc_launch_group_p2(int G, int prec, const void* d_insts, const int64_t* d_ustart,

@@ -8,8 +8,9 @@ the observations, all with the same L, K, sigma and starting estimate.  One iter
    shard's observations; include/srmra.h gives the layout);
 2. one all-reduce (sum) of that vector over the ranks;
 3. ``mstep_stats`` on the sum on every rank, so that all ranks hold the same estimate;
-4. every F-th iteration the projection x <- D(x, sigma_BM) (Algorithm 2), identical on
-   every rank.
+   on every F-th call it also applies the projection x <- D(x, sigma_BM) and the decay of
+   sigma_BM (Algorithm 2) from the schedule the library keeps for the context
+   (``set_schedule``), identically on every rank.
 
 The result is the EM iteration over the union of the shards, up to the order of the
 float sums.  With ``device=True`` the vector stays in device memory (an NCCL all-reduce);
@@ -41,16 +42,12 @@ def sharded_solve(solver, iters: int, F: int, sigma_bm1: float = 1.0,
                   decay: float = 2.0 ** -0.1, group=None, device: bool = False) -> list:
     """Algorithm 2 over the sharded observations: `iters` EM iterations, the projection
     after every F-th (F = 0: none) with sigma_BM starting at sigma_bm1 and multiplied by
-    `decay` after each projection.  Returns the per-iteration LL(theta_t)."""
+    `decay` after each projection (the schedule is handed to the library, whose M-step
+    applies it).  Returns the per-iteration LL(theta_t)."""
     buffer = None
     if device:
         import torch
         buffer = torch.empty(solver.stats_length(), dtype=torch.float64, device="cuda")
-    lls = []
-    sbm = float(sigma_bm1)
-    for t in range(iters):
-        lls.append(sharded_iteration(solver, group=group, device=device, buffer=buffer))
-        if F > 0 and (t + 1) % F == 0:
-            solver.project(sbm)
-            sbm *= decay
-    return lls
+    solver.set_schedule(F, sigma_bm1, decay)
+    return [sharded_iteration(solver, group=group, device=device, buffer=buffer)
+            for _ in range(iters)]

@@ -29,6 +29,7 @@ SRMRA_FLAG_CHECK_NUMERIC = 1
 SRMRA_FLAG_NO_CLUSTER = 2
 SRMRA_FLAG_MSTEP_COMP = 4
 SRMRA_FLAG_MSTEP_FP16 = 8
+SRMRA_FLAG_P1_TILE128 = 16
 
 
 class srmra_params(Structure):
@@ -81,6 +82,7 @@ def lib() -> ctypes.CDLL:
         "srmra_batch_solve": (c_int32, [c_void_p, c_int32, c_int32, c_double, c_double,
                                         c_void_p]),
         "srmra_batch_tuning": (c_int32, [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]),
+        "srmra_batch_tiles": (c_int32, [c_void_p, c_void_p]),
         "srmra_batch_destroy": (None, [c_void_p]),
         "srmra_batch_pass_ms": (c_int32, [c_void_p, c_void_p, c_void_p]),
         "srmra_batch_last_error": (c_char_p, [c_void_p]),
@@ -265,7 +267,10 @@ def srmra_batch_tuning(batch: int):
     a, b, c = c_int32(), c_int32(), c_int32()
     ms = c_double()
     _bcheck(lib().srmra_batch_tuning(batch, byref(a), byref(b), byref(c), byref(ms)), batch)
-    return dict(p1_scale=a.value, p2_scale=b.value, order=c.value, ms=ms.value)
+    bn = c_int32()
+    _bcheck(lib().srmra_batch_tiles(batch, byref(bn)), batch)
+    return dict(p1_scale=a.value, p2_scale=b.value, order=c.value, ms=ms.value,
+                p1_shift_tile=bn.value)
 
 
 def srmra_batch_destroy(batch: int) -> None:
@@ -324,6 +329,11 @@ class Solver:
             fn = DENOISER_FN(denoiser)
             self._fn = fn
         srmra_project(self.ctx, sigma_bm, fn, None)
+
+    def set_schedule(self, F: int, sigma_bm: float, decay: float = 2.0 ** -0.1):
+        """Algorithm 2 schedule applied by mstep_stats (and by batches solved with F < 0)."""
+        _check(lib().srmra_set_schedule(self.ctx, int(F), float(sigma_bm), float(decay)),
+               self.ctx)
 
     def set_denoiser(self, mode: str = "hard", threshold: float = 2.7, spin: bool = False):
         """Built-in denoiser: 'hard' or 'soft' threshold, optional cycle spinning."""

@@ -77,6 +77,8 @@ def test_autotuned_batch_matches_within_tolerance(S):
     b = S.Batch(ss, autotune=True)
     tun = b.tuning()
     assert tun["p1_scale"] in (1, 2) and tun["p2_scale"] in (1, 2) and tun["ms"] > 0
+    assert tun["p1_shift_tile"] in (128, 256)
+    print("autotuner", tun)
     b.solve(2, 1)
     for p, s in zip(probs, ss):
         a = solver(S, p, "bf16x3")

@@ -206,6 +206,31 @@ def test_full_size_projected_workload_one_iteration(S):
     check_one_step(S, p, steps=1, oracle="fft")
 
 
+def test_projected_workload_full_run_30_iterations(S):
+    """The projected-EM workload (L = 64, K = 2, N = 1e4, sigma = 0.3) at full size over
+    its 30 iterations of Algorithm 2 (F = 1, sigma_BM_1 = 1, Eq. decaying_function) from
+    the workload's initial guess: the GPU run against the FP64 oracle's own run (its
+    polyphase-FFT formulation, pinned to the dense one), which reports the smallest
+    distance of any DCT coefficient to the threshold (a coefficient closer than the
+    two runs' difference could be kept by one and zeroed by the other)."""
+    p = synth.workload_problem("proj_em_L64_K2_N1e4")
+    s = make_solver(S, p)
+    ll = s.solve(30, 1)
+    x, r1, r2, sbm, t = s.state()
+    s.close()
+    step = lambda x_, a, b: FO.em_iter_fft(p.y, x_, a, b, p.sigma, p.K,
+                                           workers=os.cpu_count() or 1)
+    xo, r1o, r2o, h = O.projected_em(p.y, p.x0, p.rho1_0, p.rho2_0, p.sigma, p.K, iters=30,
+                                     F=1, em_step=step)
+    errs = (rel(x, xo), rel(r1, r1o), rel(r2, r2o),
+            float(np.max(np.abs(np.asarray(ll) - h["LL"]) / np.abs(h["LL"]))))
+    print("30-iteration run: margin", h["margin"], "errors x, rho1, rho2, LL", errs)
+    assert t == 30 and abs(sbm - 2.0 ** -3) < 1e-15
+    assert h["margin"] > 1e-4
+    assert errs[0] < TOL["fp32"] and errs[1] < TOL["fp32"] and errs[2] < TOL["fp32"]
+    assert errs[3] < 1e-6
+
+
 def test_checkpoint_resume_is_bitwise(S):
     p = synth.make_problem(32, 2, 600, 0.3, seed=77, n_blobs=10)
     a = make_solver(S, p)

@@ -88,7 +88,9 @@ def test_em_step_parity_bf16x3(S, L, K, N, sigma):
     w = one_step(S, p, "bf16x3")
     tol = TOL["bf16x3"]
     assert w["x"] < tol and w["rho"] < tol and w["ll"] < tol and w["lse"] < tol
-    assert w["ll_rel"] < tol and w["lse_rel"] < tol
+    assert w["ll_rel"] < tol
+    if L // K > 1:  # with one pixel per observation lse_i can be near 0
+        assert w["lse_rel"] < tol
 
 
 # (shape, M-step flag, pass-2 form): the cluster forms with single fp16 M-step operands
@@ -106,6 +108,31 @@ def test_em_step_parity_bf16x3_forms(S, shape, flags, form):
     w = one_step(S, p, "bf16x3", flags=flags, form=form)
     tol = TOL["bf16x3"]
     assert w["x"] < tol and w["rho"] < tol and w["ll"] < tol and w["lse"] < tol
+
+
+@pytest.mark.parametrize("L,K,N,sigma", [(16, 2, 500, 0.1), (12, 3, 333, 0.4), (64, 2, 700, 0.3),
+                                         (96, 3, 1500, 0.2), (32, 4, 900, 1.0)])
+@pytest.mark.parametrize("prec", ["bf16x3", "bf16"])
+def test_pass1_tiles_of_128_shifts(S, L, K, N, sigma, prec):
+    """Pass 1 with 128-shift tiles (four TMEM accumulators; SRMRA_FLAG_P1_TILE128), the
+    tile shape the batch autotuner can choose: the same iteration as the 256-shift tiles
+    (identical 32-column order of the online log-sum-exp wherever the shift groups
+    coincide; float32 rounding otherwise), and the oracle's within the form's bound."""
+    p = synth.make_problem(L, K, N, sigma, seed=synth.seed_for(3, 300 + L))
+    out = []
+    for flags in (0, 16):
+        s = S.Solver(p.L, p.K, p.sigma, p.y, prec=prec, x0=p.x0, rho1=p.rho1_0,
+                     rho2=p.rho2_0, flags=flags)
+        s.em_iter(1)
+        out.append((s.state(), s.estep()[0]))
+        s.close()
+    (x0, r10, r20, _, _), lse0 = out[0]
+    (x1, r11, r21, _, _), lse1 = out[1]
+    assert np.max(np.abs(lse1 - lse0) / (1.0 + np.abs(lse0))) < 1e-6
+    assert rel(x1, x0) < 1e-5 and rel(r11, r10) < 1e-5 and rel(r21, r20) < 1e-5
+    if prec == "bf16x3":
+        w = one_step(S, p, prec, steps=1, flags=16)
+        assert w["x"] < TOL["bf16x3"] and w["rho"] < TOL["bf16x3"] and w["lse"] < TOL["bf16x3"]
 
 
 def test_compensated_mstep_is_closer_to_the_oracle(S):

@@ -24,6 +24,11 @@ class OracleShard:
     def __init__(self, Y, x0, r1, r2):
         self.Y = np.asarray(Y, np.float64).reshape(Y.shape[0], -1)
         self.x, self.r1, self.r2 = np.asarray(x0, np.float64), np.array(r1), np.array(r2)
+        self.t, self.F, self.sbm, self.decay = 0, 0, 1.0, 1.0
+
+    def set_schedule(self, F, sigma_bm, decay=2.0 ** -0.1):
+        """As the library: mstep_stats projects on this Algorithm 2 schedule."""
+        self.F, self.sbm, self.decay = F, sigma_bm, decay
 
     def stats_length(self):
         return L * L * (L // K) ** 2 + L * L + 1
@@ -37,6 +42,10 @@ class OracleShard:
         Z = np.asarray(v[:S * l2]).reshape(S, l2)
         c = np.asarray(v[S * l2:S * l2 + S])
         self.x, self.r1, self.r2, _, _ = O.mstep_from_sums(Z, c, self.x, K)
+        self.t += 1
+        if self.F > 0 and self.t % self.F == 0:
+            self.x = O.dct_denoise(self.x, self.sbm)[0]
+            self.sbm *= self.decay
         return float(v[-1])
 
     def project(self, sbm):
