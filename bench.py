@@ -918,7 +918,7 @@ def main():
     if rank == 0 and prec == "fp32" and not args.no_mixed:
         # the tensor-core forms of the same workload, and the errors of every form
         # against the FP64 oracle after one iteration from a common state
-        forms = ("bf16x3", "bf16") if p.l * p.l >= 64 else ("bf16x3",)
+        forms = ("bf16x3", "bf16") + (("fft32",) if p.l in (8, 16, 32) else ())
         runs = [head] + [FormRun(p, w, args.workload, f, args.steps, args.warmup, srmra,
                                  torch, stream, flush) for f in forms]
         err, how = errors_vs_oracle(p, runs, threads)
@@ -935,12 +935,14 @@ def main():
         if "bf16x3" in out["forms"]:
             out["roofline"]["bf16x3"] = out["forms"]["bf16x3"]["roofline"]
             out["bf16x3_speedup_vs_fp32"] = out["forms"]["bf16x3"]["speedup_vs_fp32"]
+            out["bf16x3_rel_err_max_vs_oracle"] = out["forms"]["bf16x3"]["rel_err_max"]
     head.close()
     if rank == 0 and prec == "fp32" and not args.no_mixed and not args.no_extra:
         if args.workload in COMPANION:
             _, _, runs2, blk = workload_block(COMPANION[args.workload], args.steps,
                                               args.warmup, srmra, torch, stream, flush,
-                                              threads, local=local)
+                                              threads, local=local,
+                                              forms=("fp32", "bf16x3", "bf16", "fft32"))
             for r in runs2:
                 r.close()
             out[COMPANION[args.workload]] = blk

@@ -11,6 +11,8 @@
 // with nu'_r = ||x'_r||^2 (exact algebra; it shrinks the operands of the contraction).
 #include <math.h>
 
+#include <algorithm>
+
 #include <mutex>
 #include <set>
 #include <utility>
@@ -546,6 +548,26 @@ int stats_t_splits(const srmra_ctx* c) {
   return c->prec == SRMRA_FFT32 ? 1 : fin_t_splits(c->g, c->num_sms);
 }
 
+// Zp[0][s][:] = sum_k Zp[k][s][:] over the nparts partial slices of pass 2 (s < S):
+// float4 rows, the slices added in order in float64, one coalesced pass, so that the
+// gather of k_fin_b reads a single slice.
+__global__ void __launch_bounds__(256) k_sum_parts(float* __restrict__ Zp, int nparts,
+                                                    int64_t slice, int64_t n4) {
+  for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < n4;
+       q += (int64_t)gridDim.x * blockDim.x) {
+    const float4 v0 = reinterpret_cast<const float4*>(Zp)[q];
+    double a0 = v0.x, a1 = v0.y, a2 = v0.z, a3 = v0.w;
+    for (int k = 1; k < nparts; ++k) {
+      const float4 v = reinterpret_cast<const float4*>(Zp + k * slice)[q];
+      a0 += v.x;
+      a1 += v.y;
+      a2 += v.z;
+      a3 += v.w;
+    }
+    reinterpret_cast<float4*>(Zp)[q] = make_float4((float)a0, (float)a1, (float)a2, (float)a3);
+  }
+}
+
 // The E-step sums of the iteration: c_s, zb_s (float64, cfin) and the partials of b'
 // (bpart, stats_t_splits of them).
 void launch_stats(srmra_ctx* c) {
@@ -557,10 +579,18 @@ void launch_stats(srmra_ctx* c) {
   if (c->prec == SRMRA_FFT32) {
     launch_fin_b_fft(c);  // b' from the frequency-domain sums: one partial
   } else {
+    int nparts = c->plan.nparts_z;
+    if (nparts > 1) {
+      const int64_t n4 = (int64_t)g.S * g.ldy / 4;  // ldy is a multiple of 16
+      const unsigned blocks = (unsigned)std::min<int64_t>(ceil_div(n4, 256), 8 * c->num_sms);
+      k_sum_parts<<<blocks, 256, 0, c->stream>>>(c->Zp, nparts, (int64_t)g.Spad * g.ldy, n4);
+      c->launches++;
+      nparts = 1;
+    }
     const int n_ts = fin_t_splits(g, c->num_sms);
     const int t_per = (int)ceil_div(g.l2, n_ts);
     k_fin_b<<<dim3((unsigned)(g.K * g.K), (unsigned)n_ts), 256, 0, c->stream>>>(
-        c->Zp, c->plan.nparts_z, g.Spad, g.ldy, g.L, g.K, g.l, t_per, c->bpart);
+        c->Zp, nparts, g.Spad, g.ldy, g.L, g.K, g.l, t_per, c->bpart);
     c->launches++;
   }
 }

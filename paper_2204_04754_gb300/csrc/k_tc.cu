@@ -42,6 +42,7 @@ constexpr int SLOT = 32768;
 constexpr int P1_SLOTS = 6;
 constexpr int P2_SLOTS_PLAIN = 5;  // per-chunk pass 2: operand ring slots
 constexpr int P2_SLOTS_COMP = 3;   // the same with the compensated M-step
+constexpr int P2_MAX_ACC = 512;    // MMAs added into one Z' accumulator (see plan_tc)
 constexpr int TC_THREADS = 192;
 constexpr float W_SCALE = 4096.f;        // 2^12, weights scaled before fp16 rounding
 constexpr float W_UNSCALE = 1.f / 4096.f;
@@ -632,7 +633,11 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
       const int s = stile * 128 + row;
       const float cb = a.colb[s], cm = a.colm[s];
       const float a2 = a.a2, c2 = a.c2;
+      // per-block float32 sums of the rounded weights, added to float64 totals once a
+      // block (a float32 total over thousands of observations would drop the small
+      // weights of a shift against its large running sum)
       float cacc = 0.f, zacc = 0.f;
+      double cacc_d = 0.0, zacc_d = 0.0;
       for (int j = 0; j < nb; ++j) {
         const int64_t ib = (int64_t)(jb0 + j) * 128;
         const int b = sc & 1, pb = pz & 1;
@@ -702,6 +707,9 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         mbar_arrive(&sempty[b]);
         fence_proxy_async_smem();
         mbar_arrive(&pfull[pb]);
+        cacc_d += (double)cacc;
+        zacc_d += (double)zacc;
+        cacc = zacc = 0.f;
         ++sc;
         ++pz;
       }
@@ -728,8 +736,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
       tc_fence_before();
       mbar_arrive(zempty);
       if (chunk == 0) {
-        a.cp[(int64_t)split * a.Spad + s] = cacc * W_UNSCALE;
-        a.zbp[(int64_t)split * a.Spad + s] = zacc * W_UNSCALE;
+        a.cp[(int64_t)split * a.Spad + s] = (float)(cacc_d * W_UNSCALE);
+        a.zbp[(int64_t)split * a.Spad + s] = (float)(zacc_d * W_UNSCALE);
       }
       ++uc;
     }
@@ -1080,7 +1088,11 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
       const int s = stile * 128 + row;
       const float cb = a.colb[s], cm = a.colm[s];
       const float a2 = a.a2, c2 = a.c2;
+      // per-block float32 sums of the rounded weights, added to float64 totals once a
+      // block (a float32 total over thousands of observations would drop the small
+      // weights of a shift against its large running sum)
       float cacc = 0.f, zacc = 0.f;
+      double cacc_d = 0.0, zacc_d = 0.0;
       for (int r0 = 0; ok && r0 < nb; r0 += G) {
         const int nq = min(G, nb - r0);
         if ((int)rank >= nq) continue;
@@ -1167,6 +1179,9 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         }
         ok = __all_sync(0xffffffffu, sent_ok);
         if (!ok) break;
+        cacc_d += (double)cacc;
+        zacc_d += (double)zacc;
+        cacc = zacc = 0.f;
         ++sc;
         ++mr;
       }
@@ -1197,8 +1212,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
       }
       if (cgrp == 0) {
         const int64_t part = (int64_t)split * G + rank;
-        a.cp[part * a.Spad + s] = cacc * W_UNSCALE;
-        a.zbp[part * a.Spad + s] = zacc * W_UNSCALE;
+        a.cp[part * a.Spad + s] = (float)(cacc_d * W_UNSCALE);
+        a.zbp[part * a.Spad + s] = (float)(zacc_d * W_UNSCALE);
       }
     }
     if (!ok) raise_timeout(abort, status);
@@ -1568,7 +1583,11 @@ __global__ void __launch_bounds__(P2I_THREADS, 1)
       const int s = stile * 128 + row;
       const float cb = a.colb[s], cm = a.colm[s];
       const float a2 = a.a2, c2 = a.c2;
+      // per-block float32 sums of the rounded weights, added to float64 totals once a
+      // block (a float32 total over thousands of observations would drop the small
+      // weights of a shift against its large running sum)
       float cacc = 0.f, zacc = 0.f;
+      double cacc_d = 0.0, zacc_d = 0.0;
       for (int r0 = 0; ok && r0 < nb; r0 += G) {
         const int nq = min(G, nb - r0);
         if ((int)rank >= nq) continue;
@@ -1637,6 +1656,9 @@ __global__ void __launch_bounds__(P2I_THREADS, 1)
         }
         fence_proxy_async_smem();
         mbar_arrive(wfull);
+        cacc_d += (double)cacc;
+        zacc_d += (double)zacc;
+        cacc = zacc = 0.f;
         ++sc;
         ++m;
       }
@@ -1667,8 +1689,8 @@ __global__ void __launch_bounds__(P2I_THREADS, 1)
       }
       if (cgrp == 0) {
         const int64_t part = (int64_t)split * G + rank;
-        a.cp[part * a.Spad + s] = cacc * W_UNSCALE;
-        a.zbp[part * a.Spad + s] = zacc * W_UNSCALE;
+        a.cp[part * a.Spad + s] = (float)(cacc_d * W_UNSCALE);
+        a.zbp[part * a.Spad + s] = (float)(zacc_d * W_UNSCALE);
       }
     }
     if (!ok) raise_timeout(abort, status);
@@ -2051,9 +2073,21 @@ void plan_tc(srmra_ctx* c, int s1, int s2) {
   const int64_t per_split_old = (int64_t)n_st2 * chunks;
   const int ns_max = (int)std::max<int64_t>(1, (4 * (int64_t)sms + per_split_old / 2) /
                                                    per_split_old);
+  // The tensor cores add each MMA's products into the f32 TMEM accumulator rounding
+  // toward zero, so a Z' entry summed over many MMAs drifts toward zero by about half
+  // an ulp per addition: measured (L=96, K=3, sigma=1, one iteration against the FP64
+  // oracle) 4.2e-5 on x with the 3128 additions of 5e4 observations in one split, 9.8e-6
+  // with 6000, and three times as much with the three MMAs of the compensated M-step.
+  // So no split adds more than P2_MAX_ACC MMAs into one accumulator (8 per block of
+  // 128 observations, 24 compensated); the partial sums of the splits are added in the
+  // finalize with ordinary rounding.
+  const int acc_per_block = p.p2_comp ? 24 : 8;
+  const int blocks_max = std::max(1, P2_MAX_ACC / acc_per_block);
+  const int ns_acc = (int)std::min<int64_t>(64, ceil_div(n_iblk, blocks_max));
   int ns = 1;
   double best_ns = 0.0;
-  for (int cand = 1; cand <= ns_max && cand <= 64 && cand <= n_iblk; ++cand) {
+  for (int cand = ns_acc; cand <= std::max(ns_max, ns_acc) && cand <= 64 && cand <= n_iblk;
+       ++cand) {
     const int64_t per = ceil_div(n_iblk, cand);
     if (cand > 1 && ceil_div(n_iblk, per) != cand) continue;
     const int64_t units = (int64_t)n_st2 * ncg * cand;
@@ -2064,6 +2098,7 @@ void plan_tc(srmra_ctx* c, int s1, int s2) {
     }
   }
   ns *= s2;
+  ns = std::max(ns, ns_acc);
   ns = ns < 1 ? 1 : (ns > n_iblk ? n_iblk : ns);
   if (ns > 64) ns = 64;
   if (p.cap_nsplit > 0 && ns > p.cap_nsplit) ns = p.cap_nsplit;
