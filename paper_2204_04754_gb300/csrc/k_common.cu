@@ -549,23 +549,38 @@ int stats_t_splits(const srmra_ctx* c) {
 }
 
 // Zp[0][s][:] = sum_k Zp[k][s][:] over the nparts partial slices of pass 2 (s < S):
-// float4 rows, the slices added in order in float64, one coalesced pass, so that the
-// gather of k_fin_b reads a single slice.
+// float4 rows, one coalesced pass, so that the gather of k_fin_b reads a single slice.
+// The slices are added in order with a compensated (Kahan) float32 sum; eight loads are
+// issued before their additions so that the pass runs at memory speed.
+__device__ __forceinline__ void kahan_add(float& s, float& c, float v) {
+  const float y = v - c;
+  const float t = s + y;
+  c = (t - s) - y;
+  s = t;
+}
 __global__ void __launch_bounds__(256) k_sum_parts(float* __restrict__ Zp, int nparts,
                                                     int64_t slice, int64_t n4) {
-  for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < n4;
-       q += (int64_t)gridDim.x * blockDim.x) {
-    const float4 v0 = reinterpret_cast<const float4*>(Zp)[q];
-    double a0 = v0.x, a1 = v0.y, a2 = v0.z, a3 = v0.w;
-    for (int k = 1; k < nparts; ++k) {
-      const float4 v = reinterpret_cast<const float4*>(Zp + k * slice)[q];
-      a0 += v.x;
-      a1 += v.y;
-      a2 += v.z;
-      a3 += v.w;
-    }
-    reinterpret_cast<float4*>(Zp)[q] = make_float4((float)a0, (float)a1, (float)a2, (float)a3);
+  const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= n4) return;
+  const float4* base = reinterpret_cast<const float4*>(Zp) + q;
+  const int64_t step = slice / 4;
+  float4 s = base[0];
+  float4 c = make_float4(0.f, 0.f, 0.f, 0.f);
+  for (int k0 = 1; k0 < nparts; k0 += 8) {
+    float4 v[8];
+#pragma unroll
+    for (int j = 0; j < 8; ++j)
+      if (k0 + j < nparts) v[j] = base[(int64_t)(k0 + j) * step];
+#pragma unroll
+    for (int j = 0; j < 8; ++j)
+      if (k0 + j < nparts) {
+        kahan_add(s.x, c.x, v[j].x);
+        kahan_add(s.y, c.y, v[j].y);
+        kahan_add(s.z, c.z, v[j].z);
+        kahan_add(s.w, c.w, v[j].w);
+      }
   }
+  reinterpret_cast<float4*>(Zp)[q] = s;
 }
 
 // The E-step sums of the iteration: c_s, zb_s (float64, cfin) and the partials of b'
@@ -582,8 +597,8 @@ void launch_stats(srmra_ctx* c) {
     int nparts = c->plan.nparts_z;
     if (nparts > 1) {
       const int64_t n4 = (int64_t)g.S * g.ldy / 4;  // ldy is a multiple of 16
-      const unsigned blocks = (unsigned)std::min<int64_t>(ceil_div(n4, 256), 8 * c->num_sms);
-      k_sum_parts<<<blocks, 256, 0, c->stream>>>(c->Zp, nparts, (int64_t)g.Spad * g.ldy, n4);
+      k_sum_parts<<<(unsigned)ceil_div(n4, 256), 256, 0, c->stream>>>(
+          c->Zp, nparts, (int64_t)g.Spad * g.ldy, n4);
       c->launches++;
       nparts = 1;
     }

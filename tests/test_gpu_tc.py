@@ -163,29 +163,30 @@ def test_precision_workload_subsample_bf16x3(S):
     assert w["x"] < TOL["bf16x3"] and w["rho"] < TOL["bf16x3"] and w["lse"] < TOL["bf16x3"]
 
 
+@pytest.mark.parametrize("prec", ["fp32", "bf16x3"])
 @pytest.mark.parametrize("name", ["precision_L96_K3_N5e4_s0.2", "precision_L96_K3_N5e4_s1.0"])
-def test_precision_workload_full_size_sampled(S, name):
-    """Full size (N = 5e4): the per-observation log-likelihood lse_i of a sample of
-    observations against the oracle's direct formula, plus sum_i lse_i = LL and
-    rho on the simplex."""
+def test_precision_workload_full_size(S, name, prec):
+    """The largest single-GPU workload at full size (L = 96, K = 3, N = 5e4), both noise
+    levels: one iteration against the FP64 oracle (its polyphase-FFT formulation, pinned
+    to the dense definition; observation ranges on all host cores) element by element:
+    x, rho1, rho2, LL and every lse_i, as plain relative errors, at the form's target
+    (1e-5 float32, 1e-4 bf16x3)."""
     p = synth.workload_problem(name)
-    s = S.Solver(p.L, p.K, p.sigma, p.y, prec="bf16x3", x0=p.x0, rho1=p.rho1_0,
+    s = S.Solver(p.L, p.K, p.sigma, p.y, prec=prec, x0=p.x0, rho1=p.rho1_0,
                  rho2=p.rho2_0)
     ll = s.em_iter(1)[0]
     lse, c = s.estep()
     x, r1, r2, _, _ = s.state()
     s.close()
-    rng = np.random.default_rng(0)
-    idx = np.sort(rng.choice(p.N, size=64, replace=False))
-    _, lse_o, _ = O.estep(p.y[idx], p.x0, p.rho1_0, p.rho2_0, p.sigma, p.K)
-    yscale = (p.y[idx].astype(np.float64) ** 2).sum(axis=(1, 2)) / (2 * p.sigma ** 2)
-    err = np.max(np.abs(lse[idx] - lse_o) / (1 + np.abs(lse_o) + yscale))
-    print(name, "sampled lse err", err)
-    assert err < 1e-4
+    xo, r1o, r2o, llo, aux = FO.em_iter_fft(p.y, p.x0, p.rho1_0, p.rho2_0, p.sigma, p.K,
+                                            workers=os.cpu_count() or 1)
+    err = dict(x=rel(x, xo), rho1=rel(r1, r1o), rho2=rel(r2, r2o), c=rel(c, aux["c"]),
+               ll=abs(ll - llo) / abs(llo),
+               lse=float(np.max(np.abs(lse - aux["lse"]) / np.abs(aux["lse"]))))
+    print(name, prec, err)
+    tol = {"fp32": 1e-5, "bf16x3": 1e-4}[prec]
+    assert all(v < tol for v in err.values()), err
     assert abs(lse.sum() - ll) < 1e-9 * abs(ll)
-    assert abs(r1.sum() - 1) < 1e-12 and abs(r2.sum() - 1) < 1e-12
-    assert abs(c.sum() - p.N) < 1e-3 * p.N
-    assert np.all(np.isfinite(x))
 
 
 @pytest.mark.parametrize("L,K,N,sigma", [(64, 2, 900, 0.3), (48, 1, 400, 0.8), (96, 4, 600, 0.5),
@@ -211,6 +212,7 @@ def test_cluster_and_per_chunk_pass2_agree(S, L, K, N, sigma):
         s.close()
     # the weight sums are grouped differently (one partial per CTA of the cluster), so
     # the two agree to float32 rounding, well inside the mixed form's 1e-4 target
+    # (measured over these shapes: at most 1.5e-6 on x and 4.8e-6 on rho)
     print("cluster vs per-chunk", L, K, N, rel(out[0][0], out[1][0]),
           rel(out[0][1], out[1][1]), rel(out[0][2], out[1][2]))
     assert rel(out[0][0], out[1][0]) < 1e-5
@@ -229,7 +231,8 @@ def test_largest_request_full_size(S):
     lse, _ = s.estep()
     x, r1, r2, _, _ = s.state()
     s.close()
-    xo, r1o, r2o, llo, aux = FO.em_iter_fft(p.y, p.x0, p.rho1_0, p.rho2_0, p.sigma, p.K)
+    xo, r1o, r2o, llo, aux = FO.em_iter_fft(p.y, p.x0, p.rho1_0, p.rho2_0, p.sigma, p.K,
+                                            workers=os.cpu_count() or 1)
     yscale = (p.y.astype(np.float64) ** 2).sum(axis=(1, 2)) / (2 * p.sigma ** 2)
     tol = TOL["bf16x3"]
     assert rel(x, xo) < tol, rel(x, xo)
