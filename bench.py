@@ -290,9 +290,9 @@ def kernel_names(prec: str, plan: dict, l: int):
     if prec == "fft32":
         return f"k_fft_p1<{l}>", f"k_fft_p2<{l}>"
     n = 3 if prec == "bf16x3" else 1
-    p2 = {"per_chunk": f"k_p2_tc<{n}, false>", "per_chunk_comp": f"k_p2_tc<{n}, true>",
+    p2 = {"per_chunk": f"k_p2_tc<{n},false>", "per_chunk_comp": f"k_p2_tc<{n},true>",
           "ring": f"k_p2c_tc<{n}>", "interleaved": f"k_p2i_tc<{n}>"}[plan["p2_form"]]
-    return f"k_p1_tc<{n}>", p2
+    return f"k_p1_tc<{n},{plan.get('p1_shift_tile', 256)}>", p2
 
 
 def tc_executed_flops(p, prec: str, plan: dict):

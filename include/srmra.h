@@ -255,10 +255,11 @@ srmra_status srmra_set_wait_limit(srmra_ctx* ctx, int64_t limit_ns, int32_t test
 
 /* srmra_get_plan -- the work decomposition the context's kernels use (no computation;
  * the executed-work counts of a profile are derived from it).  out (host, n int32
- * entries, n <= 6 are filled): [0] pass-1 shift groups per observation tile, [1] pass-1
+ * entries, n <= 7 are filled): [0] pass-1 shift groups per observation tile, [1] pass-1
  * shift tiles per group, [2] pass-2 cluster size G (CTAs sharing each weight tile; 1 =
  * none), [3] pass-2 chunk groups (each recomputes the logits of a shift tile), [4] the
- * pass-2 form (SRMRA_P2_*), [5] pass-2 observation splits.  Errors: SRMRA_EINVAL. */
+ * pass-2 form (SRMRA_P2_*), [5] pass-2 observation splits, [6] shifts per pass-1 tile of
+ * the tensor-core forms (256 or 128; 0 for the others).  Errors: SRMRA_EINVAL. */
 srmra_status srmra_get_plan(const srmra_ctx* ctx, int32_t* out, int32_t n);
 
 /* ---- Batches: many independent problems advanced together (one GPU). ----

@@ -672,9 +672,9 @@ srmra_status srmra_get_plan(const srmra_ctx* c, int32_t* out, int32_t n) {
                                     : (p.p2_gc <= 4 ? SRMRA_P2_RING : SRMRA_P2_INTERLEAVED);
   else if (c->prec == SRMRA_FFT32)
     form = SRMRA_P2_FFT;
-  const int32_t v[6] = {p.p1_groups, p.p1_tiles_per_group, p.p2_gc, p.p2_chunk_groups, form,
-                        p.p2_nsplit};
-  for (int k = 0; k < n && k < 6; ++k) out[k] = v[k];
+  const int32_t v[7] = {p.p1_groups, p.p1_tiles_per_group, p.p2_gc, p.p2_chunk_groups, form,
+                        p.p2_nsplit, is_tc_prec(c->prec) ? p.p1_bn : 0};
+  for (int k = 0; k < n && k < 7; ++k) out[k] = v[k];
   return SRMRA_OK;
 }
 

@@ -202,11 +202,11 @@ def srmra_set_wait_limit(ctx: int, limit_ns: int, test_hook: int = 0) -> None:
 
 
 def srmra_get_plan(ctx: int) -> dict:
-    v = np.zeros(6, np.int32)
-    _check(lib().srmra_get_plan(ctx, v.ctypes.data, 6), ctx)
+    v = np.zeros(7, np.int32)
+    _check(lib().srmra_get_plan(ctx, v.ctypes.data, 7), ctx)
     return {"p1_groups": int(v[0]), "p1_tiles_per_group": int(v[1]), "p2_cluster": int(v[2]),
             "p2_chunk_groups": int(v[3]), "p2_form": P2_FORMS[int(v[4])],
-            "p2_splits": int(v[5])}
+            "p2_splits": int(v[5]), "p1_shift_tile": int(v[6])}
 
 
 PHASES = ["prep", "pass1", "combine", "pass2", "final", "denoise"]
