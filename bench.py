@@ -380,7 +380,7 @@ class FormRun:
     `steps` projected-EM iterations timed with CUDA events (L2 flushed before each)."""
 
     def __init__(self, p, w, workload, prec, steps, warmup, srmra, torch, stream, flush,
-                 clocks=False, local=0):
+                 clocks=False, local=0, barrier=None):
         self.p, self.prec = p, prec
         y = torch.from_numpy(p.y).cuda()
         self.s = srmra.Solver(p.L, p.K, p.sigma, y, prec=prec, x0=p.x0, rho1=p.rho1_0,
@@ -391,12 +391,16 @@ class FormRun:
         self.s.profile(True)
         self.s.profile_read()
         torch.cuda.synchronize()
+        if barrier:  # all ranks start the timed steps together
+            barrier()
         l0 = self.s.launches
         cs = ClockSampler(gpu_index(local)) if clocks else None
         if cs:
             cs.start()
         self.step_ms = time_steps(lambda: self.s.solve(1, F, sigma_bm1=0.0, loglik=False),
-                                  steps, stream, torch, flush)
+                                  steps, stream, torch, flush)  # synchronises at the end
+        if barrier:
+            barrier()
         self.clocks = cs.stop() if cs else None
         self.launches = self.s.launches - l0
         ms, n = self.s.profile_read()
@@ -888,15 +892,11 @@ def main():
     stream = torch.cuda.current_stream()
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")  # > 129 MB L2
     threads = args.oracle_threads or os.cpu_count()
-    torch.cuda.synchronize()
-    if dist:
-        dist.barrier()
     head = FormRun(p, w, args.workload, prec, args.steps, args.warmup, srmra, torch, stream,
-                   flush, clocks=True, local=local)
+                   flush, clocks=True, local=local, barrier=dist.barrier if dist else None)
     total_ms = head.total_ms
     if dist:
         total_ms = reduce_max(total_ms, dist, "cuda")
-        dist.barrier()
     value = job_throughput(p.N * p.L * p.L, args.steps, world, total_ms)
 
     out = {"metric": METRIC, "value": value, "unit": "pairs/s", "n_gpus": world,
