@@ -215,7 +215,9 @@ def run_reference(args, rank):
         p = synth.make_problem(sp["L"], sp["K"], sp["N"], sp["sigma"], sp["seed"])
     else:
         p = synth.workload_problem(args.workload)
-    cal = cpu_oracle_rate(p, 3.0)
+    # each step a sample of about 2 s of oracle work (per-call fixed costs, such as
+    # building the L^2 templates, are then a small part of it)
+    cal = cpu_oracle_rate(p, 8.0)
     n_sub = cal["n_sub"]
     from oracle import srmra_oracle as O
     x, r1, r2 = p.x0, p.rho1_0, p.rho2_0
