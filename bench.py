@@ -69,6 +69,8 @@ def parse():
     ap.add_argument("--study", default=None, choices=[None, "precision"],
                     help="precision: per-iteration one-step errors of every form against "
                          "the FP64 oracle over a projected run")
+    ap.add_argument("--n-obs", type=int, default=None,
+                    help="fewer observations than the workload's (small profiling runs)")
     ap.add_argument("--study-iters", type=int, default=40)
     ap.add_argument("--study-forms", default="fp32,bf16x3,bf16",
                     help="forms of the study (bf16x3-comp: the compensated M-step forced)")
@@ -890,7 +892,7 @@ def main():
 
     w = synth.WORKLOADS[args.workload]
     prec = args.prec or "fp32"
-    p = synth.workload_problem(args.workload, instance=rank)
+    p = synth.workload_problem(args.workload, N=args.n_obs, instance=rank)
     stream = torch.cuda.current_stream()
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")  # > 129 MB L2
     threads = args.oracle_threads or os.cpu_count()
