@@ -39,6 +39,13 @@ struct srmra_batch {
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
   cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};  // around the grouped passes
+  // side streams for the per-problem kernels (preparation, combine, finalize and
+  // projection): independent problems run concurrently, forked from and joined to the
+  // batch stream with events (branches of the captured graph)
+  static constexpr int kSide = 8;
+  cudaStream_t side[kSide] = {};
+  cudaEvent_t fork_ev = nullptr;
+  cudaEvent_t join_ev[kSide] = {};
   int tuned_s1 = 1, tuned_s2 = 1, tuned_order = 0, tuned_bn = 256;
   double tuned_ms = 0.0;
   std::string err;
@@ -151,22 +158,48 @@ cudaError_t launch_pass(srmra_batch* b, int pass) {
   return cudaGetLastError();
 }
 
+// Runs `work(c)` for every context of the batch, problem k on side stream k mod kSide
+// (each problem's kernels stay in order on one stream), after everything enqueued on
+// the batch stream so far; the batch stream then waits for all of them.
+template <typename Work>
+cudaError_t per_problem(srmra_batch* b, Work work) {
+  cudaError_t e = cudaEventRecord(b->fork_ev, b->stream);
+  const int ns = std::min<int>(srmra_batch::kSide, (int)b->ctxs.size());
+  for (int k = 0; k < ns && e == cudaSuccess; ++k) e = cudaStreamWaitEvent(b->side[k], b->fork_ev, 0);
+  for (size_t i = 0; i < b->ctxs.size() && e == cudaSuccess; ++i) {
+    srmra_ctx* c = b->ctxs[i];
+    const cudaStream_t own = c->stream;
+    c->stream = b->side[i % srmra_batch::kSide];
+    work(c);
+    c->stream = own;
+    e = cudaGetLastError();
+  }
+  for (int k = 0; k < ns && e == cudaSuccess; ++k) {
+    e = cudaEventRecord(b->join_ev[k], b->side[k]);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(b->stream, b->join_ev[k], 0);
+  }
+  return e;
+}
+
 // One EM iteration + scheduled projection for every context of the batch.
 cudaError_t enqueue_iteration(srmra_batch* b) {
-  for (auto* c : b->ctxs) launch_prep_iter(c);
+  cudaError_t e = per_problem(b, [](srmra_ctx* c) { launch_prep_iter(c); });
+  if (e != cudaSuccess) return e;
   cudaEventRecord(b->ev[0], b->stream);
-  cudaError_t e = launch_pass(b, 1);
+  e = launch_pass(b, 1);
   if (e != cudaSuccess) return e;
   cudaEventRecord(b->ev[1], b->stream);
-  for (auto* c : b->ctxs) launch_lse_combine(c, c->plan.p1_groups);
+  e = per_problem(b, [](srmra_ctx* c) { launch_lse_combine(c, c->plan.p1_groups); });
+  if (e != cudaSuccess) return e;
   cudaEventRecord(b->ev[2], b->stream);
   e = launch_pass(b, 2);
   if (e != cudaSuccess) return e;
   cudaEventRecord(b->ev[3], b->stream);
-  for (auto* c : b->ctxs) {
+  e = per_problem(b, [](srmra_ctx* c) {
     launch_finalize(c, 0);
     launch_dct_sched(c, 2.7);
-  }
+  });
+  if (e != cudaSuccess) return e;
   return cudaGetLastError();
 }
 
@@ -220,7 +253,7 @@ srmra_status time_passes(srmra_batch* b, int reps, double* ms) {
   for (int r = 0; r < reps + 1; ++r) {
     BCK(b, cudaEventRecord(e0, b->stream));
     BCK(b, launch_pass(b, 1));
-    for (auto* c : b->ctxs) launch_lse_combine(c, c->plan.p1_groups);
+    BCK(b, per_problem(b, [](srmra_ctx* c) { launch_lse_combine(c, c->plan.p1_groups); }));
     BCK(b, launch_pass(b, 2));
     BCK(b, cudaEventRecord(e1, b->stream));
     BCK(b, cudaEventSynchronize(e1));
@@ -314,6 +347,11 @@ srmra_status srmra_batch_create(srmra_ctx** ctxs, int32_t count, uint32_t flags,
                   : b->prec == SRMRA_FFT32 ? fft_set_attributes()
                                            : simt_set_attributes();
   for (int k = 0; k < 4 && e == cudaSuccess; ++k) e = cudaEventCreate(&b->ev[k]);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->fork_ev, cudaEventDisableTiming);
+  for (int k = 0; k < srmra_batch::kSide && e == cudaSuccess; ++k) {
+    e = cudaStreamCreateWithFlags(&b->side[k], cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->join_ev[k], cudaEventDisableTiming);
+  }
   if (e == cudaSuccess) e = cudaMalloc((void**)&b->d_status, sizeof(int));
   if (e == cudaSuccess) e = cudaMemsetAsync(b->d_status, 0, sizeof(int), b->stream);
   if (e == cudaSuccess && is_tc(b->prec)) {
@@ -426,6 +464,11 @@ void srmra_batch_destroy(srmra_batch* b) {
   cudaStreamSynchronize(b->stream);
   for (int k = 0; k < 4; ++k)
     if (b->ev[k]) cudaEventDestroy(b->ev[k]);
+  if (b->fork_ev) cudaEventDestroy(b->fork_ev);
+  for (int k = 0; k < srmra_batch::kSide; ++k) {
+    if (b->side[k]) cudaStreamDestroy(b->side[k]);
+    if (b->join_ev[k]) cudaEventDestroy(b->join_ev[k]);
+  }
   if (b->exec) cudaGraphExecDestroy(b->exec);
   if (b->graph) cudaGraphDestroy(b->graph);
   if (b->cap_stream) cudaStreamDestroy(b->cap_stream);
