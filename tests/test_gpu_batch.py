@@ -103,6 +103,25 @@ def test_batched_step_against_oracle(S):
         s.close()
 
 
+def test_batch_pass1_tile_widths(S):
+    """Contexts with different pass-1 tile widths (SRMRA_FLAG_P1_TILE128) form a batch
+    only with the autotuner, which gives them one width; srmra_batch_tiles reports it."""
+    probs = problems()[:3]
+    ss = [S.Solver(p.L, p.K, p.sigma, p.y, prec="bf16x3", x0=p.x0, rho1=p.rho1_0,
+                   rho2=p.rho2_0, flags=16 if k == 1 else 0) for k, p in enumerate(probs)]
+    assert [s.plan()["p1_shift_tile"] for s in ss] == [256, 128, 256]
+    with pytest.raises(S.SrmraError) as e:
+        S.Batch(ss, autotune=False)
+    assert e.value.status == S.SRMRA_EINVAL
+    b = S.Batch(ss, autotune=True)
+    w = b.tuning()["p1_shift_tile"]
+    assert w in (128, 256) and all(s.plan()["p1_shift_tile"] == w for s in ss)
+    b.solve(1, 1)
+    b.close()
+    for s in ss:
+        s.close()
+
+
 def test_batch_rejects_mixed_precision_and_duplicates(S):
     probs = problems()[:2]
     a = solver(S, probs[0], "bf16x3")

@@ -126,9 +126,11 @@ def test_sharded_driver_through_nccl_world_of_one(S):
         b = S.Solver(p.L, p.K, p.sigma, p.y, x0=p.x0, rho1=p.rho1_0, rho2=p.rho2_0,
                      stream=stream)
         llb = b.solve(4, 2, sigma_bm1=0.05)
-        xa, r1a, _, _, ta = a.state()
-        xb, r1b, _, _, tb = b.state()
+        xa, r1a, _, sa, ta = a.state()
+        xb, r1b, _, sb, tb = b.state()
         assert ta == tb == 4
+        # the library applied Algorithm 2's schedule in the M-step of the sharded run
+        assert sa == sb == 0.05 * 2.0 ** -0.2
         # four iterations of two float32 runs that differ in the order of their sums:
         # within the float32 form's tolerance
         assert P.rel(xa, xb) < 1e-5 and P.rel(r1a, r1b) < 1e-5, (P.rel(xa, xb), P.rel(r1a, r1b))
