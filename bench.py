@@ -69,6 +69,9 @@ def parse():
     ap.add_argument("--study", default=None, choices=[None, "precision"],
                     help="precision: per-iteration one-step errors of every form against "
                          "the FP64 oracle over a projected run")
+    ap.add_argument("--flags", type=int, default=0,
+                    help="context flags of the timed forms (srmra.SRMRA_FLAG_*; e.g. 32 asks "
+                         "for the pair form of the tensor-core pass 2)")
     ap.add_argument("--n-obs", type=int, default=None,
                     help="fewer observations than the workload's (small profiling runs)")
     ap.add_argument("--study-iters", type=int, default=40)
@@ -295,7 +298,8 @@ def kernel_names(prec: str, plan: dict, l: int):
         return f"k_fft_p1<{l}>", f"k_fft_p2<{l}>"
     n = 3 if prec == "bf16x3" else 1
     p2 = {"per_chunk": f"k_p2_tc<{n},false>", "per_chunk_comp": f"k_p2_tc<{n},true>",
-          "ring": f"k_p2c_tc<{n}>", "interleaved": f"k_p2i_tc<{n}>"}[plan["p2_form"]]
+          "ring": f"k_p2c_tc<{n}>", "interleaved": f"k_p2i_tc<{n}>",
+          "pair": f"k_p2p_tc<{n}>"}[plan["p2_form"]]
     return f"k_p1_tc<{n},{plan.get('p1_shift_tile', 256)}>", p2
 
 
@@ -384,11 +388,11 @@ class FormRun:
     `steps` projected-EM iterations timed with CUDA events (L2 flushed before each)."""
 
     def __init__(self, p, w, workload, prec, steps, warmup, srmra, torch, stream, flush,
-                 clocks=False, local=0, barrier=None):
+                 clocks=False, local=0, barrier=None, flags=0):
         self.p, self.prec = p, prec
         y = torch.from_numpy(p.y).cuda()
         self.s = srmra.Solver(p.L, p.K, p.sigma, y, prec=prec, x0=p.x0, rho1=p.rho1_0,
-                              rho2=p.rho2_0, stream=stream.cuda_stream)
+                              rho2=p.rho2_0, stream=stream.cuda_stream, flags=flags)
         del y
         F = w["F"]
         self.s.solve(warmup, F, sigma_bm1=1.0, loglik=False)
@@ -897,7 +901,8 @@ def main():
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")  # > 129 MB L2
     threads = args.oracle_threads or os.cpu_count()
     head = FormRun(p, w, args.workload, prec, args.steps, args.warmup, srmra, torch, stream,
-                   flush, clocks=True, local=local, barrier=dist.barrier if dist else None)
+                   flush, clocks=True, local=local, barrier=dist.barrier if dist else None,
+                   flags=args.flags)
     total_ms = head.total_ms
     if dist:
         total_ms = reduce_max(total_ms, dist, "cuda")
@@ -924,7 +929,7 @@ def main():
         # against the FP64 oracle after one iteration from a common state
         forms = ("bf16x3", "bf16") + (("fft32",) if p.l in (8, 16, 32) else ())
         runs = [head] + [FormRun(p, w, args.workload, f, args.steps, args.warmup, srmra,
-                                 torch, stream, flush) for f in forms]
+                                 torch, stream, flush, flags=args.flags) for f in forms]
         err, how = errors_vs_oracle(p, runs, threads)
         out["error_vs_oracle"] = dict(err["fp32"], how=how)
         out["forms"] = {}

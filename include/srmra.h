@@ -95,6 +95,10 @@ typedef enum {
 /* Tensor-core forms: pass 1 uses 128-shift tiles (four TMEM accumulators) instead of
  * 256-shift tiles (two); a batch's autotuner also chooses between them. */
 #define SRMRA_FLAG_P1_TILE128 16u
+/* SRMRA_BF16X3 with up to four 256-pixel chunks (L/K <= 32): pass 2 in the pair form,
+ * 2-CTA tensor-core MMAs (cta_group::2) on two shift tiles at once, one per CTA of a
+ * pair (clusters of 2G CTAs for G chunks). */
+#define SRMRA_FLAG_P2_PAIR 32u
 
 typedef struct {
   int32_t L_high;  /* L >= 2 */
@@ -252,14 +256,16 @@ srmra_status srmra_set_wait_limit(srmra_ctx* ctx, int64_t limit_ns, int32_t test
 #define SRMRA_P2_FP32 3        /* float32 persistent clusters */
 #define SRMRA_P2_FFT 4         /* polyphase-FFT form */
 #define SRMRA_P2_PER_CHUNK_COMP 5 /* tensor cores, per chunk, compensated M-step (bf16x3) */
+#define SRMRA_P2_PAIR 6        /* tensor cores, 2-CTA MMAs, clusters of 2-8 (bf16x3) */
 
 /* srmra_get_plan -- the work decomposition the context's kernels use (no computation;
  * the executed-work counts of a profile are derived from it).  out (host, n int32
  * entries, n <= 7 are filled): [0] pass-1 shift groups per observation tile, [1] pass-1
  * shift tiles per group, [2] pass-2 cluster size G (CTAs sharing each weight tile; 1 =
- * none), [3] pass-2 chunk groups (each recomputes the logits of a shift tile), [4] the
- * pass-2 form (SRMRA_P2_*), [5] pass-2 observation splits, [6] shifts per pass-1 tile of
- * the tensor-core forms (256 or 128; 0 for the others).  Errors: SRMRA_EINVAL. */
+ * none; the pair form: pairs per cluster), [3] pass-2 chunk groups (each recomputes
+ * the logits of a shift tile), [4] the pass-2 form (SRMRA_P2_*), [5] pass-2 observation
+ * splits, [6] shifts per pass-1 tile of the tensor-core forms (256 or 128; 0 for the
+ * others).  Errors: SRMRA_EINVAL. */
 srmra_status srmra_get_plan(const srmra_ctx* ctx, int32_t* out, int32_t n);
 
 /* ---- Batches: many independent problems advanced together (one GPU). ----

@@ -220,6 +220,7 @@ void setup_ctx(srmra_ctx* c, const srmra_params* p, int num_sms, int caps[3]) {
     caps[2] = c->plan.nparts_c;
   } else if (is_tc_prec(c->prec)) {
     c->plan.p2_comp = tc_comp_mstep(g, c->prec, c->flags);
+    c->plan.p2_pair = tc_pair_form(g, c->prec, c->flags, c->plan.p2_comp);
     if (c->flags & SRMRA_FLAG_P1_TILE128) c->plan.p1_bn = 128;
     // size the partial buffers for the finest decomposition the batch tuner may pick
     plan_tc(c, 2, 2);
@@ -667,9 +668,10 @@ srmra_status srmra_get_plan(const srmra_ctx* c, int32_t* out, int32_t n) {
   const Plan& p = c->plan;
   int form = SRMRA_P2_FP32;
   if (is_tc_prec(c->prec))
-    form = p.p2_comp ? SRMRA_P2_PER_CHUNK_COMP
-                     : p.p2_gc <= 1 ? SRMRA_P2_PER_CHUNK
-                                    : (p.p2_gc <= 4 ? SRMRA_P2_RING : SRMRA_P2_INTERLEAVED);
+    form = p.p2_comp   ? SRMRA_P2_PER_CHUNK_COMP
+           : p.p2_pair ? SRMRA_P2_PAIR
+           : p.p2_gc <= 1 ? SRMRA_P2_PER_CHUNK
+                          : (p.p2_gc <= 4 ? SRMRA_P2_RING : SRMRA_P2_INTERLEAVED);
   else if (c->prec == SRMRA_FFT32)
     form = SRMRA_P2_FFT;
   const int32_t v[7] = {p.p1_groups, p.p1_tiles_per_group, p.p2_gc, p.p2_chunk_groups, form,

@@ -91,6 +91,8 @@ struct TcP2Args {
 // and the arguments of both passes.  Kept in device memory; TMA reads the maps there.
 struct TcInst {
   CUtensorMap tmY, tmYl, tmA256, tmAl256, tmA128, tmAl128, tmYT, tmYTl;
+  // pair form: 64-observation boxes of Y' (hi, lo) and 128-pixel boxes of Y'^T
+  CUtensorMap tmY64, tmYl64, tmYT128;
   TcP1Args p1;
   TcP2Args p2;
 };
@@ -1233,6 +1235,532 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
 constexpr size_t P2R_SMEM = 1024 + P2R_SLOTS * SLOT + P2R_BOOK + 1024;
 static_assert(P2R_SMEM <= 232448, "exceeds the shared memory of one CTA");
 
+// ---- pair form
+// The CTAs of a cluster form pairs (cluster ranks 2p, 2p + 1) that issue 2-CTA tcgen05
+// MMAs (cta_group::2): the even CTA of a pair issues every MMA of the pair; each CTA
+// holds its own rows of the A operand and half of the columns of the B operand, and
+// its own rows of the accumulator in its Tensor Memory.  A pair works on two 128-shift
+// tiles at once, one per CTA:
+// - the logits of a 128-observation block are a 256 x 128 product per k-step, each CTA
+//   loading its own templates and 64 of the block's observations;
+// - Z' of a 256-pixel chunk is a 256 x 256 product per k-step, each CTA loading 128 of
+//   the chunk's pixels of Y'^T;
+// so each SM reads about a quarter fewer operand bytes from shared memory per flop than
+// with one CTA's 128 x 128 and 128 x 256 products (the tensor-core pass 2 is bound by
+// shared-memory bandwidth).  The G pairs of a cluster share their weight tiles as in
+// the ring form, among the CTAs of the same parity (the same shift tile): every weight
+// tile and Y'^T tile goes through the 7-slot ring, the slots of a round's weight tiles
+// are reserved first (each tile's Y'^T fill lies nqp <= 4 places after its slot, so no
+// fill waits for a slot that only its own products release), and the owner sends its
+// tile once all G reservations are in.  Both CTAs of a pair run the same sequence of
+// fills, so a fill has the same slot in both.  The odd CTA's TMA loads complete on the
+// even CTA's barrier (cta_group::2 loads), which expects the bytes of both; a weight
+// tile copied into a CTA completes on that CTA's barrier, and the odd CTA's MMA warp
+// relays each of its weight fills to the even CTA (pfull), whose MMA thread waits on
+// both before it reads the slot of both CTAs.  Each MMA completion is committed to the barriers of both CTAs,
+// and the odd CTA's epilogue warps report a drained accumulator to the even CTA (one
+// arrival per warp).
+constexpr int P2P_MAX_G = 4;  // pairs per cluster (clusters of up to 8 CTAs)
+constexpr int P2_KEY_PAIR = 32;  // pass-2 launch keys above it: the pair form
+// barriers: full, pfull, empty (ring), sfull, sempty, zfull, zempty, mfull (rows), drain,
+// wready, never; then the mailbox, the TMEM address and the abort flag
+static_assert((3 * P2R_SLOTS + 2 + 2 + 1 + 1 + MBOX_DEPTH + 1 + 1 + 1) * 8 +
+                      MBOX_DEPTH * P2P_MAX_G * 4 + 4 + 4 <= P2R_BOOK,
+              "pair-form bookkeeping exceeds its P2R_BOOK bytes");
+
+template <int NPROD>
+__global__ void __launch_bounds__(TC_THREADS, 1)
+    k_p2p_tc(const TcInst* __restrict__ insts, const int64_t* __restrict__ ustart, int n_inst,
+             int G, int* status) {
+  static_assert(NPROD == 3, "the pair form is built for split-bf16 logits");
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* smem = align1024(smem_raw);
+  uint64_t* full = (uint64_t*)(smem + P2R_SLOTS * SLOT);
+  uint64_t* pfull = full + P2R_SLOTS;  // even CTA: the odd CTA's fill of the slot is in
+  uint64_t* empty = pfull + P2R_SLOTS;
+  uint64_t* sfull = empty + P2R_SLOTS;
+  uint64_t* sempty = sfull + 2;
+  uint64_t* zfull = sempty + 2;
+  uint64_t* zempty = zfull + 1;
+  uint64_t* mfull = zempty + 1;  // [MBOX_DEPTH]: one barrier per mailbox row
+  uint64_t* drain = mfull + MBOX_DEPTH;
+  uint64_t* wready = drain + 1;  // the 128 epilogue threads have written the weight tile
+  uint64_t* never = wready + 1;  // nothing arrives on it (test hook)
+  uint32_t* mbox = (uint32_t*)(never + 1);  // [MBOX_DEPTH][P2P_MAX_G] reserved slots
+  uint32_t* tptr = mbox + MBOX_DEPTH * P2P_MAX_G;
+  volatile int* abort = (volatile int*)(tptr + 1);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const uint64_t wlim = insts[0].p2.wait_ns;
+  const int hook = insts[0].p2.hook;
+  const uint32_t rank = cluster_rank();
+  const uint32_t peer = rank ^ 1u;  // the other CTA of the pair
+  const int h = (int)(rank & 1u), pr = (int)(rank >> 1);
+  const int64_t cid = blockIdx.x / (2 * G), ncl = gridDim.x / (2 * G);
+
+  if (threadIdx.x == 0) {
+    for (int k = 0; k < P2R_SLOTS; ++k) {
+      mbar_init(&full[k], 1);
+      mbar_init(&pfull[k], 1);
+      mbar_init(&empty[k], 1);
+    }
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(&sfull[b], 1);
+      mbar_init(&sempty[b], 128 + 4);  // even CTA: its 128 threads + the odd CTA's 4 warps
+    }
+    mbar_init(zfull, 1);
+    mbar_init(zempty, 128 + 4);
+    for (int k = 0; k < MBOX_DEPTH; ++k) mbar_init(&mfull[k], G);
+    mbar_init(drain, 1);
+    mbar_init(wready, 128);
+    mbar_init(never, 1);
+    *abort = 0;
+    fence_mbar_init();
+  }
+  // every CTA's barriers exist before any peer arrives on them, and both CTAs of a pair
+  // are running before they allocate Tensor Memory together
+  cluster_sync_all();
+  if (warp == 1) {
+    tmem_alloc_pair(tptr, 512);
+    tmem_relinquish_pair();
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  cluster_sync_all();  // the pair's allocation is complete in both CTAs
+  const uint32_t tbase = *tptr;
+  const int64_t total = ustart[n_inst];
+
+  if (warp == 0) {
+    if (lane == 0) {
+      uint32_t it = 0, sent[P2P_MAX_G] = {};
+      bool wfill[P2R_SLOTS] = {};  // the slot's last fill is a weight tile (lands locally)
+      uint32_t wcnt[P2R_SLOTS] = {};  // weight-tile fills of each slot so far
+      bool ok = true;
+      auto reserve = [&](uint32_t tx) -> int {
+        const int st = it % P2R_SLOTS;
+        if (!mbar_wait(&empty[st], ((it / P2R_SLOTS) & 1) ^ 1, abort, wlim)) {
+          ok = false;
+          return -1;
+        }
+        if (tx) mbar_expect_tx(&full[st], tx);
+        return st;
+      };
+      // a TMA fill of the pair: the even CTA expects the bytes of both CTAs on its
+      // barrier, the odd CTA's loads complete there too
+      auto reserve_tma = [&](uint32_t bytes) -> int {
+        const int st = reserve(h == 0 ? 2u * bytes : 0u);
+        if (st >= 0) wfill[st] = false;
+        return st;
+      };
+      const uint32_t lead_full = mapa(smem_u32(full), peer);  // odd CTA: the even CTA's full[0]
+      auto load = [&](int st, int off, const CUtensorMap* map, int c0, int c1) {
+        if (h == 0)
+          tma_load_2d(smem + st * SLOT + off, map, &full[st], c0, c1);
+        else
+          tma_load_2d_pair(smem + st * SLOT + off, map, lead_full + 8u * (uint32_t)st, c0, c1);
+      };
+      for (int64_t u = cid; ok && u < total; u += ncl) {
+        const int ki = find_inst(ustart, n_inst, u);
+        const TcInst* I = insts + ki;
+        const TcP2Args& a = I->p2;
+        const int64_t lu = u - ustart[ki];
+        const int ncg = (a.n_chunks + G - 1) / G;
+        const int per_split = (a.n_stiles / 2) * ncg;
+        const int split = (int)(lu / per_split), rem = (int)(lu % per_split);
+        const int stile = (rem / ncg) * 2 + h, chunk = (rem % ncg) * G + pr;
+        const bool cvalid = chunk < a.n_chunks;
+        const int jb0 = split * a.iblk_per_split;
+        const int nb = min(a.n_iblk, jb0 + a.iblk_per_split) - jb0;
+        const int rounds = (nb + G - 1) / G;
+        for (int j = 0; ok && j <= rounds; ++j) {
+          const int r0 = j * G, nq = j < rounds ? min(G, nb - r0) : 0;
+          if (pr < nq) {  // logits of the pair's block: this CTA's 64 observations of it
+            const int ib = (jb0 + r0 + pr) * 128 + h * 64;
+            for (int kb = 0; ok && kb < a.nk; kb += 2) {
+              const int nkk = min(2, a.nk - kb);
+              for (int t = 0; ok && t < nkk; ++t) {  // templates of k-blocks kb, kb + 1
+                const int st = reserve_tma(32768);
+                if (!ok) break;
+                load(st, 0, &I->tmA128, (kb + t) * 64, stile * 128);
+                load(st, 16384, &I->tmAl128, (kb + t) * 64, stile * 128);
+                ++it;
+              }
+              if (!ok) break;
+              const int st = reserve_tma(16384u * (uint32_t)nkk);  // observations: hi, lo
+              if (!ok) break;
+              for (int t = 0; t < nkk; ++t) {
+                load(st, t * 16384, &I->tmY64, (kb + t) * 64, ib);
+                load(st, t * 16384 + 8192, &I->tmYl64, (kb + t) * 64, ib);
+              }
+              ++it;
+            }
+          }
+          // round j - 1: a slot for the weight tile of every block, announced to the
+          // tile's owner (the CTA of the same parity in the block's pair), then this
+          // CTA's 128 pixels of the Y'^T tile of every block
+          const int rp = (j - 1) * G, nqp = j >= 1 ? min(G, nb - rp) : 0;
+          for (int i = 0; ok && i < nqp; ++i) {
+            const int st = reserve(i != pr ? 32768u : 0u);
+            if (!ok) break;
+            wfill[st] = true;
+            ++wcnt[st];
+            const uint32_t owner = 2u * (uint32_t)i + (uint32_t)h;
+            // row sent % DEPTH of the owner's mailbox, and that row's own barrier
+            const uint32_t row = sent[i] % MBOX_DEPTH;
+            st_cluster_u32(mapa(smem_u32(mbox + row * P2P_MAX_G + pr), owner), (uint32_t)st);
+            mbar_arrive_cluster(mapa(smem_u32(&mfull[row]), owner));
+            ++sent[i];
+            ++it;
+          }
+          for (int i = 0; ok && cvalid && i < nqp; ++i) {
+            const int st = reserve_tma(32768);
+            if (!ok) break;
+            const int ibq = (jb0 + rp + i) * 128;
+            for (int hh = 0; hh < 2; ++hh)
+              load(st, hh * 16384, &I->tmYT128, ibq + hh * 64, chunk * 256 + h * 128);
+            ++it;
+          }
+        }
+      }
+      if (!ok) raise_timeout(abort, status);
+      {
+        // the fills already issued land before the CTA exits, also when another role
+        // gave up and stopped consuming them (the odd CTA's TMA fills complete on the
+        // even CTA's barriers, whose producer waits for them; the final cluster barrier
+        // keeps the odd CTA until then)
+        // the odd CTA's barriers see only its weight fills, so their phases count those
+        const uint32_t lo = it > P2R_SLOTS ? it - P2R_SLOTS : 0;
+        int zero = 0;
+        for (uint32_t k = lo; k < it; ++k) {
+          const int st = k % P2R_SLOTS;
+          if (h == 0)
+            mbar_wait(&full[st], (k / P2R_SLOTS) & 1, (volatile int*)&zero);
+          else if (wfill[st])
+            mbar_wait(&full[st], (wcnt[st] - 1) & 1, (volatile int*)&zero);
+        }
+      }
+    }
+  } else if (warp == 1) {
+    if (lane == 0) {
+      // even CTA: the pair's MMAs; odd CTA: relays its completed fills to the even CTA,
+      // in the order in which the even CTA's MMA thread waits for them
+      const bool issuer = h == 0;
+      constexpr uint32_t idS = idesc_bf16_f32(256, 128);
+      constexpr uint32_t idZ = idesc_f16_f32(256, 256);
+      uint32_t it = 0, sc = 0, uc = 0;
+      bool ok = true;
+      // TMA fill k has landed in both CTAs (issuer; the odd CTA skips it)
+      auto take = [&](uint32_t k) -> int {
+        const int st = k % P2R_SLOTS;
+        if (issuer && !mbar_wait_cluster(&full[st], (k / P2R_SLOTS) & 1, abort, wlim)) {
+          ok = false;
+          return -1;
+        }
+        return st;
+      };
+      // weight-tile fill k has landed in both CTAs (issuer) / relay it (odd CTA).  The
+      // odd CTA's barrier of the slot and the even CTA's pfull of it see only weight
+      // fills: their phases count those (wc), the even CTA's full counts every fill.
+      uint32_t wc[P2R_SLOTS] = {};
+      auto take_w = [&](uint32_t k) -> int {
+        const int st = k % P2R_SLOTS;
+        const uint32_t wpar = wc[st] & 1;
+        ++wc[st];
+        if (!mbar_wait(&full[st], issuer ? (k / P2R_SLOTS) & 1 : wpar, abort, wlim)) {
+          ok = false;
+          return -1;
+        }
+        if (issuer) {
+          if (!mbar_wait_cluster(&pfull[st], wpar, abort, wlim)) {
+            ok = false;
+            return -1;
+          }
+        } else {
+          mbar_arrive_cluster(mapa(smem_u32(&pfull[st]), peer));
+        }
+        return st;
+      };
+      // the products that read a slot are done: free it in both CTAs
+      auto release = [&](uint64_t* bar) {
+        mma_commit_pair(smem_u32(bar));
+        mma_commit_pair(mapa(smem_u32(bar), peer));
+      };
+      for (int64_t u = cid; ok && u < total; u += ncl) {
+        const int ki = find_inst(ustart, n_inst, u);
+        const TcInst* I = insts + ki;
+        const TcP2Args& a = I->p2;
+        const int64_t lu = u - ustart[ki];
+        const int ncg = (a.n_chunks + G - 1) / G;
+        const int per_split = (a.n_stiles / 2) * ncg;
+        const int rem = (int)(lu % per_split);
+        const int chunk = (rem % ncg) * G + pr;
+        const bool cvalid = chunk < a.n_chunks;
+        const int split = (int)(lu / per_split);
+        const int jb0 = split * a.iblk_per_split;
+        const int nb = min(a.n_iblk, jb0 + a.iblk_per_split) - jb0;
+        bool first_z = true;
+        const int rounds = (nb + G - 1) / G;
+        for (int j = 0; ok && j <= rounds; ++j) {
+          const int r0 = j * G, nq = j < rounds ? min(G, nb - r0) : 0;
+          if (pr < nq) {
+            const int b = sc & 1;
+            if (issuer && !mbar_wait_cluster(&sempty[b], ((sc >> 1) & 1) ^ 1, abort, wlim)) {
+              ok = false;
+              break;
+            }
+            tc_fence_after();
+            const uint32_t d = tbase + (uint32_t)(b * 128);
+            for (int kb = 0; ok && kb < a.nk; kb += 2) {
+              const int nkk = min(2, a.nk - kb);
+              int stA[2] = {0, 0};
+              for (int t = 0; ok && t < nkk; ++t) stA[t] = take(it++);
+              if (!ok) break;
+              const int stY = take(it++);
+              if (!ok || !issuer) continue;
+              tc_fence_after();
+              for (int t = 0; t < nkk; ++t) {
+                const uint8_t* sA = smem + stA[t] * SLOT;
+                const uint8_t* sY = smem + stY * SLOT + t * 16384;
+                const uint64_t dA = desc_sw128(sA), dAl = desc_sw128(sA + 16384);
+                const uint64_t dY = desc_sw128(sY), dYl = desc_sw128(sY + 8192);
+#pragma unroll
+                for (int k4 = 0; k4 < 4; ++k4) {
+                  mma_f16_pair(d, desc_advance(dA, k4), desc_advance(dY, k4), idS,
+                               (kb + t > 0 || k4 > 0) ? 1u : 0u);
+                  mma_f16_pair(d, desc_advance(dA, k4), desc_advance(dYl, k4), idS, 1u);
+                  mma_f16_pair(d, desc_advance(dAl, k4), desc_advance(dY, k4), idS, 1u);
+                }
+                release(&empty[stA[t]]);
+              }
+              release(&empty[stY]);
+            }
+            if (!ok) break;
+            if (issuer) release(&sfull[b]);
+            ++sc;
+          }
+          // Z' of round j - 1: weight tile i (slot it + i) times this pair's Y'^T tile i
+          // (slot it + nqp + i)
+          const int nqp = j >= 1 ? min(G, nb - (j - 1) * G) : 0;
+          const uint32_t base = it;
+          it += (uint32_t)(cvalid ? 2 * nqp : nqp);
+          for (int i = 0; ok && i < nqp; ++i) {
+            const int stW = take_w(base + (uint32_t)i);
+            if (!ok) break;
+            if (cvalid) {
+              if (issuer && first_z && !mbar_wait_cluster(zempty, (uc & 1) ^ 1, abort, wlim)) {
+                ok = false;
+                break;
+              }
+              const int stT = take(base + (uint32_t)(nqp + i));
+              if (!ok) break;
+              if (issuer) {
+                tc_fence_after();
+                const uint32_t dZ = tbase + 256u;
+                for (int hh = 0; hh < 2; ++hh) {
+                  const uint64_t dP = desc_sw128(smem + stW * SLOT + hh * 16384);
+                  const uint64_t dT = desc_sw128(smem + stT * SLOT + hh * 16384);
+#pragma unroll
+                  for (int k4 = 0; k4 < 4; ++k4)
+                    mma_f16_pair(dZ, desc_advance(dP, k4), desc_advance(dT, k4), idZ,
+                                 (!first_z || hh > 0 || k4 > 0) ? 1u : 0u);
+                }
+                release(&empty[stT]);
+              }
+              first_z = false;
+            }
+            if (issuer) release(&empty[stW]);
+          }
+        }
+        if (!ok) break;
+        if (cvalid) {
+          if (issuer) release(zfull);
+          ++uc;
+        }
+      }
+      if (!ok) raise_timeout(abort, status);
+      if (issuer) {
+        // every issued MMA completes before the Tensor Memory is released, also when
+        // another role gave up and left accumulators unread
+        mma_commit_pair(smem_u32(drain));
+        int zero = 0;
+        mbar_wait(drain, 0, (volatile int*)&zero);
+      }
+    }
+  } else {
+    const int q = warp & 3;
+    const int row = q * 32 + lane;
+    const uint32_t lane_addr = tbase + ((uint32_t)(q * 32) << 16);
+    float2* wobs = (float2*)(smem + P2R_SLOTS * SLOT + P2R_BOOK) + q * 32;  // warp's staging
+    uint32_t sc = 0, mr = 0, uc = 0;
+    bool ok = true;
+    // an accumulator of the pair has been read: the even CTA counts its own 128 threads,
+    // the odd CTA reports once per warp
+    auto drained = [&](uint64_t* bar) {
+      tc_fence_before();
+      if (h == 0) {
+        mbar_arrive(bar);
+      } else {
+        __syncwarp();
+        if (lane == 0) mbar_arrive_cluster(mapa(smem_u32(bar), peer));
+      }
+    };
+    for (int64_t u = cid; ok && u < total; u += ncl) {
+      const int ki = find_inst(ustart, n_inst, u);
+      const TcInst* I = insts + ki;
+      const TcP2Args& a = I->p2;
+      const int64_t lu = u - ustart[ki];
+      const int ncg = (a.n_chunks + G - 1) / G;
+      const int per_split = (a.n_stiles / 2) * ncg;
+      const int split = (int)(lu / per_split), rem = (int)(lu % per_split);
+      const int stile = (rem / ncg) * 2 + h, cgrp = rem % ncg;
+      const int chunk = cgrp * G + pr;
+      const bool cvalid = chunk < a.n_chunks;
+      const int jb0 = split * a.iblk_per_split;
+      const int nb = min(a.n_iblk, jb0 + a.iblk_per_split) - jb0;
+      const int s = stile * 128 + row;
+      const float cb = a.colb[s], cm = a.colm[s];
+      const float a2 = a.a2, c2 = a.c2;
+      // per-block float32 sums of the rounded weights, added to float64 totals once a
+      // block
+      float cacc = 0.f, zacc = 0.f;
+      double cacc_d = 0.0, zacc_d = 0.0;
+      for (int r0 = 0; ok && r0 < nb; r0 += G) {
+        const int nq = min(G, nb - r0);
+        if (pr >= nq) continue;
+        const int64_t ib = (int64_t)(jb0 + r0 + pr) * 128;
+        const int b = sc & 1;
+        // (ybar, lse2) of the next 32-observation chunk, loaded one chunk ahead of its
+        // use; lse2 = +inf past N gives weight 0
+        float ny = a.ybar[ib + lane];
+        float nl = (ib + lane < a.N) ? a.lse2[ib + lane] : INFINITY;
+        // test hook: the first cluster's rank 0 never builds its first tile, so the waits
+        // of the CTAs of its parity for that tile run out as well
+        const bool held = hook == 2 && blockIdx.x == 0 && sc == 0;
+        ok = __all_sync(0xffffffffu,
+                        (!held || mbar_wait(never, 0, abort, wlim)) &&
+                            mbar_wait_cluster(&sfull[b], (sc >> 1) & 1, abort, wlim));
+        if (!ok) break;
+        tc_fence_after();
+        // the weights of this row, as fp16 pairs in the order of the tile's columns
+        uint32_t packed[64];
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+          __syncwarp();  // the warp is done with the previous chunk's terms
+          wobs[lane] = make_float2(ny, nl);
+          __syncwarp();
+          if (c < 3) {
+            const int64_t io = ib + (c + 1) * 32 + lane;
+            ny = a.ybar[io];
+            nl = (io < a.N) ? a.lse2[io] : INFINITY;
+          }
+          float v[32];
+          tmem_ld32(lane_addr + (uint32_t)(b * 128 + c * 32), v);
+          tmem_ld_wait();
+#pragma unroll
+          for (int e = 0; e < 32; e += 2) {
+            float w2[2];
+#pragma unroll
+            for (int hh = 0; hh < 2; ++hh) {
+              const float2 yl = wobs[e + hh];
+              const float ybi = yl.x;
+              const float dd = ybi - cm;
+              const float val = fmaf(v[e + hh], a2, cb - yl.y) - c2 * dd * dd;
+              const float w = exp2f(val) * W_SCALE;
+              w2[hh] = __half2float(__float2half_rn(w));
+              cacc += w2[hh];
+              zacc = fmaf(w2[hh], ybi, zacc);
+            }
+            const __half2 pv = __floats2half2_rn(w2[0], w2[1]);
+            packed[c * 16 + (e >> 1)] = *reinterpret_cast<const uint32_t*>(&pv);
+          }
+        }
+        drained(&sempty[b]);  // the logits are no longer needed
+        ok = __all_sync(0xffffffffu, mbar_wait_cluster(&mfull[mr % MBOX_DEPTH],
+                                                       (mr / MBOX_DEPTH) & 1, abort, wlim));
+        if (!ok) break;
+        const uint32_t* mrow = mbox + (mr % MBOX_DEPTH) * P2P_MAX_G;
+        const int own = (int)mrow[pr];
+        uint8_t* prow = smem + own * SLOT + row * 128;
+#pragma unroll
+        for (int col16 = 0; col16 < 16; ++col16) {  // 16-byte units along the observations
+          const int kb2 = col16 >> 3, cc = col16 & 7;
+          *reinterpret_cast<uint4*>(prow + kb2 * 16384 + ((cc ^ (row & 7)) << 4)) =
+              make_uint4(packed[4 * col16], packed[4 * col16 + 1], packed[4 * col16 + 2],
+                         packed[4 * col16 + 3]);
+        }
+        fence_proxy_async_smem();
+        mbar_arrive(wready);
+        bool sent_ok = true;
+        if (row == 0) {  // all 128 rows written: send the tile to the CTAs of this parity
+          sent_ok = mbar_wait(wready, mr & 1, abort, wlim);
+          if (sent_ok) {
+            const uint8_t* src = smem + own * SLOT;
+            for (int jq = 0; jq < G; ++jq) {
+              if (jq == pr) continue;
+              const uint32_t dcta = 2u * (uint32_t)jq + (uint32_t)h;
+              const int dst = (int)mrow[jq];
+              bulk_copy_to_peer(mapa(smem_u32(smem + dst * SLOT), dcta), src, 32768,
+                                mapa(smem_u32(&full[dst]), dcta));
+            }
+            bulk_commit();
+            bulk_wait_read0();
+            mbar_arrive(&full[own]);
+          }
+        }
+        ok = __all_sync(0xffffffffu, sent_ok);
+        if (!ok) break;
+        cacc_d += (double)cacc;
+        zacc_d += (double)zacc;
+        cacc = zacc = 0.f;
+        ++sc;
+        ++mr;
+      }
+      if (!ok) break;
+      if (cvalid) {
+        ok = __all_sync(0xffffffffu, mbar_wait_cluster(zfull, uc & 1, abort, wlim));
+        if (!ok) break;
+        tc_fence_after();
+        float* zrow = a.Zp + ((int64_t)split * a.Spad + s) * a.ldy;
+#pragma unroll 1
+        for (int c = 0; c < 8; ++c) {
+          float v[32];
+          tmem_ld32(lane_addr + (uint32_t)(256 + c * 32), v);
+          tmem_ld_wait();
+          const int p0 = chunk * 256 + c * 32;
+          if (p0 < a.ldy) {
+#pragma unroll
+            for (int e = 0; e < 32; e += 4)
+              if (p0 + e < a.ldy)
+                *reinterpret_cast<float4*>(zrow + p0 + e) =
+                    make_float4(v[e] * W_UNSCALE, v[e + 1] * W_UNSCALE, v[e + 2] * W_UNSCALE,
+                                v[e + 3] * W_UNSCALE);
+          }
+        }
+        drained(zempty);
+        ++uc;
+      }
+      if (cgrp == 0) {
+        const int64_t part = (int64_t)split * G + pr;
+        a.cp[part * a.Spad + s] = (float)(cacc_d * W_UNSCALE);
+        a.zbp[part * a.Spad + s] = (float)(zacc_d * W_UNSCALE);
+      }
+    }
+    if (!ok) raise_timeout(abort, status);
+    if (row == 0) bulk_wait0();  // the tiles sent to the peers have landed
+  }
+  __syncthreads();
+  // neither CTA of a pair releases the pair's Tensor Memory before the even CTA's MMAs
+  // are done and both CTAs' epilogues have left it
+  cluster_sync_all();
+  if (warp == 1) {
+    tc_fence_after();
+    tmem_dealloc_pair(tbase, 512);
+  }
+  cluster_sync_all();  // no CTA leaves while a peer may still copy into it
+}
+
+constexpr size_t P2P_SMEM = P2R_SMEM;
+
 // ---- interleaved form
 constexpr uint32_t MBOX_TAG_MASK = 0x0FFFFFFFu;  // entry = tag << 4 | slot, tag = use + 1
 
@@ -1974,6 +2502,7 @@ cudaError_t set_p2_attrs() {
   return set_smem(k_p2_tc<NPROD, false>, P2_SMEM);
 }
 cudaError_t set_p2comp_attrs() { return set_smem(k_p2_tc<3, true>, P2_SMEM_COMP); }
+cudaError_t set_p2p_attrs() { return set_smem(k_p2p_tc<3>, P2P_SMEM); }
 
 // The cluster form for clusters of G: the ring form up to P2R_MAX_G, the interleaved
 // form above.
@@ -1998,6 +2527,7 @@ void p2c_form(int G, const void** fn, int* threads, size_t* smem) {
 int choose_p2_cluster(int chunks, int l2, int64_t n_iblk, int prec, int num_sms);
 template <int NPROD>
 int max_clusters_p2(int G, int num_sms);
+int max_clusters_pair(int G, int num_sms);
 
 // Whether a bf16x3 context takes the compensated M-step (hi + lo fp16 operands for
 // Z' = W^T Y').  With single fp16 operands the rounding of the weights and of Y'
@@ -2018,9 +2548,22 @@ bool tc_comp_mstep(const Geom& g, int prec, unsigned flags) {
   return (double)g.N < n_min;
 }
 
-// Pass-2 launch group of a context: its cluster size, or 0 for the compensated
-// per-chunk kernel.
-int tc_p2_key(const srmra_ctx* c) { return c->plan.p2_comp ? 0 : c->plan.p2_gc; }
+// Pass-2 launch group of a context: its cluster size, 0 for the compensated per-chunk
+// kernel, P2_KEY_PAIR + G for the pair form with G pairs.
+int tc_p2_key(const srmra_ctx* c) {
+  if (c->plan.p2_comp) return 0;
+  return c->plan.p2_pair ? P2_KEY_PAIR + c->plan.p2_gc : c->plan.p2_gc;
+}
+
+// Whether a context takes the pair form of pass 2: split-bf16 operands with the single
+// fp16 M-step, clusters allowed, up to four 256-pixel chunks (one per pair), and
+// SRMRA_FLAG_P2_PAIR set.
+bool tc_pair_form(const Geom& g, int prec, unsigned flags, bool comp) {
+  if (prec != SRMRA_BF16X3 || comp || (flags & SRMRA_FLAG_NO_CLUSTER)) return false;
+  if (!(flags & SRMRA_FLAG_P2_PAIR)) return false;
+  const int chunks = (g.l2 + 255) / 256;
+  return chunks >= 1 && chunks <= P2P_MAX_G;
+}
 
 // Work decomposition of the tensor-core passes.  s1 multiplies the number of shift
 // groups of pass 1 and s2 the number of observation ranges of pass 2: finer units
@@ -2058,16 +2601,21 @@ void plan_tc(srmra_ctx* c, int s1, int s2) {
   const int chunks = (int)ceil_div(g.l2, 256);
   const int n_iblk = (int)(g.Npad / 128);
   // cluster size of pass 2: CTAs that share each weight tile, one pixel chunk each
-  const int G = (c->no_cluster || p.p2_comp) ? 1
-                                             : choose_p2_cluster(chunks, g.l2, n_iblk, c->prec, sms);
+  const int G = p.p2_pair ? chunks
+                          : (c->no_cluster || p.p2_comp)
+                                ? 1
+                                : choose_p2_cluster(chunks, g.l2, n_iblk, c->prec, sms);
   // observation splits of pass 2: each split adds a partial Z' (Spad x l2 float32) that
   // pass 2 writes and the finalize reads, so take the split count that minimises the
   // busiest cluster's block-rounds plus the partials' cost in the same units (a partial
   // of 4096 x 1024 floats measured about 1.4 block-rounds)
   const int ncg = (int)ceil_div(chunks, G);
-  const int64_t slots2 = G > 1 ? (int64_t)(c->prec == SRMRA_BF16X3 ? max_clusters_p2<3>(G, sms)
-                                                                   : max_clusters_p2<1>(G, sms))
-                               : (int64_t)sms;
+  const int64_t slots2 = p.p2_pair ? (int64_t)std::max(1, max_clusters_pair(G, sms))
+                         : G > 1 ? (int64_t)(c->prec == SRMRA_BF16X3 ? max_clusters_p2<3>(G, sms)
+                                                                     : max_clusters_p2<1>(G, sms))
+                                 : (int64_t)sms;
+  // work units per observation range: (shift tile, chunk group), or pairs of shift tiles
+  const int64_t st_units = p.p2_pair ? n_st2 / 2 : n_st2;
   const double part_cost = 1.4 * (double)g.Spad * (double)g.ldy / (4096.0 * 1024.0);
   // no more splits than about four units per SM would give (bounds the partial buffers)
   const int64_t per_split_old = (int64_t)n_st2 * chunks;
@@ -2090,7 +2638,7 @@ void plan_tc(srmra_ctx* c, int s1, int s2) {
        ++cand) {
     const int64_t per = ceil_div(n_iblk, cand);
     if (cand > 1 && ceil_div(n_iblk, per) != cand) continue;
-    const int64_t units = (int64_t)n_st2 * ncg * cand;
+    const int64_t units = st_units * ncg * cand;
     const double cost = (double)ceil_div(units, slots2) * (double)per + part_cost * cand;
     if (best_ns == 0.0 || cost < best_ns) {
       best_ns = cost;
@@ -2125,6 +2673,7 @@ cudaError_t tc_set_attributes(int prec) {
     if (e == cudaSuccess) e = set_smem(k_p2_tc<3, false>, P2_SMEM);
     if (e == cudaSuccess) e = set_p2comp_attrs();
     if (e == cudaSuccess) e = set_p2c_attrs<3>();
+    if (e == cudaSuccess) e = set_p2p_attrs();
   } else {
     e = set_smem(k_p1_tc<1, 256>, P1_SMEM);
     if (e == cudaSuccess) e = set_smem(k_p1_tc<1, 128>, P1_SMEM);
@@ -2156,7 +2705,11 @@ cudaError_t prep_obs_tc(srmra_ctx* c) {
   if (ok && c->prec == SRMRA_BF16X3)
     ok = make_map(&c->tmYl128, c->Yl, g.ldk, g.Npad, g.ldk, 128) &&
          make_map(&c->tmAl128, c->Al, g.ldk, g.Spad, g.ldk, 128) &&
-         make_map(&c->tmAl256, c->Al, g.ldk, g.Spad, g.ldk, 256);
+         make_map(&c->tmAl256, c->Al, g.ldk, g.Spad, g.ldk, 256) &&
+         make_map(&c->tmY64, c->Yh, g.ldk, g.Npad, g.ldk, 64) &&
+         make_map(&c->tmYl64, c->Yl, g.ldk, g.Npad, g.ldk, 64) &&
+         make_map(&c->tmYT128, c->YTf, g.Npad, g.l2, g.Npad, 128,
+                  CU_TENSOR_MAP_DATA_TYPE_FLOAT16);
   if (!ok) return cudaErrorInvalidValue;
   return tc_upload_inst(c);
 }
@@ -2185,6 +2738,9 @@ void fill_inst(const srmra_ctx* c, TcInst* I) {
   I->tmAl128 = (c->prec == SRMRA_BF16X3) ? c->tmAl128 : c->tmA128;
   I->tmYT = c->tmYT;
   I->tmYTl = c->plan.p2_comp ? c->tmYTl : c->tmYT;
+  I->tmY64 = c->tmY64;
+  I->tmYl64 = c->tmYl64;
+  I->tmYT128 = c->tmYT128;
   TcP1Args& a = I->p1;
   a.nk = (int)ceil_div(g.l2, 64);
   a.n_stiles = g.Spad / p.p1_bn;
@@ -2211,7 +2767,9 @@ void fill_inst(const srmra_ctx* c, TcInst* I) {
   b.iblk_per_split = p.p2_iblk_per_split;
   // work units of pass 2: (shift tile, chunk group, observation range); a chunk group is
   // one pixel chunk for the per-chunk kernel and G chunks for the cluster kernel
-  b.n_units = (int64_t)b.n_stiles * p.p2_chunk_groups * p.p2_nsplit;
+  // (the pair form takes two shift tiles per unit, one per CTA of a pair)
+  b.n_units = (int64_t)(p.p2_pair ? b.n_stiles / 2 : b.n_stiles) * p.p2_chunk_groups *
+              p.p2_nsplit;
   b.N = g.N;
   b.Spad = g.Spad;
   b.ldy = g.ldy;
@@ -2306,6 +2864,66 @@ cudaError_t launch_cluster_p2(int G, const TcInst* d_insts, const int64_t* d_ust
   return cudaLaunchKernelEx(&cfg, k_p2i_tc<NPROD>, d_insts, d_ustart, n, G, status);
 }
 
+// Co-resident clusters of G pairs (2G CTAs) of the pair-form kernel (queried once per
+// device and G); 0 if the GPU cannot place one.
+int max_clusters_pair_impl(int G, int num_sms) {
+  static std::mutex mu;
+  static std::map<std::pair<int, int>, int> cache;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) dev = -1;
+  std::lock_guard<std::mutex> lock(mu);
+  {
+    auto hit = cache.find({dev, G});
+    if (hit != cache.end()) return hit->second;
+  }
+  cudaGetLastError();
+  set_p2p_attrs();
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)(2 * G * (num_sms / (2 * G))), 1, 1);
+  cfg.blockDim = dim3((unsigned)TC_THREADS, 1, 1);
+  cfg.dynamicSmemBytes = P2P_SMEM;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = (unsigned)(2 * G);
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  int n = 0;
+  if (cudaOccupancyMaxActiveClusters(&n, (const void*)k_p2p_tc<3>, &cfg) != cudaSuccess) {
+    cudaGetLastError();
+    n = 0;
+  }
+  cache[{dev, G}] = n > 0 ? n : 0;
+  return n > 0 ? n : 0;
+}
+
+cudaError_t launch_pair_p2(int G, const TcInst* d_insts, const int64_t* d_ustart, int n,
+                           int64_t total, int* status, cudaStream_t stream, int num_sms) {
+  {
+    cudaError_t e = once_per_device(ATTR_TC_P2P, set_p2p_attrs);
+    if (e != cudaSuccess) return e;
+  }
+  if (G < 1 || G > P2P_MAX_G) return cudaErrorInvalidValue;
+  int ncl = max_clusters_pair_impl(G, num_sms);
+  if (ncl < 1) return cudaErrorInvalidConfiguration;
+  if (total < ncl) ncl = (int)total;
+  if (ncl < 1) return cudaSuccess;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)(2 * G * ncl), 1, 1);
+  cfg.blockDim = dim3((unsigned)TC_THREADS, 1, 1);
+  cfg.dynamicSmemBytes = P2P_SMEM;
+  cfg.stream = stream;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeClusterDimension;
+  at[0].val.clusterDim.x = (unsigned)(2 * G);
+  at[0].val.clusterDim.y = 1;
+  at[0].val.clusterDim.z = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, k_p2p_tc<3>, d_insts, d_ustart, n, G, status);
+}
+
 template <int NPROD>
 cudaError_t launch_group(int pass, int bn, const TcInst* d_insts, const int64_t* d_ustart, int n,
                          int64_t total, int* status, cudaStream_t stream, int num_sms) {
@@ -2336,6 +2954,7 @@ int max_clusters_p2(int G, int num_sms) {
 }
 template int max_clusters_p2<1>(int, int);
 template int max_clusters_p2<3>(int, int);
+int max_clusters_pair(int G, int num_sms) { return max_clusters_pair_impl(G, num_sms); }
 
 // Cluster size of pass 2 for `chunks` 256-pixel chunks of Z' (l2 pixels, n_iblk blocks of
 // 128 observations).  Up to 4 chunks one cluster covers them all (G = chunks, ring form).
@@ -2382,6 +3001,10 @@ cudaError_t tc_launch_group_p2(int G, int prec, const void* d_insts, const int64
                                int n, int64_t total, int* status, cudaStream_t stream,
                                int num_sms) {
   const TcInst* insts = (const TcInst*)d_insts;
+  if (G > P2_KEY_PAIR) {  // the pair form (bf16x3 only)
+    if (prec != SRMRA_BF16X3) return cudaErrorInvalidValue;
+    return launch_pair_p2(G - P2_KEY_PAIR, insts, d_ustart, n, total, status, stream, num_sms);
+  }
   if (G == 0) {  // the per-chunk kernel with the compensated M-step (bf16x3 only)
     if (prec != SRMRA_BF16X3) return cudaErrorInvalidValue;
     const unsigned grid = (unsigned)(total < num_sms ? total : num_sms);

@@ -45,6 +45,7 @@ enum : int {
   ATTR_TC_P2C = 9,    // + NPROD
   ATTR_TC_P2COMP = 13,
   ATTR_TC_P1N = 14,   // + NPROD: the 128-shift pass-1 tiles
+  ATTR_TC_P2P = 18,   // the pair form of pass 2
 };
 cudaError_t once_per_device(int key, cudaError_t (*set)());
 
@@ -100,6 +101,7 @@ struct Plan {
   int fft_p1_obs_per_block = 1;  // FFT form, pass 1 (per-observation outputs only)
   int fft_p1_blocks = 1;
   bool p2_comp = false;     // tensor-core pass 2 with the compensated M-step (bf16x3)
+  bool p2_pair = false;     // tensor-core pass 2 in the pair form (2-CTA MMAs, bf16x3)
   int cap_p1_groups = 0;    // capacity of the pass-1 partial buffers (0 = unbounded)
   int cap_nsplit = 0;       // capacity of the pass-2 partial buffers (0 = unbounded)
 };
@@ -127,6 +129,7 @@ struct srmra_ctx {
   __nv_bfloat16* Ah = nullptr;   // [Spad][ldk] centred templates, bf16 hi
   __nv_bfloat16* Al = nullptr;   // [Spad][ldk] bf16 lo (split form only)
   CUtensorMap tmY128, tmYl128, tmYT, tmYTl, tmA128, tmAl128, tmA256, tmAl256;
+  CUtensorMap tmY64, tmYl64, tmYT128;  // pair form of pass 2 (split form only)
   void* d_inst = nullptr;           // this context's launch descriptor (tensor-core form)
   int64_t* d_ustart = nullptr;      // [4] unit prefix sums of pass 1 and pass 2
   int64_t h_ustart[4] = {0, 0, 0, 0};
@@ -209,6 +212,7 @@ int fin_t_splits(const Geom& g, int num_sms);
 // ---- k_tc.cu (tensor-core forms)
 bool tc_comp_mstep(const Geom& g, int prec, unsigned flags);
 int tc_p2_key(const srmra_ctx* c);  // pass-2 launch group (cluster size; 0 = compensated)
+bool tc_pair_form(const Geom& g, int prec, unsigned flags, bool comp);
 void plan_tc(srmra_ctx* c, int s1 = 1, int s2 = 1);
 cudaError_t tc_replan(srmra_ctx* c, int s1, int s2, int p1_bn);
 cudaError_t tc_set_attributes(int prec);

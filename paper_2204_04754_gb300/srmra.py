@@ -30,6 +30,7 @@ SRMRA_FLAG_NO_CLUSTER = 2
 SRMRA_FLAG_MSTEP_COMP = 4
 SRMRA_FLAG_MSTEP_FP16 = 8
 SRMRA_FLAG_P1_TILE128 = 16
+SRMRA_FLAG_P2_PAIR = 32
 
 
 class srmra_params(Structure):
@@ -194,7 +195,7 @@ def srmra_launch_count(ctx: int) -> int:
 
 
 P2_FORMS = {0: "per_chunk", 1: "ring", 2: "interleaved", 3: "fp32", 4: "fft",
-            5: "per_chunk_comp"}
+            5: "per_chunk_comp", 6: "pair"}
 
 
 def srmra_set_wait_limit(ctx: int, limit_ns: int, test_hook: int = 0) -> None:

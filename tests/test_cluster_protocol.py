@@ -28,7 +28,13 @@ Ring form (clusters up to 4).  Every weight tile, the owner's included, goes thr
 and announces it on a counting barrier per mailbox row, and an owner sends its tile
 once all G reservations are in.  The model checks the kernel's order (weight slots one
 block ahead of their Y'^T tiles), and that it catches the order that reserves all weight
-slots of a round first (a deadlock) and a mailbox with fewer rows than ring slots."""
+slots of a round first (a deadlock) and a mailbox with fewer rows than ring slots.
+
+Pair form (clusters of G pairs of CTAs issuing 2-CTA MMAs).  The ring protocol among
+the CTAs of one parity, with one Y'^T fill per weight tile (128 observations x 128
+pixels): all weight slots of a round are reserved first, and the MMA thread takes each
+tile's Y'^T fill right after the tile.  The model checks that order with ring-sized and
+small numbers of k-blocks, and that it deadlocks with two fills per tile."""
 import random
 
 import pytest
@@ -409,6 +415,135 @@ def run_ring(G, units, order, seed=0, nk=16, cvalid=None, mbox=MBOX):
         ro[1] = next(ro[0], None)
 
 
+def run_pair(G, units, seed=0, nk=16, cvalid=None, mbox=MBOX, t_per_w=1):
+    """The pair form (clusters of G pairs): each CTA's ring, seen from one parity (the
+    two CTAs of a pair fill the same slots in step, and the even CTA's MMA thread takes a
+    fill once it has landed in both, so one parity's CTAs carry the whole dependency
+    structure).  Per round: the logit fills of the pair's block (two template fills and
+    one observation fill per two k-blocks), then for round j - 1 a slot for every weight
+    tile (announced to its owner, which sends once all G reservations are in) followed by
+    t_per_w Y'^T fills per tile; the MMA thread takes weight tile i, then its Y'^T fills,
+    out of the ring order.  Returns True when every role finishes, False on a deadlock."""
+    rnd = random.Random(seed)
+    st = [dict(free=[0] * RING_SLOTS, full=[0] * RING_SLOTS, sfull=[0, 0], sempty=[0, 0], zfull=0,
+               zempty=0, mfull=[0] * mbox, mbox=[[None] * G for _ in range(mbox)],
+               rounds=[[None] * G for _ in range(mbox)])
+          for _ in range(G)]
+    valid = cvalid or [True] * G
+
+    def logit_fills():
+        return sum(min(2, nk - kb) + 1 for kb in range(0, nk, 2))
+
+    def producer(r):
+        it = 0
+        sent = [0] * G
+
+        def reserve():
+            nonlocal it
+            s, need = it % RING_SLOTS, it // RING_SLOTS
+            yield lambda: st[r]["free"][s] >= need
+            it += 1
+            return s
+
+        for nb in units:
+            rounds = -(-nb // G)
+            for j in range(rounds + 1):
+                nq = min(G, nb - j * G) if j < rounds else 0
+                if r < nq:
+                    for _ in range(logit_fills()):
+                        s = yield from reserve()
+                        st[r]["full"][s] += 1
+                nqp = min(G, nb - (j - 1) * G) if j >= 1 else 0
+                for kq in range(nqp):
+                    s = yield from reserve()
+                    row = sent[kq] % mbox
+                    st[kq]["mbox"][row][r] = s
+                    st[kq]["rounds"][row][r] = sent[kq]
+                    st[kq]["mfull"][row] += 1
+                    sent[kq] += 1
+                if valid[r]:
+                    for _ in range(nqp * t_per_w):
+                        s = yield from reserve()
+                        st[r]["full"][s] += 1
+
+    def mma(r):
+        it = sc = uc = 0
+
+        def take(k):
+            s, need = k % RING_SLOTS, k // RING_SLOTS + 1
+            yield lambda: st[r]["full"][s] >= need
+            return s
+
+        for nb in units:
+            rounds = -(-nb // G)
+            first = True
+            for j in range(rounds + 1):
+                nq = min(G, nb - j * G) if j < rounds else 0
+                if r < nq:
+                    b, need = sc & 1, sc >> 1
+                    yield lambda b=b, need=need: st[r]["sempty"][b] >= need
+                    for _ in range(logit_fills()):
+                        s = yield from take(it)
+                        it += 1
+                        st[r]["free"][s] += 1
+                    st[r]["sfull"][b] += 1
+                    sc += 1
+                nqp = min(G, nb - (j - 1) * G) if j >= 1 else 0
+                base = it
+                it += nqp + (nqp * t_per_w if valid[r] else 0)
+                for i in range(nqp):
+                    sw = yield from take(base + i)
+                    if valid[r]:
+                        if first:
+                            yield lambda u=uc: st[r]["zempty"] >= u
+                        for t in range(t_per_w):
+                            s = yield from take(base + nqp + i * t_per_w + t)
+                            st[r]["free"][s] += 1
+                        first = False
+                    st[r]["free"][sw] += 1
+            if valid[r]:
+                st[r]["zfull"] += 1
+                uc += 1
+
+    def epilogue(r):
+        sc = mr = uc = 0
+        for nb in units:
+            for r0 in range(0, nb, G):
+                if r >= min(G, nb - r0):
+                    continue
+                b, need = sc & 1, (sc >> 1) + 1
+                yield lambda b=b, need=need: st[r]["sfull"][b] >= need
+                st[r]["sempty"][b] += 1
+                row, mneed = mr % mbox, G * (mr // mbox + 1)
+                yield lambda row=row, mneed=mneed: st[r]["mfull"][row] >= mneed
+                if st[r]["rounds"][row] != [mr] * G:
+                    raise MailboxRace((r, mr, st[r]["rounds"][row]))
+                slots = list(st[r]["mbox"][row])
+                for j in range(G):
+                    st[j]["full"][slots[j]] += 1
+                sc += 1
+                mr += 1
+            if valid[r]:
+                yield lambda u=uc: st[r]["zfull"] >= u + 1
+                st[r]["zempty"] += 1
+                uc += 1
+
+    roles = []
+    for r in range(G):
+        for f in (producer, mma, epilogue):
+            g = f(r)
+            roles.append([g, next(g, None)])
+    while True:
+        live = [ro for ro in roles if ro[1] is not None]
+        if not live:
+            return True
+        ready = [ro for ro in live if ro[1]()]
+        if not ready:
+            return False
+        ro = rnd.choice(ready)
+        ro[1] = next(ro[0], None)
+
+
 UNITS = [[24] * 4, [23] * 4, [24, 23, 24, 23], [6], [2], [5, 3], [1], [7, 1, 9], [13] * 3,
          [16] * 2, [40], [9, 7], [1] * 10, [2, 1, 1, 1, 1, 1, 1, 3]]
 
@@ -496,3 +631,20 @@ def test_ring_model_catches_a_mailbox_shallower_than_the_ring():
 def test_ring_model_catches_the_weights_first_order():
     assert not run_ring(4, [6], "weights_first")
     assert not run_ring(4, [24] * 2, "weights_first", seed=1)
+
+
+@pytest.mark.parametrize("G", [1, 2, 3, 4])
+def test_pair_form_order_never_deadlocks(G):
+    for units in UNITS:
+        for cvalid in cvalid_patterns(G)[:4]:
+            for nk in (16, 9, 2, 1):
+                for seed in range(2):
+                    assert run_pair(G, units, seed=seed, cvalid=cvalid, nk=nk), \
+                        (units, cvalid, nk)
+
+
+def test_pair_model_catches_too_many_fills_per_weight_tile():
+    """Reserving all weight slots of a round first is safe only while each tile's Y'^T
+    fills lie within the ring: with two 64-observation fills per tile (the single-CTA
+    layout) the last tile's fills wait for slots that only its own products release."""
+    assert not run_pair(4, [24] * 2, t_per_w=2, nk=8)

@@ -49,10 +49,12 @@ def oracle_step_ok(s, p, x, r1, r2, tol):
 
 # (L, K, N, sigma, flags, pass-2 form): the ring cluster form (4 chunks, clusters of 4),
 # the interleaved cluster form (9 chunks, one cluster of 9), the per-chunk kernel and
-# its compensated M-step (flags: 8 keeps single fp16 M-step operands, 2 turns the
-# clusters off, 4 forces the compensated M-step)
+# its compensated M-step, the pair form (4 pairs, clusters of 8) (flags: 8 keeps single
+# fp16 M-step operands, 2 turns the clusters off, 4 forces the compensated M-step, 32
+# asks for the pair form)
 CASES = [(64, 2, 700, 0.3, 8, "ring"), (96, 2, 1000, 0.5, 8, "interleaved"),
-         (64, 2, 700, 0.3, 2 | 8, "per_chunk"), (64, 2, 700, 0.3, 4, "per_chunk_comp")]
+         (64, 2, 700, 0.3, 2 | 8, "per_chunk"), (64, 2, 700, 0.3, 4, "per_chunk_comp"),
+         (64, 2, 700, 0.3, 32 | 8, "pair")]
 
 
 @pytest.mark.parametrize("L,K,N,sigma,flags,form", CASES)

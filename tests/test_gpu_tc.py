@@ -110,6 +110,34 @@ def test_em_step_parity_bf16x3_forms(S, shape, flags, form):
     assert w["x"] < tol and w["rho"] < tol and w["ll"] < tol and w["lse"] < tol
 
 
+# the pair form (SRMRA_FLAG_P2_PAIR) with 1, 2, 3 and 4 pairs per cluster; odd numbers
+# of k-blocks (l^2 = 576: 9; l^2 = 16: 1) and a ragged shift tile (L = 12, K = 3)
+PAIRS = [(32, 2, 1000, 0.3), (12, 3, 333, 0.4), (40, 2, 1500, 0.5), (48, 2, 2000, 0.4),
+         (64, 2, 2500, 0.3), (96, 3, 3000, 0.2)]
+
+
+@pytest.mark.parametrize("L,K,N,sigma", PAIRS)
+def test_pair_form_parity(S, L, K, N, sigma):
+    """Pass 2 with 2-CTA MMAs: the oracle's iteration within the mixed form's 1e-4, and
+    the single-CTA cluster (or per-chunk) form's within float32 rounding of the same
+    products."""
+    p = synth.make_problem(L, K, N, sigma, seed=synth.seed_for(3, 700 + L))
+    w = one_step(S, p, "bf16x3", flags=S.SRMRA_FLAG_P2_PAIR, form="pair")
+    tol = TOL["bf16x3"]
+    assert w["x"] < tol and w["rho"] < tol and w["ll"] < tol and w["lse"] < tol
+    out = []
+    for flags in (0, S.SRMRA_FLAG_P2_PAIR):
+        s = S.Solver(p.L, p.K, p.sigma, p.y, prec="bf16x3", x0=p.x0, rho1=p.rho1_0,
+                     rho2=p.rho2_0, flags=flags)
+        s.em_iter(2)
+        out.append(s.state())
+        s.close()
+    (x0, r10, r20, _, _), (x1, r11, r21, _, _) = out
+    d = (rel(x1, x0), rel(r11, r10), rel(r21, r20))
+    print("pair vs single-CTA form", L, K, N, d)
+    assert max(d) < 1e-5, d
+
+
 @pytest.mark.parametrize("L,K,N,sigma", [(16, 2, 500, 0.1), (12, 3, 333, 0.4), (64, 2, 700, 0.3),
                                          (96, 3, 1500, 0.2), (32, 4, 900, 1.0)])
 @pytest.mark.parametrize("prec", ["bf16x3", "bf16"])
