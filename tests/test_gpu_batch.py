@@ -122,6 +122,36 @@ def test_batch_pass1_tile_widths(S):
         s.close()
 
 
+def test_batch_with_pair_form_contexts(S):
+    """Contexts that ask for the pair form of pass 2 (SRMRA_FLAG_P2_PAIR; it applies to
+    bf16x3 problems of up to four pixel chunks without the compensated M-step) batched
+    with contexts of the other forms: one grouped launch per form, results identical to
+    solving each alone."""
+    probs = problems()
+
+    def mk(p):
+        return S.Solver(p.L, p.K, p.sigma, p.y, prec="bf16x3", x0=p.x0, rho1=p.rho1_0,
+                        rho2=p.rho2_0, flags=S.SRMRA_FLAG_P2_PAIR)
+    alone = []
+    for p in probs:
+        s = mk(p)
+        s.solve(3, 1)
+        alone.append(s.state())
+        s.close()
+    ss = [mk(p) for p in probs]
+    forms = [s.plan()["p2_form"] for s in ss]
+    assert forms.count("pair") == 5 and "interleaved" in forms, forms
+    b = S.Batch(ss, autotune=False)
+    b.solve(3, 1)
+    for k, s in enumerate(ss):
+        x, r1, _, _, t = s.state()
+        assert x.tobytes() == alone[k][0].tobytes() and r1.tobytes() == alone[k][1].tobytes()
+        assert t == 3
+    b.close()
+    for s in ss:
+        s.close()
+
+
 def test_batch_rejects_mixed_precision_and_duplicates(S):
     probs = problems()[:2]
     a = solver(S, probs[0], "bf16x3")
