@@ -1245,21 +1245,23 @@ static_assert(P2R_SMEM <= 232448, "exceeds the shared memory of one CTA");
 //   loading its own templates and 64 of the block's observations;
 // - Z' of a 256-pixel chunk is a 256 x 256 product per k-step, each CTA loading 128 of
 //   the chunk's pixels of Y'^T;
-// so each SM reads about a quarter fewer operand bytes from shared memory per flop than
-// with one CTA's 128 x 128 and 128 x 256 products (the tensor-core pass 2 is bound by
-// shared-memory bandwidth).  The G pairs of a cluster share their weight tiles as in
-// the ring form, among the CTAs of the same parity (the same shift tile): every weight
-// tile and Y'^T tile goes through the 7-slot ring, the slots of a round's weight tiles
-// are reserved first (each tile's Y'^T fill lies nqp <= 4 places after its slot, so no
-// fill waits for a slot that only its own products release), and the owner sends its
-// tile once all G reservations are in.  Both CTAs of a pair run the same sequence of
-// fills, so a fill has the same slot in both.  The odd CTA's TMA loads complete on the
-// even CTA's barrier (cta_group::2 loads), which expects the bytes of both; a weight
-// tile copied into a CTA completes on that CTA's barrier, and the odd CTA's MMA warp
-// relays each of its weight fills to the even CTA (pfull), whose MMA thread waits on
-// both before it reads the slot of both CTAs.  Each MMA completion is committed to the barriers of both CTAs,
-// and the odd CTA's epilogue warps report a drained accumulator to the even CTA (one
-// arrival per warp).
+// so each SM reads a quarter fewer operand bytes from shared memory per flop than with
+// one CTA's 128 x 128 and 128 x 256 products.  (Measured on GB300 this did not make the
+// tensor pipe busier per SM, and clusters of 8 CTAs fit on fewer SMs than clusters of
+// 4: the form is slower than the ring form and is used only on request,
+// SRMRA_FLAG_P2_PAIR.)  The G pairs of a cluster share their weight tiles as in the ring
+// form, among the CTAs of the same parity (the same shift tile): every weight tile and
+// Y'^T tile goes through the 7-slot ring, the slots of a round's weight tiles are
+// reserved first (each tile's Y'^T fill lies nqp <= 4 places after its slot, so no fill
+// waits for a slot that only its own products release), and the owner sends its tile
+// once all G reservations are in.  Both CTAs of a pair run the same sequence of fills,
+// so a fill has the same slot in both.  The odd CTA's TMA loads complete on the even
+// CTA's barrier (cta_group::2 loads), which expects the bytes of both; a weight tile
+// copied into a CTA completes on that CTA's barrier, and the odd CTA's MMA warp relays
+// each of its weight fills to the even CTA (pfull), whose MMA thread waits on both
+// before it reads the slot of both CTAs.  Each MMA completion is committed to the
+// barriers of both CTAs, and the odd CTA's epilogue warps report a drained accumulator
+// to the even CTA (one arrival per warp).
 constexpr int P2P_MAX_G = 4;  // pairs per cluster (clusters of up to 8 CTAs)
 constexpr int P2_KEY_PAIR = 32;  // pass-2 launch keys above it: the pair form
 // barriers: full, pfull, empty (ring), sfull, sempty, zfull, zempty, mfull (rows), drain,
@@ -1425,10 +1427,10 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
       if (!ok) raise_timeout(abort, status);
       {
         // the fills already issued land before the CTA exits, also when another role
-        // gave up and stopped consuming them (the odd CTA's TMA fills complete on the
-        // even CTA's barriers, whose producer waits for them; the final cluster barrier
-        // keeps the odd CTA until then)
-        // the odd CTA's barriers see only its weight fills, so their phases count those
+        // gave up and stopped consuming them.  The odd CTA's TMA fills complete on the
+        // even CTA's barriers, whose producer waits for them (the final cluster barrier
+        // keeps the odd CTA until then); the odd CTA's own barriers see only its weight
+        // fills, so their phases count those.
         const uint32_t lo = it > P2R_SLOTS ? it - P2R_SLOTS : 0;
         int zero = 0;
         for (uint32_t k = lo; k < it; ++k) {
@@ -1442,8 +1444,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     }
   } else if (warp == 1) {
     if (lane == 0) {
-      // even CTA: the pair's MMAs; odd CTA: relays its completed fills to the even CTA,
-      // in the order in which the even CTA's MMA thread waits for them
+      // even CTA: the pair's MMAs; odd CTA: relays its completed weight-tile fills to the
+      // even CTA, in the order in which the even CTA's MMA thread waits for them
       const bool issuer = h == 0;
       constexpr uint32_t idS = idesc_bf16_f32(256, 128);
       constexpr uint32_t idZ = idesc_f16_f32(256, 256);
