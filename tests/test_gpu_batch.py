@@ -150,6 +150,15 @@ def test_batch_with_pair_form_contexts(S):
     b.close()
     for s in ss:
         s.close()
+    # with the autotuner (other observation-range splits for the pair-form launches too)
+    ss = [mk(p) for p in probs]
+    b = S.Batch(ss, autotune=True)
+    b.solve(3, 1)
+    for k, s in enumerate(ss):
+        assert rel(s.state()[0], alone[k][0]) < 1e-5
+    b.close()
+    for s in ss:
+        s.close()
 
 
 def test_batch_rejects_mixed_precision_and_duplicates(S):
