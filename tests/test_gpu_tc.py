@@ -191,17 +191,20 @@ def test_precision_workload_subsample_bf16x3(S):
     assert w["x"] < TOL["bf16x3"] and w["rho"] < TOL["bf16x3"] and w["lse"] < TOL["bf16x3"]
 
 
-@pytest.mark.parametrize("prec", ["fp32", "bf16x3"])
+@pytest.mark.parametrize("prec", ["fp32", "bf16x3", "bf16x3-pair"])
 @pytest.mark.parametrize("name", ["precision_L96_K3_N5e4_s0.2", "precision_L96_K3_N5e4_s1.0"])
 def test_precision_workload_full_size(S, name, prec):
     """The largest single-GPU workload at full size (L = 96, K = 3, N = 5e4), both noise
     levels: one iteration against the FP64 oracle (its polyphase-FFT formulation, pinned
     to the dense definition; observation ranges on all host cores) element by element:
     x, rho1, rho2, LL and every lse_i, as plain relative errors, at the form's target
-    (1e-5 float32, 1e-4 bf16x3)."""
+    (1e-5 float32, 1e-4 bf16x3; bf16x3-pair: the opt-in 2-CTA pass 2)."""
     p = synth.workload_problem(name)
-    s = S.Solver(p.L, p.K, p.sigma, p.y, prec=prec, x0=p.x0, rho1=p.rho1_0,
-                 rho2=p.rho2_0)
+    flags = S.SRMRA_FLAG_P2_PAIR if prec.endswith("-pair") else 0
+    s = S.Solver(p.L, p.K, p.sigma, p.y, prec=prec.split("-")[0], x0=p.x0, rho1=p.rho1_0,
+                 rho2=p.rho2_0, flags=flags)
+    if flags:
+        assert s.plan()["p2_form"] == "pair"
     ll = s.em_iter(1)[0]
     lse, c = s.estep()
     x, r1, r2, _, _ = s.state()
@@ -212,7 +215,7 @@ def test_precision_workload_full_size(S, name, prec):
                ll=abs(ll - llo) / abs(llo),
                lse=float(np.max(np.abs(lse - aux["lse"]) / np.abs(aux["lse"]))))
     print(name, prec, err)
-    tol = {"fp32": 1e-5, "bf16x3": 1e-4}[prec]
+    tol = {"fp32": 1e-5, "bf16x3": 1e-4, "bf16x3-pair": 1e-4}[prec]
     assert all(v < tol for v in err.values()), err
     assert abs(lse.sum() - ll) < 1e-9 * abs(ll)
 
