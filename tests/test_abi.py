@@ -86,3 +86,18 @@ def test_no_cpu_fallback(lib):
 
 def test_version_string(lib):
     assert lib.srmra_version().startswith(b"srmra")
+
+
+def test_binding_constants_match_the_header():
+    """The flag values and pass-2 form codes of include/srmra.h and of the Python
+    binding agree, and the binding names every form the header defines."""
+    from paper_2204_04754_gb300 import srmra
+    txt = open(HEADER).read()
+    flags = dict(re.findall(r"^#define (SRMRA_FLAG_\w+) (\d+)u", txt, flags=re.M))
+    assert len(flags) >= 6
+    for name, v in flags.items():
+        assert getattr(srmra, name) == int(v), name
+    forms = {int(v): n for n, v in re.findall(r"^#define SRMRA_P2_(\w+) (\d+)", txt, flags=re.M)}
+    assert sorted(forms) == sorted(srmra.P2_FORMS), (forms, srmra.P2_FORMS)
+    for code, name in forms.items():
+        assert srmra.P2_FORMS[code] == name.lower(), (code, name)
