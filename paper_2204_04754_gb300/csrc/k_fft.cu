@@ -35,7 +35,13 @@ namespace {
 
 __constant__ float2 c_tw[32];  // e^{-2 pi i m / 64}, m < 32
 
-constexpr int FFT_WARPS = 8;      // warps per CTA of the two passes
+constexpr int FFT_WARPS = 8;      // warps per CTA of pass 1
+// warps per CTA of pass 2: each warp keeps the c and zb sums of its lag row in registers
+// and its G sum in shared memory, so more warps fit than with all three in shared memory
+template <int N>
+constexpr int p2_warps() {
+  return N == 32 ? 12 : 16;
+}
 constexpr int SPEC_WARPS = 4;     // warps per CTA of the spectra kernels
 
 constexpr int brev(int i, int n) {
@@ -267,29 +273,28 @@ __global__ void __launch_bounds__(32 * FFT_WARPS) k_fft_p1(FftPassArgs a, float*
 // over the block's observations in a fixed order (each warp in increasing i, then the
 // warps in order).
 template <int N>
-__global__ void __launch_bounds__(32 * FFT_WARPS) k_fft_p2(FftPassArgs a, float* __restrict__ cp,
+__global__ void __launch_bounds__(32 * p2_warps<N>(), 1) k_fft_p2(FftPassArgs a, float* __restrict__ cp,
                                                            float* __restrict__ zbp, int Spad,
                                                            float2* __restrict__ Gp) {
   extern __shared__ __align__(16) unsigned char fsm[];
+  constexpr int W = p2_warps<N>();
   float2* sX = (float2*)fsm;                              // [N*N]
   float2* tiles = sX + N * N;                             // [W][N*(N+1)]
-  float2* sG = tiles + FFT_WARPS * N * (N + 1);           // [W][N*N]
-  float* sCol = (float*)(sG + FFT_WARPS * N * N);         // [N*(N+1)]
-  float* sC = sCol + N * (N + 1);                         // [W][N*(N+1)]
-  float* sZ = sC + FFT_WARPS * N * (N + 1);               // [W][N*(N+1)]
+  float2* sG = tiles + W * N * (N + 1);                   // [W][N*N]
+  float* sCol = (float*)(sG + W * N * N);                 // [N*(N+1)]
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int r = blockIdx.y, b = blockIdx.x;
   float2* tile = tiles + warp * N * (N + 1);
   float2* g = sG + warp * N * N;
-  float* cw = sC + warp * N * (N + 1);
-  float* zw = sZ + warp * N * (N + 1);
+  float crow[N], zrow[N];  // c and zb of lag row t1 = lane, over this warp's observations
+#pragma unroll
+  for (int k = 0; k < N; ++k) crow[k] = zrow[k] = 0.f;
   for (int idx = lane; idx < N * N; idx += 32) g[idx] = make_float2(0.f, 0.f);
-  for (int idx = lane; idx < N * (N + 1); idx += 32) cw[idx] = zw[idx] = 0.f;
   float mr;
   stage_phase<N>(a, r, sX, sCol, mr);
   const int64_t i0 = (int64_t)b * a.B;
   const int64_t i1 = min(a.N, i0 + a.B);
-  for (int64_t i = i0 + warp; i < i1; i += FFT_WARPS) {
+  for (int64_t i = i0 + warp; i < i1; i += W) {
     float2 v[N];
     const float yb = a.ybar[i];
     const float dd = yb - mr;
@@ -299,8 +304,8 @@ __global__ void __launch_bounds__(32 * FFT_WARPS) k_fft_p2(FftPassArgs a, float*
 #pragma unroll
       for (int k = 0; k < N; ++k) {
         const float w = exp2f(v[k].x - ls);
-        cw[lane * (N + 1) + k] += w;
-        zw[lane * (N + 1) + k] = fmaf(w, yb, zw[lane * (N + 1) + k]);
+        crow[k] += w;
+        zrow[k] = fmaf(w, yb, zrow[k]);
         v[k] = make_float2(w, 0.f);
       }
     }
@@ -320,6 +325,15 @@ __global__ void __launch_bounds__(32 * FFT_WARPS) k_fft_p2(FftPassArgs a, float*
       }
     }
   }
+  // each warp's c and zb rows into its transpose tile (floats: c, then zb)
+  if (lane < N) {
+    float* cz = (float*)tile;
+#pragma unroll
+    for (int k = 0; k < N; ++k) {
+      cz[lane * (N + 1) + k] = crow[k];
+      cz[N * (N + 1) + lane * (N + 1) + k] = zrow[k];
+    }
+  }
   __syncthreads();
   // the warps' sums in order; c and zb go to the dense forms' per-shift partial layout
   const int r1 = r / a.K, r2 = r % a.K;
@@ -327,9 +341,10 @@ __global__ void __launch_bounds__(32 * FFT_WARPS) k_fft_p2(FftPassArgs a, float*
     const int t1 = idx / N, t2 = idx % N;
     float c = 0.f, z = 0.f;
     float2 gg = make_float2(0.f, 0.f);
-    for (int w = 0; w < FFT_WARPS; ++w) {
-      c += sC[w * N * (N + 1) + t1 * (N + 1) + t2];
-      z += sZ[w * N * (N + 1) + t1 * (N + 1) + t2];
+    for (int w = 0; w < W; ++w) {
+      const float* cz = (const float*)(tiles + w * N * (N + 1));
+      c += cz[t1 * (N + 1) + t2];
+      z += cz[N * (N + 1) + t1 * (N + 1) + t2];
       const float2 q = sG[w * N * N + idx];
       gg.x += q.x;
       gg.y += q.y;
@@ -382,8 +397,8 @@ constexpr size_t p1_smem_bytes() {
 
 template <int N>
 constexpr size_t p2_smem_bytes() {
-  return sizeof(float2) * (N * N + FFT_WARPS * N * (N + 1) + FFT_WARPS * N * N) +
-         sizeof(float) * (N * (N + 1) + 2 * FFT_WARPS * N * (N + 1));
+  return sizeof(float2) * (N * N + p2_warps<N>() * N * (N + 1) + p2_warps<N>() * N * N) +
+         sizeof(float) * (N * (N + 1));
 }
 
 cudaError_t upload_twiddles() {
@@ -449,7 +464,7 @@ void plan_fft(srmra_ctx* c) {
   p.fft_obs_per_block = (int)B;
   p.fft_blocks = (int)ceil_div(g.N, B);
   // pass 1 writes only per-observation results and fits two CTAs per SM: twice the CTAs
-  // (pass 2 keeps one per SM, bounded by its shared memory, and one partial per block)
+  // (pass 2 keeps one per SM, of 12 or 16 warps, and one partial per block)
   const int64_t B1 = round_up(ceil_div(g.N, 2 * (int64_t)nb), FFT_WARPS);
   p.fft_p1_obs_per_block = (int)B1;
   p.fft_p1_blocks = (int)ceil_div(g.N, B1);
@@ -512,13 +527,13 @@ cudaError_t launch_pass2_fft(srmra_ctx* c) {
   const dim3 grid((unsigned)c->plan.fft_blocks, (unsigned)(g.K * g.K));
   switch (g.l) {
     case 8:
-      k_fft_p2<8><<<grid, 32 * FFT_WARPS, p2_smem_bytes<8>(), c->stream>>>(a, c->cp, c->zbp, g.Spad, c->Gp);
+      k_fft_p2<8><<<grid, 32 * p2_warps<8>(), p2_smem_bytes<8>(), c->stream>>>(a, c->cp, c->zbp, g.Spad, c->Gp);
       break;
     case 16:
-      k_fft_p2<16><<<grid, 32 * FFT_WARPS, p2_smem_bytes<16>(), c->stream>>>(a, c->cp, c->zbp, g.Spad, c->Gp);
+      k_fft_p2<16><<<grid, 32 * p2_warps<16>(), p2_smem_bytes<16>(), c->stream>>>(a, c->cp, c->zbp, g.Spad, c->Gp);
       break;
     default:
-      k_fft_p2<32><<<grid, 32 * FFT_WARPS, p2_smem_bytes<32>(), c->stream>>>(a, c->cp, c->zbp, g.Spad, c->Gp);
+      k_fft_p2<32><<<grid, 32 * p2_warps<32>(), p2_smem_bytes<32>(), c->stream>>>(a, c->cp, c->zbp, g.Spad, c->Gp);
       break;
   }
   c->launches++;
