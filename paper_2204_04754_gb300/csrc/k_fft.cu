@@ -19,6 +19,13 @@
 // oracle beside that of the dense float32 form on the same inputs; the two agree in
 // size (tests/test_gpu_fft.py).
 //
+// Two observations per transform: the spectra Y^'_i . conj(X^'_r) of real images are
+// Hermitian, so one inverse FFT2 of P_i + i P_{i+1} gives corr_i in its real part and
+// corr_{i+1} in its imaginary part; likewise one forward FFT2 of the real weight maps
+// w_i + i w_{i+1} gives F, and W^_i = (F[k] + conj F[-k]) / 2, W^_{i+1} =
+// (F[k] - conj F[-k]) / (2i).  Both passes pair observations (2j, 2j + 1) the same way,
+// so pass 2's logits round exactly like pass 1's.
+//
 // FFTs: l x l with l in {8, 16, 32}.  One warp transforms one tile: lane j holds one
 // line (l complex values) in registers and runs a radix-2 decimation-in-time FFT on it;
 // the other direction is reached through a padded shared-memory transpose (row stride
@@ -200,27 +207,48 @@ __device__ __forceinline__ void stage_phase(const FftPassArgs& a, int r, float2*
   __syncthreads();
 }
 
+// Observations i and i + 1 (`two`: whether i + 1 exists) against the staged phase:
+// v[k] = l^2 (corr_i, corr_{i+1})[t1 = lane][t2 = k].
 template <int N>
-__device__ __forceinline__ void correlate(const FftPassArgs& a, int64_t i, const float2* sX,
-                                          float2* tile, int lane, float2 (&v)[N]) {
-  const float2* yf = a.Yf + i * (N * N);
-#pragma unroll
-  for (int k = 0; k < N; ++k)
-    v[k] = lane < N ? cmul_conj(yf[k * N + lane], sX[k * N + lane]) : make_float2(0.f, 0.f);
-  fft_reg<N, true>(v);  // column lane (over k1)
-  transpose<N, true>(v, tile, lane);
-  fft_reg<N, true>(v);  // row lane (over k2): v[k] = l^2 corr[t1 = lane][t2 = k]
-}
-
-// v[k].x = logit2 of lag (t1 = lane, t2 = k) of observation i and the staged phase.
-template <int N>
-__device__ __forceinline__ void phase_logits(const FftPassArgs& a, int64_t i, const float2* sX,
-                                             const float* sCol, float2* tile, int lane,
-                                             float cst, float2 (&v)[N]) {
-  correlate<N>(a, i, sX, tile, lane, v);
+__device__ __forceinline__ void correlate2(const FftPassArgs& a, int64_t i, bool two,
+                                           const float2* sX, float2* tile, int lane,
+                                           float2 (&v)[N]) {
+  // unconditional loads (the second spectrum weighted by 0 when absent), so that all
+  // of a lane's loads can be in flight at once
+  const float2* yf0 = a.Yf + i * (N * N);
+  const float2* yf1 = two ? yf0 + N * N : yf0;
+  const float s1 = two ? 1.f : 0.f;
   if (lane < N) {
 #pragma unroll
-    for (int k = 0; k < N; ++k) v[k].x = fmaf(v[k].x, a.a2n, sCol[lane * (N + 1) + k] + cst);
+    for (int k = 0; k < N; ++k) {
+      const float2 x = sX[k * N + lane];
+      const float2 p0 = cmul_conj(yf0[k * N + lane], x);
+      const float2 p1 = cmul_conj(yf1[k * N + lane], x);
+      v[k] = make_float2(p0.x - s1 * p1.y, p0.y + s1 * p1.x);  // P_i + i P_{i+1}
+    }
+  } else {
+#pragma unroll
+    for (int k = 0; k < N; ++k) v[k] = make_float2(0.f, 0.f);
+  }
+  fft_reg<N, true>(v);  // column lane (over k1)
+  transpose<N, true>(v, tile, lane);
+  fft_reg<N, true>(v);  // row lane (over k2)
+}
+
+// v[k] = (logit2 of observation i, of observation i + 1) at lag (t1 = lane, t2 = k) of the
+// staged phase; cst0, cst1 their -c2 (ybar - m_r)^2 terms.
+template <int N>
+__device__ __forceinline__ void phase_logits2(const FftPassArgs& a, int64_t i, bool two,
+                                              const float2* sX, const float* sCol, float2* tile,
+                                              int lane, float cst0, float cst1, float2 (&v)[N]) {
+  correlate2<N>(a, i, two, sX, tile, lane, v);
+  if (lane < N) {
+#pragma unroll
+    for (int k = 0; k < N; ++k) {
+      const float cb = sCol[lane * (N + 1) + k];
+      v[k].x = fmaf(v[k].x, a.a2n, cb + cst0);
+      v[k].y = fmaf(v[k].y, a.a2n, cb + cst1);
+    }
   }
 }
 
@@ -228,7 +256,7 @@ __device__ __forceinline__ void phase_logits(const FftPassArgs& a, int64_t i, co
 // Per (observation block, phase r): the running (max, sum of 2^(logit2 - max)) over the
 // l^2 lags of phase r, written as the partial of group r.
 template <int N>
-__global__ void __launch_bounds__(32 * FFT_WARPS) k_fft_p1(FftPassArgs a, float* __restrict__ pm,
+__global__ void __launch_bounds__(32 * FFT_WARPS, 2) k_fft_p1(FftPassArgs a, float* __restrict__ pm,
                                                            float* __restrict__ ps) {
   extern __shared__ __align__(16) unsigned char fsm[];
   float2* sX = (float2*)fsm;                         // [N*N]
@@ -238,31 +266,50 @@ __global__ void __launch_bounds__(32 * FFT_WARPS) k_fft_p1(FftPassArgs a, float*
   const int r = blockIdx.y;
   float mr;
   stage_phase<N>(a, r, sX, sCol, mr);
-  const int64_t i0 = (int64_t)blockIdx.x * a.B;
+  const int64_t i0 = (int64_t)blockIdx.x * a.B;  // even: B is a multiple of FFT_WARPS
   const int64_t i1 = min(a.N, i0 + a.B);
-  for (int64_t i = i0 + warp; i < i1; i += FFT_WARPS) {
+  for (int64_t i = i0 + 2 * warp; i < i1; i += 2 * FFT_WARPS) {  // pairs (i, i + 1)
+    const bool two = i + 1 < i1;
     float2 v[N];
-    const float dd = a.ybar[i] - mr;
-    const float cst = -a.c2 * dd * dd;
-    phase_logits<N>(a, i, sX, sCol, tiles + warp * N * (N + 1), lane, cst, v);
-    float mx = -INFINITY;
+    const float dd0 = a.ybar[i] - mr;
+    const float dd1 = two ? a.ybar[i + 1] - mr : 0.f;
+    phase_logits2<N>(a, i, two, sX, sCol, tiles + warp * N * (N + 1), lane, -a.c2 * dd0 * dd0,
+                     -a.c2 * dd1 * dd1, v);
+    float mx0 = -INFINITY, mx1 = -INFINITY;
     if (lane < N) {
 #pragma unroll
-      for (int k = 0; k < N; ++k) mx = fmaxf(mx, v[k].x);
+      for (int k = 0; k < N; ++k) {
+        mx0 = fmaxf(mx0, v[k].x);
+        mx1 = fmaxf(mx1, v[k].y);
+      }
     }
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
-    const float base = (mx == -INFINITY) ? 0.f : mx;
-    float sm = 0.f;
+    for (int o = 16; o > 0; o >>= 1) {
+      mx0 = fmaxf(mx0, __shfl_xor_sync(0xffffffffu, mx0, o));
+      mx1 = fmaxf(mx1, __shfl_xor_sync(0xffffffffu, mx1, o));
+    }
+    const float base0 = (mx0 == -INFINITY) ? 0.f : mx0;
+    const float base1 = (mx1 == -INFINITY) ? 0.f : mx1;
+    float sm0 = 0.f, sm1 = 0.f;
     if (lane < N) {
 #pragma unroll
-      for (int k = 0; k < N; ++k) sm += exp2f(v[k].x - base);
+      for (int k = 0; k < N; ++k) {
+        sm0 += exp2f(v[k].x - base0);
+        sm1 += exp2f(v[k].y - base1);
+      }
     }
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) sm += __shfl_xor_sync(0xffffffffu, sm, o);
+    for (int o = 16; o > 0; o >>= 1) {
+      sm0 += __shfl_xor_sync(0xffffffffu, sm0, o);
+      sm1 += __shfl_xor_sync(0xffffffffu, sm1, o);
+    }
     if (lane == 0) {
-      pm[(int64_t)r * a.Npad + i] = mx;
-      ps[(int64_t)r * a.Npad + i] = sm;
+      pm[(int64_t)r * a.Npad + i] = mx0;
+      ps[(int64_t)r * a.Npad + i] = sm0;
+      if (two) {
+        pm[(int64_t)r * a.Npad + i + 1] = mx1;
+        ps[(int64_t)r * a.Npad + i + 1] = sm1;
+      }
     }
   }
 }
@@ -270,8 +317,8 @@ __global__ void __launch_bounds__(32 * FFT_WARPS) k_fft_p1(FftPassArgs a, float*
 // ---------------------------------------------------------------------- pass 2
 // Per (observation block b, phase r): w = 2^(logit2 - lse2) over the lags of phase r;
 // c and zb per shift of phase r, and G_r = sum_i conj(FFT2(w_{i,r})) . Y^'_i, summed
-// over the block's observations in a fixed order (each warp in increasing i, then the
-// warps in order).
+// over the block's observations in a fixed order (each warp over its observation pairs
+// in increasing i, then the warps in order).
 template <int N>
 __global__ void __launch_bounds__(32 * p2_warps<N>(), 1) k_fft_p2(FftPassArgs a, float* __restrict__ cp,
                                                            float* __restrict__ zbp, int Spad,
@@ -294,33 +341,52 @@ __global__ void __launch_bounds__(32 * p2_warps<N>(), 1) k_fft_p2(FftPassArgs a,
   stage_phase<N>(a, r, sX, sCol, mr);
   const int64_t i0 = (int64_t)b * a.B;
   const int64_t i1 = min(a.N, i0 + a.B);
-  for (int64_t i = i0 + warp; i < i1; i += W) {
+  for (int64_t i = i0 + 2 * warp; i < i1; i += 2 * W) {  // pairs (i, i + 1), as in pass 1
+    const bool two = i + 1 < i1;
     float2 v[N];
-    const float yb = a.ybar[i];
-    const float dd = yb - mr;
-    phase_logits<N>(a, i, sX, sCol, tile, lane, -a.c2 * dd * dd, v);
-    const float ls = a.lse2[i];
+    const float yb0 = a.ybar[i], yb1 = two ? a.ybar[i + 1] : 0.f;
+    const float dd0 = yb0 - mr, dd1 = yb1 - mr;
+    phase_logits2<N>(a, i, two, sX, sCol, tile, lane, -a.c2 * dd0 * dd0, -a.c2 * dd1 * dd1, v);
+    const float ls0 = a.lse2[i], ls1 = two ? a.lse2[i + 1] : 0.f;
     if (lane < N) {
 #pragma unroll
       for (int k = 0; k < N; ++k) {
-        const float w = exp2f(v[k].x - ls);
-        crow[k] += w;
-        zrow[k] = fmaf(w, yb, zrow[k]);
-        v[k] = make_float2(w, 0.f);
+        const float w0 = exp2f(v[k].x - ls0);
+        const float w1 = two ? exp2f(v[k].y - ls1) : 0.f;
+        crow[k] += w0;
+        zrow[k] = fmaf(w0, yb0, zrow[k]);
+        crow[k] += w1;
+        zrow[k] = fmaf(w1, yb1, zrow[k]);
+        v[k] = make_float2(w0, w1);
       }
     }
-    // FFT2 of the weight map (row lane = t1 first), then conj(W^) . Y^' by column
+    // F = FFT2(w_i + i w_{i+1}) (row lane = t1 first): v[k] = F[k1 = k][k2 = lane]
     fft_reg<N, false>(v);
     transpose<N, false>(v, tile, lane);
-    fft_reg<N, false>(v);  // v[k] = W^[k1 = k][k2 = lane]
-    if (lane < N) {
-      const float2* yf = a.Yf + i * (N * N);
+    fft_reg<N, false>(v);
+    // W^_i = (F[k] + conj F[-k]) / 2 and W^_{i+1} = (F[k] - conj F[-k]) / (2i); F[-k] is
+    // element (N - k1) mod N of lane (N - k2) mod N.  Then G += conj(W^) . Y^' by column.
+    const int src = (N - lane) & (N - 1);
+    const float2* yf0 = a.Yf + i * (N * N);
+    const float2* yf1 = two ? yf0 + N * N : yf0;  // unconditional loads, as in correlate2
+    const float h1 = two ? 0.5f : 0.f;
 #pragma unroll
-      for (int k = 0; k < N; ++k) {
-        const float2 p = cmul_conj(yf[k * N + lane], v[k]);
+    for (int k = 0; k < N; ++k) {
+      const int km = (N - k) & (N - 1);
+      const float fmx = __shfl_sync(0xffffffffu, v[km].x, src);
+      const float fmy = __shfl_sync(0xffffffffu, v[km].y, src);
+      if (lane < N) {
+        const float2 f = v[k];
+        const float2 y0 = yf0[k * N + lane], y1 = yf1[k * N + lane];
+        const float2 w0 = make_float2(0.5f * (f.x + fmx), 0.5f * (f.y - fmy));
+        const float2 w1 = make_float2(h1 * (f.y + fmy), -h1 * (f.x - fmx));
         float2 acc = g[k * N + lane];
-        acc.x += p.x;
-        acc.y += p.y;
+        const float2 p0 = cmul_conj(y0, w0);
+        acc.x += p0.x;
+        acc.y += p0.y;
+        const float2 p1 = cmul_conj(y1, w1);
+        acc.x += p1.x;
+        acc.y += p1.y;
         g[k * N + lane] = acc;
       }
     }
