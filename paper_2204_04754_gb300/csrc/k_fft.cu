@@ -88,8 +88,18 @@ __device__ __forceinline__ void fft_reg(float2 (&v)[N]) {
       for (int j = 0; j < h; ++j) {
         const float2 a = v[k + j];
         float2 b = v[k + j + h];
-        if (j != 0) {
-          float2 w = c_tw[j * (32 / h)];  // e^{-2 pi i j / (2h)}
+        const int m = j * (32 / h);  // twiddle e^{-2 pi i m / 64} (conjugated when INV)
+        if (m == 16) {  // -i (+i): an exchange of the parts
+          b = INV ? make_float2(-b.y, b.x) : make_float2(b.y, -b.x);
+        } else if (m == 8 || m == 24) {  // (1 -+ i) c and (-1 -+ i) c, c = cos(pi / 4)
+          const float c = c_tw[8].x;
+          const float sp = c * (b.x + b.y), sm = c * (b.x - b.y);
+          if (m == 8)
+            b = INV ? make_float2(sm, sp) : make_float2(sp, -sm);
+          else
+            b = INV ? make_float2(-sp, sm) : make_float2(-sm, -sp);
+        } else if (m != 0) {
+          float2 w = c_tw[m];
           if (INV) w.y = -w.y;
           b = cmul(b, w);
         }
