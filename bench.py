@@ -720,12 +720,15 @@ def serve_block(requests, rates, pool_size, slots, budget_gb, prec, srmra, synth
     free, total = torch.cuda.mem_get_info()
     budget = int(min(free * 0.8, budget_gb * 2 ** 30))
     srv = srmra.Server(budget, max_active=slots, prec=prec, stream=stream.cuda_stream)
-    # warm the kernels and graph machinery on a tiny request (not part of the trace)
-    wp = synth.make_problem(64, 4, 2000, 0.5, seed=synth.seed_for(5, 999))
-    wid = srv.submit(wp.L, wp.K, wp.sigma, wp.y, 2, F=F)
+    # warm the kernels and graph machinery on tiny requests (not part of the trace; with
+    # "auto" one of each form)
+    warm = [(64, 4)] + ([(48, 2)] if prec == "auto" else [])
+    wps = [synth.make_problem(L, K, 2000, 0.5, seed=synth.seed_for(5, 999)) for L, K in warm]
+    wids = [srv.submit(wp.L, wp.K, wp.sigma, wp.y, 2, F=F) for wp in wps]
     while srv.step()[0] > 0:
         pass
-    srv.result(wid, wp.L)
+    for wp, wid in zip(wps, wids):
+        srv.result(wid, wp.L)
     pairs = sum(p.N * p.L * p.L * iters for p in probs)
     sweep = []
     if clocks:
@@ -746,6 +749,9 @@ def serve_block(requests, rates, pool_size, slots, budget_gb, prec, srmra, synth
          "distinct_problems": pool,
          "problems": [{"L": L, "K": K, "N": N, "sigma": sg} for L, K, N, sg in specs],
          "slots": slots, "budget_bytes": budget, "data_generation_s": gen_s,
+         "forms": ({"fft32": sum(1 for p in probs if p.L // p.K in (8, 16, 32)),
+                    "bf16x3": sum(1 for p in probs if p.L // p.K not in (8, 16, 32))}
+                   if prec == "auto" else {prec: n}),
          "p50_ms": head["p50_ms"], "p99_ms": head["p99_ms"], "max_ms": head["max_ms"],
          "solves_per_s": head["solves_per_s"], "pairs_per_s": head["pairs_per_s"],
          "makespan_s": head["makespan_s"], "server_steps": head["server_steps"],
@@ -965,6 +971,9 @@ def main():
                                           srmra, synth, torch, stream, flush)
         out["serve"] = serve_block(16, [2.0], 6, args.serve_slots, args.serve_budget_gb,
                                    "bf16x3", srmra, synth, torch, stream)
+        # the same trace with each request in the form the server picks for it
+        out["serve_auto"] = serve_block(16, [2.0], 6, args.serve_slots, args.serve_budget_gb,
+                                        "auto", srmra, synth, torch, stream)
     if rank == 0 and world == 1 and not args.no_cpu:
         cb = cpu_oracle_rate(p, args.cpu_seconds)
         cb.pop("n_sub", None)

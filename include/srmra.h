@@ -356,11 +356,16 @@ srmra_status srmra_em_iter_batch(srmra_ctx** ctxs, int32_t count, int32_t n_iter
  * Submission may come from another thread than the one calling srmra_server_step. */
 typedef struct srmra_server srmra_server;
 
+/* prec: the form every request runs in (srmra_precision), or SRMRA_SERVER_AUTO: each
+ * request runs in the polyphase-FFT form when L/K is 8, 16 or 32 (faster and more
+ * accurate than the tensor-core forms there) and in SRMRA_BF16X3 otherwise; the server
+ * then keeps one batch per form and advances them in turn each step. */
+#define SRMRA_SERVER_AUTO 4
 srmra_status srmra_server_create(int64_t device_budget_bytes, int32_t max_active,
                                  int32_t prec, void* cuda_stream, srmra_server** out);
 
 /* y: N x l x l float32 host array (p->N, p->L_high, p->K, p->sigma; p->prec is replaced by
- * the server's form); x0: L x L float32 host or NULL (mean-upsampled init).  ENOMEM if
+ * the server's form, or by the form SRMRA_SERVER_AUTO picks); x0: L x L float32 host or NULL (mean-upsampled init).  ENOMEM if
  * the request alone exceeds the budget.  *request_id identifies it. */
 srmra_status srmra_server_submit(srmra_server* s, const srmra_params* p, const float* y,
                                  const float* x0, int32_t iters, int32_t F, double sigma_bm1,

@@ -14,7 +14,9 @@
 //   3. retires requests that reached their iteration count: the estimate is copied to
 //      host memory, the context and its device memory are released.
 // Requests that arrive while others are running join at the next iteration boundary, so
-// their work shares the device with the running ones.  A request's arithmetic does not
+// their work shares the device with the running ones.  A server created with
+// SRMRA_SERVER_AUTO picks each request's form from its size (the polyphase-FFT form where
+// it exists, L/K in {8, 16, 32}, split bf16 otherwise) and keeps one batch per form.  A request's arithmetic does not
 // depend on the other requests in the batch (same per-problem work decomposition, no
 // cross-problem reductions), so its result equals a solve of the same problem alone.
 #include <chrono>
@@ -64,8 +66,8 @@ struct srmra_server {
   std::vector<Request*> running;
   std::unordered_map<int64_t, Request*> all;
   int64_t used = 0;
-  srmra_batch* batch = nullptr;
-  bool dirty = true;
+  srmra_batch* batch[4] = {nullptr, nullptr, nullptr, nullptr};  // one per precision form
+  bool dirty[4] = {true, true, true, true};
   int64_t iterations = 0;
   std::string err;
 };
@@ -113,7 +115,8 @@ srmra_status srmra_server_create(int64_t device_budget_bytes, int32_t max_active
   *out = nullptr;
   if (device_budget_bytes <= 0 || max_active < 1)
     return sfail(nullptr, SRMRA_EINVAL, "need a positive memory budget and slot count");
-  if (prec != SRMRA_FP32 && prec != SRMRA_BF16 && prec != SRMRA_BF16X3 && prec != SRMRA_FFT32)
+  if (prec != SRMRA_FP32 && prec != SRMRA_BF16 && prec != SRMRA_BF16X3 && prec != SRMRA_FFT32 &&
+      prec != SRMRA_SERVER_AUTO)
     return sfail(nullptr, SRMRA_EINVAL, "unknown precision form");
   auto* s = new (std::nothrow) srmra_server();
   if (!s) return sfail(nullptr, SRMRA_ENOMEM, "host allocation failed");
@@ -134,6 +137,11 @@ srmra_status srmra_server_submit(srmra_server* s, const srmra_params* p, const f
     return sfail(s, SRMRA_EINVAL, "need iters >= 1, F >= 0, decay > 0, sigma_bm1 > 0");
   srmra_params q = *p;
   q.prec = s->prec;
+  if (s->prec == SRMRA_SERVER_AUTO) {
+    const int l = p->K > 0 ? p->L_high / p->K : 0;
+    q.prec = (l == 8 || l == 16 || l == 32) && l * p->K == p->L_high ? SRMRA_FFT32
+                                                                      : SRMRA_BF16X3;
+  }
   if (F > 0 && q.L_high % 8 != 0)
     return sfail(s, SRMRA_EINVAL, "built-in denoiser needs L % 8 == 0");
   int64_t bytes = 0;
@@ -199,36 +207,46 @@ srmra_status srmra_server_step(srmra_server* s, int32_t* n_running, int32_t* n_q
     std::vector<float>().swap(r->y);  // the observations now live on the device
     r->state = 1;
     s->running.push_back(r);
-    s->dirty = true;
+    s->dirty[r->p.prec] = true;
   }
   int32_t finished = 0;
   if (!s->running.empty()) {
-    if (s->dirty) {
-      if (s->batch) srmra_batch_destroy(s->batch);
-      s->batch = nullptr;
+    // one batch per precision form among the running requests, advanced in turn
+    for (int f = 0; f < 4; ++f) {
       std::vector<srmra_ctx*> ctxs;
-      for (Request* r : s->running) ctxs.push_back(r->ctx);
-      srmra_status st = srmra_batch_create(ctxs.data(), (int32_t)ctxs.size(), 0, &s->batch);
-      if (st != SRMRA_OK) return sfail(s, st, srmra_batch_last_error(nullptr));
-      s->dirty = false;
+      for (Request* r : s->running)
+        if (r->p.prec == f) ctxs.push_back(r->ctx);
+      if (ctxs.empty()) continue;
+      if (s->dirty[f] || !s->batch[f]) {
+        if (s->batch[f]) srmra_batch_destroy(s->batch[f]);
+        s->batch[f] = nullptr;
+        srmra_status st =
+            srmra_batch_create(ctxs.data(), (int32_t)ctxs.size(), 0, &s->batch[f]);
+        if (st != SRMRA_OK) return sfail(s, st, srmra_batch_last_error(nullptr));
+        s->dirty[f] = false;
+      }
+      srmra_status st = srmra_batch_solve(s->batch[f], 1, -1, 0.0, 1.0, nullptr);
+      if (st != SRMRA_OK) return sfail(s, st, srmra_batch_last_error(s->batch[f]));
     }
-    srmra_status st = srmra_batch_solve(s->batch, 1, -1, 0.0, 1.0, nullptr);
-    if (st != SRMRA_OK) return sfail(s, st, srmra_batch_last_error(s->batch));
     ++s->iterations;
     std::vector<Request*> still;
     for (Request* r : s->running) {
       if (r->ctx->t >= r->iters) {
+        s->dirty[r->p.prec] = true;
         retire(s, r);
         ++finished;
-        s->dirty = true;
       } else {
         still.push_back(r);
       }
     }
     s->running.swap(still);
-    if (s->running.empty() && s->batch) {
-      srmra_batch_destroy(s->batch);
-      s->batch = nullptr;
+    for (int f = 0; f < 4; ++f) {
+      bool any = false;
+      for (Request* r : s->running) any = any || r->p.prec == f;
+      if (!any && s->batch[f]) {
+        srmra_batch_destroy(s->batch[f]);
+        s->batch[f] = nullptr;
+      }
     }
   }
   std::lock_guard<std::mutex> lock(s->mu);
@@ -274,7 +292,8 @@ srmra_status srmra_server_memory(srmra_server* s, int64_t* used, int64_t* budget
 
 void srmra_server_destroy(srmra_server* s) {
   if (!s) return;
-  if (s->batch) srmra_batch_destroy(s->batch);
+  for (int f = 0; f < 4; ++f)
+    if (s->batch[f]) srmra_batch_destroy(s->batch[f]);
   for (auto& kv : s->all) {
     if (kv.second->ctx) srmra_destroy(kv.second->ctx);
     delete kv.second;

@@ -31,6 +31,7 @@ SRMRA_FLAG_MSTEP_COMP = 4
 SRMRA_FLAG_MSTEP_FP16 = 8
 SRMRA_FLAG_P1_TILE128 = 16
 SRMRA_FLAG_P2_PAIR = 32
+SRMRA_SERVER_AUTO = 4  # srmra_server_create: the form picked per request
 
 
 class srmra_params(Structure):
@@ -583,13 +584,15 @@ class Mom:
 
 
 class Server:
-    """Continuous-batching request server (see include/srmra.h)."""
+    """Continuous-batching request server (see include/srmra.h).  prec: a form for every
+    request, or "auto" (the polyphase-FFT form where L/K is 8, 16 or 32, else bf16x3)."""
 
     def __init__(self, budget_bytes: int, max_active: int, prec: str = "bf16x3",
                  stream: int = 0):
         out = c_void_p()
         self.prec = prec
-        st = lib().srmra_server_create(int(budget_bytes), int(max_active), PRECISIONS[prec],
+        code = SRMRA_SERVER_AUTO if prec == "auto" else PRECISIONS[prec]
+        st = lib().srmra_server_create(int(budget_bytes), int(max_active), code,
                                        c_void_p(stream or None), byref(out))
         self._scheck(st, None)
         self.handle = out.value
@@ -603,7 +606,9 @@ class Server:
                decay: float = 2.0 ** -0.1, x0=None) -> int:
         y = np.ascontiguousarray(y, np.float32)
         x0 = None if x0 is None else np.ascontiguousarray(x0, np.float32)
-        p = srmra_params(int(L), int(K), int(y.shape[0]), float(sigma), PRECISIONS[self.prec], 0)
+        # (the server replaces the form with its own, or with the one it picks)
+        p = srmra_params(int(L), int(K), int(y.shape[0]), float(sigma),
+                         PRECISIONS.get(self.prec, SRMRA_BF16X3), 0)
         rid = c_int64()
         self._scheck(lib().srmra_server_submit(self.handle, byref(p), _ptr(y), _ptr(x0),
                                                int(iters), int(F), float(sigma_bm1),

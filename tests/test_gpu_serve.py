@@ -29,17 +29,30 @@ def problems():
             for k, (L, K, N, s, _) in enumerate(REQS)]
 
 
-@pytest.mark.parametrize("prec", ["bf16x3", "fp32"])
+def form_of(prec, p):
+    """The form a request of problem p runs in on a server of form prec ("auto": the
+    polyphase-FFT form where L/K is 8, 16 or 32, else bf16x3)."""
+    if prec != "auto":
+        return prec
+    return "fft32" if p.L // p.K in (8, 16, 32) else "bf16x3"
+
+
+@pytest.mark.parametrize("prec", ["bf16x3", "fp32", "auto"])
 def test_results_same_alone_and_in_the_mix(S, prec):
+    """With "auto" the mix holds FFT-form and bf16x3 requests (two batches per step)."""
     probs = problems()
     iters = [r[4] for r in REQS]
+    forms = [form_of(prec, p) for p in probs]
+    if prec == "auto":
+        assert {"fft32", "bf16x3"} <= set(forms), forms
     alone = []
-    for p, it in zip(probs, iters):
-        s = S.Solver(p.L, p.K, p.sigma, p.y, prec=prec)
+    for p, it, f in zip(probs, iters, forms):
+        s = S.Solver(p.L, p.K, p.sigma, p.y, prec=f)
         s.solve(it, 1)
         alone.append(s.state())
         s.close()
-    need = [S.srmra_estimate_device_bytes(p.L, p.K, p.N, p.sigma, prec) for p in probs]
+    need = [S.srmra_estimate_device_bytes(p.L, p.K, p.N, p.sigma, f)
+            for p, f in zip(probs, forms)]
     # room for about three requests at once, and for every request on its own
     budget = max(sum(need[:3]), max(need))
     srv = S.Server(budget, max_active=4, prec=prec)
