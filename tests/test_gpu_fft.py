@@ -22,6 +22,9 @@ CASES = [
     (24, 3, 333, 0.5),    # l = 8, K = 3, N % 8 != 0
     (32, 4, 129, 0.6),    # l = 8, K = 4
     (8, 1, 130, 0.5),     # K = 1: classic 2D MRA
+    # odd N: the last observation pair of the last block holds one observation
+    (64, 2, 701, 0.3),    # l = 32
+    (32, 2, 333, 0.4),    # l = 16
 ]
 
 
